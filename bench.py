@@ -1,0 +1,379 @@
+"""Benchmark of the SMPC replanning loop (one 'step' = one replan).
+
+Workload (config 2 of the workloads): 7-DoF arm, K = 4096 roll-outs,
+H = 64, 8 SMPC iterations per replan, a 160 x 160 x 120 distance field at
+1 cm built from 20 seeded boxes and balls, and a target pose moving on a
+seeded circle at 0.2 m/s.  The 200-replan episode repeats until --steps
+replans have run (the state restarts every 200).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  'value' is device-timed (inputs resident in
+HBM, CUDA events per replan on the launching stream, a 256 MiB buffer
+written between replans to flush L2); 'e2e' is the same metric through the
+C ABI with host buffers (copies in and out inside the timed region).
+With torchrun (N > 1) every rank plans its own arm (independent replicas).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rollout-steps/s; replan p50/p99 ms served vs per-request plain, same GPU"
+UNIT = "rollout-steps/s"
+EPISODE = 200
+# Algorithmic FP32 operations of one roll-out step (FMA = 2; transcendental
+# calls, integer Philox work and loads not counted), from the kernel's
+# source-level arithmetic: sampling 46, roll-out scans 128, control costs 66,
+# kinematics 349, 28 sphere lookups 1736, SE(3) pose error 135, state limits
+# and null space 127, accumulation 5.  The terminal step (no spheres or
+# state limits) is 729.
+FLOPS_STEP = 2592
+FLOPS_TERMINAL = 729
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2032.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+def load_workload():
+    import workloads
+    sc = workloads.load_scene("cfg2")
+    return {
+        "scene": sc,
+        "phi": workloads.build_scene_grid(sc),
+        "robot": workloads.panda_robot(),
+        "cp": workloads.default_cost_params(sc["q0"]),
+        "K": int(sc["K"]), "H": int(sc["H"]), "iters": int(sc["iters"]),
+        "dt": float(sc["dt"]), "lam": float(sc["lambda"]),
+        "sigma": np.full(7, sc["sigma"], dtype=np.float32),
+    }
+
+
+def targets(w, n):
+    import workloads
+    sc = w["scene"]
+    T0 = sc["T_goal"].reshape(4, 4)
+    return np.stack([workloads.moving_target(T0, sc["path_seed"], (r % EPISODE) * w["dt"],
+                                             speed=sc["target_speed"]).ravel()
+                     for r in range(n)]).astype(np.float32)
+
+
+def config_dict(w, world, flush):
+    g = w["scene"]["grid"]
+    return {"workload": "SMPC replanning loop (config 2): 7-DoF arm, K=4096 roll-outs, H=64, "
+                        "8 iterations per replan, 200-replan episodes, moving target",
+            "K": w["K"], "H": w["H"], "iters_per_replan": w["iters"],
+            "grid": [g.nx, g.ny, g.nz], "voxel_m": g.res, "grid_dtype": "f32",
+            "replicas": world, "parallelism": f"replicas{world}",
+            "l2": f"flushed between replans ({flush} MiB write)"}
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_time(w, K_sample, iters, budget_s, n_threads, seed=100):
+    """Time the FP64 oracle's SMPC iterations on a roll-out sample."""
+    import oracle
+    sc = w["scene"]
+    R = oracle.make_robot(w["robot"])
+    G = oracle.Grid(sc["grid"], w["phi"])
+    Cc = oracle.make_cost(w["cp"])
+    T = sc["T_goal"].reshape(4, 4)
+    U = np.zeros((w["H"], 7))
+    done, steps = 0, 0
+    t0 = time.perf_counter()
+    while done < iters:
+        U, _, _ = oracle.smpc_iterate(R, G, Cc, sc["q0"], sc["qd0"], T, U, K_sample, w["dt"],
+                                      w["lam"], w["sigma"], seed, done, n_threads=n_threads)
+        done += 1
+        steps += K_sample * w["H"]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return steps / dt, done, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm (host cores), one bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    w = load_workload()
+    cores = oracle.cores_available()
+    K_sample = 64
+    R = oracle.make_robot(w["robot"])
+    sc = w["scene"]
+    G = oracle.Grid(sc["grid"], w["phi"])
+    Cc = oracle.make_cost(w["cp"])
+    Ts = targets(w, args.warmup + args.steps)
+    q, qd, U = sc["q0"].astype(np.float64), sc["qd0"].astype(np.float64), np.zeros((w["H"], 7))
+    t_timed = 0.0
+    for r in range(args.warmup + args.steps):
+        if r % EPISODE == 0:
+            q, qd, U = sc["q0"].astype(np.float64), sc["qd0"].astype(np.float64), np.zeros((w["H"], 7))
+        t0 = time.perf_counter()
+        q, qd, U, _, _ = oracle.replan(R, G, Cc, q, qd, Ts[r].reshape(4, 4), U, K_sample, w["dt"],
+                                       w["lam"], w["sigma"], 100, r % EPISODE, w["iters"],
+                                       n_threads=cores)
+        if r >= args.warmup:
+            t_timed += time.perf_counter() - t0
+    units = K_sample * w["H"] * w["iters"] * args.steps
+    value = units / t_timed
+    sample = (f"{K_sample} of the 4096 roll-outs per replan (same H, iterations, grid and "
+              f"target path), {args.steps} replans")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_timed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, 1, 0) | {"l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2512_22575_b300 as pm
+
+    w = load_workload()
+    K, H, iters, dt, lam, sigma = w["K"], w["H"], w["iters"], w["dt"], w["lam"], w["sigma"]
+    sc = w["scene"]
+    seed = 100 + rank
+    n_total = args.warmup + args.steps
+    Ts_host = targets(w, n_total)
+
+    planner = pm.Planner(w["robot"], sc["grid"], w["cp"], device=local)
+    planner.set_distance_field(w["phi"])
+    stream = torch.cuda.Stream(device=dev)
+    flush_mb = args.flush_mb
+    flush = torch.empty(flush_mb << 20, dtype=torch.uint8, device=dev)
+
+    Ts = torch.from_numpy(Ts_host).to(dev)
+    q0 = torch.from_numpy(sc["q0"].astype(np.float32)).to(dev)
+    qd0 = torch.from_numpy(sc["qd0"].astype(np.float32)).to(dev)
+    q, qd = q0.clone(), qd0.clone()
+    U = torch.zeros((H, 7), dtype=torch.float32, device=dev)
+    u0 = torch.empty(7, dtype=torch.float32, device=dev)
+    best = torch.empty(1, dtype=torch.float32, device=dev)
+
+    def episode_reset(r):
+        if r % EPISODE == 0:
+            q.copy_(q0); qd.copy_(qd0); U.zero_()
+
+    with torch.cuda.stream(stream):
+        for r in range(args.warmup):
+            episode_reset(r)
+            planner.replan(q, qd, Ts[r], U, K, iters, dt, lam, sigma, seed, r % EPISODE,
+                           u0_out=u0, best_cost=best, stream=stream)
+            flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    planner.profile_enable(True)
+    planner.profile_read(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            r = args.warmup + i
+            episode_reset(r)
+            ev[i][0].record(stream)
+            planner.replan(q, qd, Ts[r], U, K, iters, dt, lam, sigma, seed, r % EPISODE,
+                           u0_out=u0, best_cost=best, stream=stream)
+            ev[i][1].record(stream)
+            flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    kernel_ms, launches = planner.profile_read(reset=True)
+    planner.profile_enable(False)
+    step_ms = np.array([s.elapsed_time(e) for s, e in ev])
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = K * H * iters * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    n_e2e = min(args.steps, args.e2e_steps)
+    qh, qdh = sc["q0"].astype(np.float32).copy(), sc["qd0"].astype(np.float32).copy()
+    Uh = np.zeros((H, 7), np.float32)
+    u0h, besth = np.empty(7, np.float32), np.empty(1, np.float32)
+    for r in range(3):
+        planner.replan(qh, qdh, Ts_host[r], Uh, K, iters, dt, lam, sigma, seed, r,
+                       u0_out=u0h, best_cost=besth)
+    qh, qdh = sc["q0"].astype(np.float32).copy(), sc["qd0"].astype(np.float32).copy()
+    Uh[:] = 0
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        r = i % EPISODE
+        if r == 0:
+            qh[:] = sc["q0"]; qdh[:] = sc["qd0"]; Uh[:] = 0
+        planner.replan(qh, qdh, Ts_host[r], Uh, K, iters, dt, lam, sigma, seed, r,
+                       u0_out=u0h, best_cost=besth)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = K * H * iters * n_e2e * world / e2e_s
+    state_bytes = 36 * 4                    # q0, qd0, R_g, t_g, sigma as staged
+    h2d = state_bytes + H * 7 * 4           # + U
+    d2h = 25 * 4 + H * 7 * 4                # q, qd, u0, best + U
+
+    # roofline of the iteration kernel (algorithmic FP32 flops / event-timed duration)
+    flops_launch = K * ((H - 1) * FLOPS_STEP + FLOPS_TERMINAL)
+    avg_kernel_s = kernel_ms / 1e3 / max(launches, 1)
+    achieved = flops_launch / avg_kernel_s / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "smpc_iteration_kernel<C=2,L=32,float>",
+                "kernel_ms_per_launch": avg_kernel_s * 1e3, "launches_timed": launches,
+                "flops_per_launch": flops_launch,
+                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
+                              f"x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (unit counts and max clock)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_dict(w, world, flush_mb),
+        "replan_ms": {"p50": float(np.percentile(step_ms, 50)),
+                      "p99": float(np.percentile(step_ms, 99)), "mean": float(step_ms.mean())},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": n_e2e,
+                "ms_per_step": 1e3 * e2e_s / n_e2e},
+        "gpu_launches": args.steps * (iters + 1),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    planner.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.cores_available()
+        v, n_it, secs = cpu_oracle_time(w, K, 1000, args.cpu_budget, cores)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_it} full SMPC iterations of the config-2 workload (K=4096, H=64) "
+                      f"in {secs:.1f} s, OpenMP over roll-outs"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--flush-mb", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

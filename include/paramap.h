@@ -1,0 +1,232 @@
+/*
+ * paramap.h -- C ABI of the B300 (sm_103a) sampling-based MPC hot path.
+ *
+ * One SMPC iteration (ParaMaP, arXiv 2512.22575, Algorithm 1 and Sec. IV-C)
+ * over a batch of K candidate roll-outs of a 7-DoF arm: Gaussian
+ * perturbations of the nominal joint-acceleration sequence (Eq. 19),
+ * Euler roll-out (Eq. 2), forward kinematics (Eq. 1), collision-sphere
+ * clearance from a dense distance field (Eqs. 14-16), SE(3) pose error
+ * (Eqs. 8-13), joint-limit, smoothness, null-space and terminal costs
+ * (Eqs. 17-22), soft-min weights (Eq. 25) and the weighted-mean update of
+ * the nominal sequence (Eq. 26).  All of it runs in the library's CUDA
+ * kernels on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a pm_status; nothing throws across the ABI.  On any
+ *    status other than PM_OK the caller's output buffers are left untouched
+ *    and pm_last_error() describes the failure.
+ *  - Pointers marked "host or device" may point to host memory (pageable or
+ *    pinned) or to device memory of the context's GPU; the library detects
+ *    which.  If any output pointer is host memory the call waits for its
+ *    stream before returning; if all inputs and outputs are device memory
+ *    the call only enqueues work on the stream (outputs are valid once the
+ *    stream reaches that point).
+ *  - The caller owns every buffer it passes.  The library copies the robot
+ *    description, cost parameters and distance field into memory it owns.
+ *  - A context may be used from one host thread at a time (calls on one
+ *    context are serialised by an internal lock); different contexts are
+ *    independent.
+ *  - Layouts: joint vectors are float[n_joints]; control sequences U are
+ *    row-major float[H][n_joints]; poses are row-major float[16]
+ *    homogeneous matrices; the distance field is float[nz][ny][nx]
+ *    (x fastest).
+ *  - This build compiles the kinematic chain for n_joints == 7.
+ */
+#ifndef PARAMAP_H
+#define PARAMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_MAX_JOINTS 8
+#define PM_MAX_SPHERES 64
+#define PM_MAX_HORIZON 256
+#define PM_MAX_ROLLOUTS (1 << 22)
+
+typedef struct pm_ctx pm_ctx;
+
+typedef enum {
+    PM_OK = 0,
+    PM_EINVAL = 1,     /* an argument is out of range, NaN or missing        */
+    PM_ENOMEM = 2,     /* a device or pinned-host allocation failed          */
+    PM_EBUSY = 3,      /* serving: request not admitted before its deadline  */
+    PM_ETIMEOUT = 4,   /* a bounded device wait gave up (status word set)    */
+    PM_ECUDA = 5,      /* a CUDA runtime call failed                         */
+    PM_ENOTREADY = 6,  /* serving: the ticket's result is not ready yet      */
+    PM_EINTERNAL = 7
+} pm_status;
+
+typedef enum { PM_F32 = 0, PM_F16 = 1, PM_BF16 = 2 } pm_dtype;
+
+/*
+ * Arm description (Sec. IV-A, Eq. 1; sphere model of Sec. IV-B-2, Fig. 2).
+ * Modified (Craig) DH per joint i = 1..n, stored at index i-1:
+ *   T_i = T_{i-1} RotX(alpha[i-1]) TransX(a[i-1]) RotZ(q_i + theta_offset[i-1])
+ *         TransZ(d[i-1]),
+ * and the end effector is the flange T_n TransZ(flange_d).
+ * Sphere s is centred at R^{L} sphere_offset[s] + t^{L} with L =
+ * sphere_link[s] in 1..n (frame index) and has radius sphere_radius[s].
+ * self_pairs lists sphere index pairs (i, j) of the self-collision set S of
+ * Eq. 15 (may be empty; n_self_pairs = 0).
+ */
+typedef struct {
+    int n_joints;
+    const float *a, *d, *alpha, *theta_offset;   /* [n_joints]            */
+    float flange_d;
+    const float *q_min, *q_max;                  /* [n_joints] rad        */
+    const float *qd_max, *qdd_max;               /* [n_joints], symmetric */
+    int n_spheres;                               /* 0..PM_MAX_SPHERES     */
+    const int *sphere_link;                      /* [n_spheres]           */
+    const float *sphere_offset;                  /* [n_spheres][3]        */
+    const float *sphere_radius;                  /* [n_spheres]           */
+    int n_self_pairs;
+    const int *self_pairs;                       /* [n_self_pairs][2]     */
+} pm_robot;
+
+/*
+ * Dense distance field phi of Eq. 14 (unsigned Euclidean distance in metres
+ * to the nearest occupied voxel centre, 0 inside obstacles).  Voxel (i, j, l)
+ * has centre origin + (i + 0.5, j + 0.5, l + 0.5) * res; each axis needs at
+ * least 2 voxels.  phi(p) is the trilinear interpolation of the centre
+ * samples with p clamped to the grid (edge replication outside).
+ * dtype selects the device copy's storage: PM_F32, or PM_F16 / PM_BF16 to
+ * halve the gather traffic (the lookup arithmetic stays FP32).
+ */
+typedef struct {
+    int nx, ny, nz;
+    float res;
+    float origin[3];
+    int dtype;
+} pm_grid_desc;
+
+/*
+ * Cost weights (Sec. IV-B).  Q and QH are the diagonals of Q_k (k < H) and
+ * Q_H acting on xi = [v; omega] (Eqs. 13, 22).  w_env, d_act: Eq. 16;
+ * w_self: Eq. 16 over self_pairs; w_q, w_qd, w_qdd with the box tightened by
+ * margin_frac * (max - min) per joint: Eqs. 17-18; w_s: Eq. 20; w_ns with
+ * q_ref[n_joints]: Eq. 21.
+ */
+typedef struct {
+    float Q[6], QH[6];
+    float w_env, d_act, w_self;
+    float w_q, w_qd, w_qdd, margin_frac;
+    float w_s, w_ns;
+    const float *q_ref;
+} pm_cost_params;
+
+/*
+ * Create a planning context on CUDA device `device` for one arm and one
+ * distance-field geometry.  Copies *robot and *costs; allocates the device
+ * field of the size grid describes (filled by pm_set_distance_field).
+ * Errors: PM_EINVAL (n_joints != 7, a count out of range, NaN, grid axis
+ * < 2), PM_ECUDA, PM_ENOMEM.  On success *out owns all device memory until
+ * pm_destroy.
+ */
+pm_status pm_create(const pm_robot *robot, const pm_grid_desc *grid,
+                    const pm_cost_params *costs, int device, pm_ctx **out);
+
+/*
+ * Copy the dense float32 distance field [nz][ny][nx] into the context
+ * (converting to the context's storage dtype).  `grid` is host memory if
+ * grid_is_device == 0, else device memory of the context's GPU.  The copy
+ * completes before the call returns.  Errors: PM_EINVAL (NULL), PM_ECUDA.
+ */
+pm_status pm_set_distance_field(pm_ctx *ctx, const float *grid, int grid_is_device);
+
+/*
+ * One SMPC iteration (Algorithm 1; Eqs. 19-26).
+ *   q0, qd0   [7]     start state q_0, qdot_0 (host or device)
+ *   T_goal    [16]    target pose T_g, row-major (host or device)
+ *   U         [H][7]  in: nominal sequence Ubar; out: U* of Eq. 26
+ *                     (host or device; device buffers are updated in place)
+ *   K                 number of roll-outs M, 1..PM_MAX_ROLLOUTS
+ *   H                 horizon, 1..PM_MAX_HORIZON
+ *   dt                integration step of Eq. 2 (semi-implicit Euler:
+ *                     qd_{k+1} = qd_k + dt u_k, q_{k+1} = q_k + dt qd_{k+1})
+ *   lambda            temperature of Eq. 25, > 0
+ *   sigma     [7]     per-joint standard deviation of D (host)
+ *   seed, iter_index  noise of roll-out m at step k is Philox4x32-10 with
+ *                     key (seed lo, seed hi) and counter (m, k, b, iter_index)
+ *                     mapped by Box-Muller (b = 0: joints 0-3, b = 1: 4-6)
+ *   costs_out [K]     S^(m) of Eq. 24, or NULL (host or device)
+ *   cuda_stream       cudaStream_t to run on, or NULL for the context's own
+ * Errors: PM_EINVAL (range, NaN in q0/qd0/T_goal/sigma, no field set; U is
+ * left untouched), PM_ENOMEM, PM_ECUDA.
+ */
+pm_status pm_smpc_iterate(pm_ctx *ctx, const float *q0, const float *qd0,
+                          const float *T_goal, float *U, int K, int H, float dt,
+                          float lambda, const float *sigma, uint64_t seed,
+                          uint32_t iter_index, float *costs_out, void *cuda_stream);
+
+/*
+ * One receding-horizon replan (Sec. IV-C, last paragraph): n_iters SMPC
+ * iterations from the nominal U with iter_index = replan_index * n_iters +
+ * it, then the first control u_0* is executed for one step of the same
+ * integrator and the sequence is shifted one step left (last row repeated)
+ * to warm-start the next replan.
+ *   q, qd     [7]    in: current state; out: state after u_0* (host or device)
+ *   T_goal    [16]   target pose for this replan (host or device)
+ *   U         [H][7] in: nominal; out: shifted U* (host or device)
+ *   u0_out    [7]    executed control u_0*, or NULL (host or device)
+ *   best_cost [1]    min_m S^(m) of the last iteration, or NULL (host or device)
+ * Other arguments as pm_smpc_iterate.  Errors as pm_smpc_iterate.
+ */
+pm_status pm_replan(pm_ctx *ctx, float *q, float *qd, const float *T_goal, float *U,
+                    int K, int H, int n_iters, float dt, float lambda,
+                    const float *sigma, uint64_t seed, uint32_t replan_index,
+                    float *u0_out, float *best_cost, void *cuda_stream);
+
+/*
+ * Diagnostics used by the parity tests (same device code as the hot path).
+ *
+ * pm_philox4x32_10: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key) for
+ *   i < n, as the sampler computes it (Salmon et al., SC'11; Eq. 19).
+ *   ctr, out: device memory, uint32[n][4].  Enqueued on cuda_stream.
+ * pm_sample_noise: eps[m][k][j] = sigma_j z_j(m, k) for m < K, k < H, j < 7
+ *   (Alg. 1 line 3).  eps: device float[K][H][7].  Enqueued on cuda_stream.
+ * pm_rollout_trace: per-step cost terms of roll-outs 0..K-1 of the iteration
+ *   pm_smpc_iterate would run with the same arguments; trace: device
+ *   float[K][H+1][8] with columns (pose, env, self, lim_q, lim_qd, lim_qdd,
+ *   smooth, ns); row H holds the terminal cost in the pose column.  State
+ *   terms of row 0 are the same for every roll-out and are left at 0.
+ *   U is read, not updated.  Waits for the stream.
+ */
+pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, size_t n,
+                           void *cuda_stream);
+pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed,
+                          uint32_t iter_index, float *eps, void *cuda_stream);
+pm_status pm_rollout_trace(pm_ctx *ctx, const float *q0, const float *qd0,
+                           const float *T_goal, const float *U, int K, int H, float dt,
+                           const float *sigma, uint64_t seed, uint32_t iter_index,
+                           float *trace);
+
+/*
+ * Kernel timing (observability; no counterpart in the paper).  While enabled,
+ * every SMPC iteration kernel the context launches is bracketed by a pair of
+ * CUDA events recorded on the stream it runs on.  pm_profile_read waits for
+ * the context's last stream, returns the summed kernel time in milliseconds
+ * and the number of timed launches, and clears the record if reset != 0.
+ * Errors: PM_EINVAL (NULL ctx / outputs), PM_ECUDA.
+ */
+pm_status pm_profile_enable(pm_ctx *ctx, int enable);
+pm_status pm_profile_read(pm_ctx *ctx, double *total_ms, uint64_t *launches, int reset);
+
+/* Release every resource of the context (NULL is a no-op). */
+void pm_destroy(pm_ctx *ctx);
+
+/* Human-readable description of the last failure on ctx (or of the last
+ * failure of a context-free call when ctx is NULL).  Valid until the next
+ * call on the same context. */
+const char *pm_last_error(pm_ctx *ctx);
+
+/* Library version string. */
+const char *pm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARAMAP_H */

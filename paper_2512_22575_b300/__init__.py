@@ -1,0 +1,250 @@
+"""Python binding of libparamap.so, the B300 SMPC hot path (ParaMaP, arXiv 2512.22575).
+
+Argument marshalling only: every step of the SMPC iteration runs in the
+library's CUDA kernels.  The functions carry the C ABI's names without the
+``pm_`` prefix (``create``, ``set_distance_field``, ``smpc_iterate``,
+``replan``, ``philox4x32_10``, ``sample_noise``, ``rollout_trace``,
+``destroy``, ``last_error``).  Array arguments may be numpy arrays (host
+memory) or torch tensors (host or CUDA); they must be contiguous float32
+(uint32 for Philox).  A failing call raises ``PmError`` with the library's
+message.  Importing this package loads the library and raises if it is
+missing: there is no fallback implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._abi import (PM_BF16, PM_F16, PM_F32, PmCostParams, PmError, PmGridDesc, PmRobot,
+                   STATUS_NAMES, lib, lib_path)
+
+__all__ = [
+    "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
+    "create", "set_distance_field", "smpc_iterate", "replan", "philox4x32_10",
+    "sample_noise", "rollout_trace", "profile_enable", "profile_read", "destroy",
+    "last_error", "Planner",
+]
+
+_DTYPES = {"f32": PM_F32, "f16": PM_F16, "bf16": PM_BF16,
+           PM_F32: PM_F32, PM_F16: PM_F16, PM_BF16: PM_BF16}
+
+
+def version():
+    return lib().pm_version().decode()
+
+
+def last_error(ctx=None):
+    return lib().pm_last_error(ctx).decode()
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        raise PmError(status, STATUS_NAMES.get(status, str(status)), last_error(ctx))
+
+
+def _ptr(x, dtype=np.float32, n=None, writable=False):
+    """Raw address of a numpy array / torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float32: "torch.float32", np.uint32: "torch.uint32"}[dtype]
+        if str(x.dtype) != want:
+            raise ValueError(f"tensor dtype {x.dtype} != {want}")
+        if n is not None and x.numel() < n:
+            raise ValueError(f"tensor has {x.numel()} elements, need {n}")
+        return C.c_void_p(x.data_ptr())
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise ValueError(f"expected a C-contiguous numpy {np.dtype(dtype).name} array")
+    if writable and not x.flags.writeable:
+        raise ValueError("output array is read-only")
+    if n is not None and x.size < n:
+        raise ValueError(f"array has {x.size} elements, need {n}")
+    return C.c_void_p(x.ctypes.data)
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+class _Keep:
+    """Holds the numpy buffers a C struct points into."""
+
+    def __init__(self):
+        self.bufs = []
+
+    def f32(self, a, n=None):
+        a = _f32(a)
+        if n is not None and a.size < n:
+            raise ValueError(f"expected at least {n} values, got {a.size}")
+        self.bufs.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_float))
+
+    def i32(self, a):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+        self.bufs.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def create(robot, grid_desc, costs, device=0, dtype="f32"):
+    """pm_create: robot / costs as dicts (see workloads.robot), grid_desc with
+    nx, ny, nz, res, origin.  Returns an opaque context handle."""
+    keep = _Keep()
+    n = int(robot["n_joints"])
+    r = PmRobot()
+    r.n_joints = n
+    r.a = keep.f32(robot["a"], n); r.d = keep.f32(robot["d"], n)
+    r.alpha = keep.f32(robot["alpha"], n); r.theta_offset = keep.f32(robot["theta_offset"], n)
+    r.flange_d = float(robot["flange_d"])
+    r.q_min = keep.f32(robot["q_min"], n); r.q_max = keep.f32(robot["q_max"], n)
+    r.qd_max = keep.f32(robot["qd_max"], n); r.qdd_max = keep.f32(robot["qdd_max"], n)
+    ns = len(robot["sphere_radius"])
+    r.n_spheres = ns
+    r.sphere_link = keep.i32(robot["sphere_link"])
+    r.sphere_offset = keep.f32(robot["sphere_offset"], 3 * ns)
+    r.sphere_radius = keep.f32(robot["sphere_radius"], ns)
+    pairs = np.asarray(robot.get("self_pairs", np.zeros((0, 2))), dtype=np.int32).reshape(-1, 2)
+    r.n_self_pairs = len(pairs)
+    r.self_pairs = keep.i32(pairs) if len(pairs) else None
+    g = PmGridDesc()
+    g.nx, g.ny, g.nz = int(grid_desc.nx), int(grid_desc.ny), int(grid_desc.nz)
+    g.res = float(grid_desc.res)
+    for i in range(3):
+        g.origin[i] = float(grid_desc.origin[i])
+    g.dtype = _DTYPES[dtype]
+    cp = PmCostParams()
+    for i in range(6):
+        cp.Q[i] = float(costs["Q"][i]); cp.QH[i] = float(costs["QH"][i])
+    for k in ("w_env", "d_act", "w_self", "w_q", "w_qd", "w_qdd", "margin_frac", "w_s", "w_ns"):
+        setattr(cp, k, float(costs[k]))
+    cp.q_ref = keep.f32(costs["q_ref"], n)
+    out = C.c_void_p()
+    _check(lib().pm_create(C.byref(r), C.byref(g), C.byref(cp), int(device), C.byref(out)))
+    return out
+
+
+def set_distance_field(ctx, grid):
+    """pm_set_distance_field: grid float32 [nz][ny][nx] (numpy or CUDA tensor)."""
+    is_dev = hasattr(grid, "is_cuda") and grid.is_cuda
+    if not hasattr(grid, "data_ptr"):
+        grid = _f32(grid)
+    _check(lib().pm_set_distance_field(ctx, _ptr(grid), int(is_dev)), ctx)
+
+
+def smpc_iterate(ctx, q0, qd0, T_goal, U, K, dt, lam, sigma, seed, iter_index,
+                 costs_out=None, stream=None):
+    """pm_smpc_iterate: U [H][7] is updated in place to U*."""
+    H = int(U.shape[0])
+    sigma = _f32(sigma, 7)
+    _check(lib().pm_smpc_iterate(ctx, _ptr(q0, n=7), _ptr(qd0, n=7), _ptr(T_goal, n=16),
+                                 _ptr(U, n=7 * H, writable=True), int(K), H, float(dt),
+                                 float(lam), _ptr(sigma), C.c_uint64(int(seed)),
+                                 C.c_uint32(int(iter_index)), _ptr(costs_out, n=int(K), writable=True),
+                                 _stream(stream)), ctx)
+
+
+def replan(ctx, q, qd, T_goal, U, K, n_iters, dt, lam, sigma, seed, replan_index,
+           u0_out=None, best_cost=None, stream=None):
+    """pm_replan: q, qd advanced and U shifted in place."""
+    H = int(U.shape[0])
+    sigma = _f32(sigma, 7)
+    _check(lib().pm_replan(ctx, _ptr(q, n=7, writable=True), _ptr(qd, n=7, writable=True),
+                           _ptr(T_goal, n=16), _ptr(U, n=7 * H, writable=True), int(K), H,
+                           int(n_iters), float(dt), float(lam), _ptr(sigma),
+                           C.c_uint64(int(seed)), C.c_uint32(int(replan_index)),
+                           _ptr(u0_out, n=7, writable=True), _ptr(best_cost, n=1, writable=True),
+                           _stream(stream)), ctx)
+
+
+def rollout_trace(ctx, q0, qd0, T_goal, U, K, dt, sigma, seed, iter_index, trace):
+    """pm_rollout_trace: trace is a CUDA float32 tensor [K][H+1][8]."""
+    H = int(U.shape[0])
+    sigma = _f32(sigma, 7)
+    _check(lib().pm_rollout_trace(ctx, _ptr(q0, n=7), _ptr(qd0, n=7), _ptr(T_goal, n=16),
+                                  _ptr(U, n=7 * H), int(K), H, float(dt), _ptr(sigma),
+                                  C.c_uint64(int(seed)), C.c_uint32(int(iter_index)),
+                                  _ptr(trace, n=int(K) * (H + 1) * 8, writable=True)), ctx)
+
+
+def philox4x32_10(ctr, key, out, stream=None):
+    """pm_philox4x32_10 on CUDA uint32 tensors ctr, out of shape [n][4]."""
+    n = ctr.numel() // 4
+    _check(lib().pm_philox4x32_10(_ptr(ctr, np.uint32, 4 * n), C.c_uint64(int(key)),
+                                  _ptr(out, np.uint32, 4 * n), C.c_size_t(n), _stream(stream)))
+
+
+def sample_noise(K, H, sigma, seed, iter_index, eps, stream=None):
+    """pm_sample_noise into a CUDA float32 tensor eps [K][H][7]."""
+    sigma = _f32(sigma, 7)
+    _check(lib().pm_sample_noise(int(K), int(H), _ptr(sigma), C.c_uint64(int(seed)),
+                                 C.c_uint32(int(iter_index)), _ptr(eps, n=int(K) * int(H) * 7),
+                                 _stream(stream)))
+
+
+def profile_enable(ctx, enable=True):
+    """pm_profile_enable: bracket iteration kernels with CUDA events."""
+    _check(lib().pm_profile_enable(ctx, int(bool(enable))), ctx)
+
+
+def profile_read(ctx, reset=True):
+    """pm_profile_read: (summed kernel milliseconds, timed launches)."""
+    ms = C.c_double()
+    n = C.c_uint64()
+    _check(lib().pm_profile_read(ctx, C.byref(ms), C.byref(n), int(bool(reset))), ctx)
+    return ms.value, n.value
+
+
+def destroy(ctx):
+    lib().pm_destroy(ctx)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Planner:
+    """Owns one context; methods forward to the functions above."""
+
+    def __init__(self, robot, grid_desc, costs, device=0, dtype="f32"):
+        self.ctx = create(robot, grid_desc, costs, device, dtype)
+        self.grid_desc = grid_desc
+
+    def set_distance_field(self, grid):
+        set_distance_field(self.ctx, grid)
+
+    def smpc_iterate(self, *a, **kw):
+        smpc_iterate(self.ctx, *a, **kw)
+
+    def replan(self, *a, **kw):
+        replan(self.ctx, *a, **kw)
+
+    def rollout_trace(self, *a, **kw):
+        rollout_trace(self.ctx, *a, **kw)
+
+    def profile_enable(self, enable=True):
+        profile_enable(self.ctx, enable)
+
+    def profile_read(self, reset=True):
+        return profile_read(self.ctx, reset)
+
+    def close(self):
+        if self.ctx is not None:
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+lib()  # load now: a missing or unbuilt library is an import error, never a fallback

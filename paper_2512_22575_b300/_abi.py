@@ -1,0 +1,82 @@
+"""ctypes declarations of include/paramap.h (loading only; no compute)."""
+import ctypes as C
+import os
+
+PM_F32, PM_F16, PM_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_EBUSY", 4: "PM_ETIMEOUT",
+                5: "PM_ECUDA", 6: "PM_ENOTREADY", 7: "PM_EINTERNAL"}
+
+_PF = C.POINTER(C.c_float)
+_PI = C.POINTER(C.c_int)
+_V = C.c_void_p
+
+
+class PmError(RuntimeError):
+    def __init__(self, status, name, message):
+        super().__init__(f"{name}: {message}")
+        self.status = status
+        self.name = name
+
+
+class PmRobot(C.Structure):
+    _fields_ = [("n_joints", C.c_int), ("a", _PF), ("d", _PF), ("alpha", _PF),
+                ("theta_offset", _PF), ("flange_d", C.c_float), ("q_min", _PF), ("q_max", _PF),
+                ("qd_max", _PF), ("qdd_max", _PF), ("n_spheres", C.c_int), ("sphere_link", _PI),
+                ("sphere_offset", _PF), ("sphere_radius", _PF), ("n_self_pairs", C.c_int),
+                ("self_pairs", _PI)]
+
+
+class PmGridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("res", C.c_float),
+                ("origin", C.c_float * 3), ("dtype", C.c_int)]
+
+
+class PmCostParams(C.Structure):
+    _fields_ = [("Q", C.c_float * 6), ("QH", C.c_float * 6), ("w_env", C.c_float),
+                ("d_act", C.c_float), ("w_self", C.c_float), ("w_q", C.c_float),
+                ("w_qd", C.c_float), ("w_qdd", C.c_float), ("margin_frac", C.c_float),
+                ("w_s", C.c_float), ("w_ns", C.c_float), ("q_ref", _PF)]
+
+
+# Every exported entry point of include/paramap.h with its ctypes signature.
+SIGNATURES = {
+    "pm_create": (C.c_int, [C.POINTER(PmRobot), C.POINTER(PmGridDesc), C.POINTER(PmCostParams),
+                            C.c_int, C.POINTER(C.c_void_p)]),
+    "pm_set_distance_field": (C.c_int, [_V, _V, C.c_int]),
+    "pm_smpc_iterate": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_float, C.c_float, _V,
+                                  C.c_uint64, C.c_uint32, _V, _V]),
+    "pm_replan": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
+                            _V, C.c_uint64, C.c_uint32, _V, _V, _V]),
+    "pm_philox4x32_10": (C.c_int, [_V, C.c_uint64, _V, C.c_size_t, _V]),
+    "pm_sample_noise": (C.c_int, [C.c_int, C.c_int, _V, C.c_uint64, C.c_uint32, _V, _V]),
+    "pm_rollout_trace": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_float, _V,
+                                   C.c_uint64, C.c_uint32, _V]),
+    "pm_profile_enable": (C.c_int, [_V, C.c_int]),
+    "pm_profile_read": (C.c_int, [_V, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
+    "pm_destroy": (None, [_V]),
+    "pm_last_error": (C.c_char_p, [_V]),
+    "pm_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libparamap.so")
+
+
+def lib():
+    """Load libparamap.so (built in-tree by paper_2512_22575_b300.build)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "`python paper_2512_22575_b300/build.py`")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib

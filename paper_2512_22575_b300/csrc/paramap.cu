@@ -1,0 +1,741 @@
+// C ABI of the SMPC hot path (include/paramap.h): contexts, argument checks,
+// host<->device staging and kernel dispatch.  The arithmetic lives in
+// smpc_device.cuh / smpc_kernels.cuh.
+#include "paramap.h"
+#include "smpc_dispatch.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using namespace pm;
+
+struct pm_ctx {
+    int device = 0;
+    int n_sm = 0;
+    RobotConst rc{};
+    pm_grid_desc gd{};
+    size_t grid_elems = 0;
+    void *d_grid = nullptr;
+    bool has_grid = false;
+    cudaStream_t stream = nullptr;
+    // Ring of staging slots for host inputs: slot i holds q0 [0..7], qd0
+    // [8..15] and T_goal [16..31]; its event marks the copy as done so the
+    // pinned slot can be reused.
+    float *d_stage = nullptr;
+    float *h_stage = nullptr;           // pinned
+    cudaEvent_t slot_ev[16] = {};
+    bool slot_pending[16] = {};
+    int slot = 0;
+    float *d_U = nullptr;
+    size_t cap_U = 0;
+    float *h_U = nullptr;               // pinned [PM_MAX_HORIZON * 8]
+    float *d_costs = nullptr;
+    size_t cap_costs = 0;
+    float *h_out = nullptr;             // pinned: costs / small outputs
+    size_t cap_h_out = 0;
+    float *d_part = nullptr;
+    size_t cap_part = 0;
+    unsigned *d_counter = nullptr;
+    float *d_c0 = nullptr;              // [c0, best, q(8), qd(8), u0(8)]
+    bool prof = false;                  // bracket iteration kernels with events
+    std::vector<cudaEvent_t> prof_ev;   // pairs (start, end)
+    size_t prof_used = 0;               // events recorded since the last reset
+    cudaStream_t prof_stream = nullptr;
+    std::string err;
+    std::mutex mu;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+const char *kVersion = "paramap-b300 0.1 (sm_103a)";
+
+pm_status set_err(pm_ctx *ctx, pm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf; else g_err = buf;
+    return st;
+}
+
+#define PM_CUDA(ctx, call)                                                                \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_err((ctx), e_ == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, \
+                           "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                           __LINE__);                                                     \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_all(const float *p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+TileShape pick_shape(int H)
+{
+    for (const TileShape &s : kShapes)
+        if (s.C * s.L >= H) return s;
+    return kShapes[sizeof(kShapes) / sizeof(kShapes[0]) - 1];
+}
+
+IterKernel lookup_kernel(int dtype, TileShape s, bool trace)
+{
+    switch (dtype) {
+    case PM_F32: return iteration_kernel_f32(s.C, s.L, trace);
+    case PM_F16: return iteration_kernel_f16(s.C, s.L, trace);
+    case PM_BF16: return iteration_kernel_bf16(s.C, s.L, trace);
+    default: return nullptr;
+    }
+}
+
+int resident_blocks_per_sm(IterKernel fn)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(reinterpret_cast<const void *>(fn));
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    n = std::max(n, 1);
+    cache[reinterpret_cast<const void *>(fn)] = n;
+    return n;
+}
+
+size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------ small kernels
+__global__ void convert_grid_kernel(const float *src, void *dst, size_t n, int dtype)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        if (dtype == PM_F16) static_cast<__half *>(dst)[i] = __float2half_rn(src[i]);
+        else static_cast<__nv_bfloat16 *>(dst)[i] = __float2bfloat16_rn(src[i]);
+    }
+}
+
+__global__ void philox_words_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                                    size_t n)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        uint32_t x0 = ctr[4 * i], x1 = ctr[4 * i + 1], x2 = ctr[4 * i + 2], x3 = ctr[4 * i + 3];
+        philox4x32_10(x0, x1, x2, x3, k0, k1);
+        out[4 * i] = x0; out[4 * i + 1] = x1; out[4 * i + 2] = x2; out[4 * i + 3] = x3;
+    }
+}
+
+struct Sigma { float s[8]; };
+
+__global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint32_t s_hi,
+                                    uint32_t iter, float *eps)
+{
+    const size_t total = static_cast<size_t>(K) * H;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const uint32_t m = static_cast<uint32_t>(i / H), k = static_cast<uint32_t>(i % H);
+        float z[8];
+        step_normals(s_lo, s_hi, iter, m, k, z);
+        for (int j = 0; j < kNJ; ++j) eps[i * kNJ + j] = sg.s[j] * z[j];
+    }
+}
+
+// Receding-horizon step (Sec. IV-C): execute u0* for one integrator step and
+// shift U one step left, repeating the last row.  One block.
+__global__ void replan_advance_kernel(const float *q0, const float *qd0, float *U, int H, float dt,
+                                      float *q_out, float *qd_out, float *u0_out, const float *c0,
+                                      float *best_out)
+{
+    __shared__ float sU[kMaxHorizon * kNJ];
+    const int n = H * kNJ;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sU[i] = U[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) U[i] = (i < n - kNJ) ? sU[i + kNJ] : sU[i];
+    if (threadIdx.x < kNJ) {
+        const int j = threadIdx.x;
+        const float u0 = sU[j];
+        const float qd = fmaf(dt, u0, qd0[j]);
+        const float q = fmaf(dt, qd, q0[j]);
+        q_out[j] = q;
+        qd_out[j] = qd;
+        if (u0_out) u0_out[j] = u0;
+    }
+    if (threadIdx.x == 0 && best_out) *best_out = c0[1];
+}
+
+// ------------------------------------------------------------ helpers
+pm_status ensure_capacity(pm_ctx *c, int K, int H, int nb)
+{
+    const size_t needU = static_cast<size_t>(kMaxHorizon) * kNJ;
+    if (!c->d_U) {
+        PM_CUDA(c, cudaMalloc(&c->d_U, needU * sizeof(float)));
+        c->cap_U = needU;
+    }
+    if (static_cast<size_t>(K) > c->cap_costs) {
+        size_t cap = std::max<size_t>(K, 4096);
+        if (c->d_costs) cudaFree(c->d_costs);
+        c->d_costs = nullptr;
+        c->cap_costs = 0;
+        PM_CUDA(c, cudaMalloc(&c->d_costs, cap * sizeof(float)));
+        c->cap_costs = cap;
+    }
+    if (static_cast<size_t>(K) > c->cap_h_out) {
+        size_t cap = std::max<size_t>(K, 4096);
+        if (c->h_out) cudaFreeHost(c->h_out);
+        c->h_out = nullptr;
+        c->cap_h_out = 0;
+        PM_CUDA(c, cudaMallocHost(&c->h_out, cap * sizeof(float)));
+        c->cap_h_out = cap;
+    }
+    const size_t needP = static_cast<size_t>(nb) * (2 + static_cast<size_t>(H) * kNJ);
+    if (needP > c->cap_part) {
+        size_t cap = std::max(needP, static_cast<size_t>(kMaxBlocks) * (2 + 64 * kNJ));
+        if (c->d_part) cudaFree(c->d_part);
+        c->d_part = nullptr;
+        c->cap_part = 0;
+        PM_CUDA(c, cudaMalloc(&c->d_part, cap * sizeof(float)));
+        c->cap_part = cap;
+    }
+    return PM_OK;
+}
+
+GridConst grid_const(const pm_ctx *c)
+{
+    GridConst g;
+    g.phi = c->d_grid;
+    g.nx = c->gd.nx; g.ny = c->gd.ny; g.nz = c->gd.nz;
+    g.inv_res = 1.0f / c->gd.res;
+    g.ox = c->gd.origin[0]; g.oy = c->gd.origin[1]; g.oz = c->gd.origin[2];
+    g.mx = static_cast<float>(c->gd.nx - 1);
+    g.my = static_cast<float>(c->gd.ny - 1);
+    g.mz = static_cast<float>(c->gd.nz - 1);
+    return g;
+}
+
+// Validate the per-call arguments shared by iterate / replan / trace.
+pm_status check_call(pm_ctx *c, const float *q0, const float *qd0, const float *T_goal,
+                     const float *U, int K, int H, float dt, float lambda, const float *sigma,
+                     bool need_lambda)
+{
+    if (!c->has_grid) return set_err(c, PM_EINVAL, "no distance field set (pm_set_distance_field)");
+    if (!q0 || !qd0 || !T_goal || !U || !sigma) return set_err(c, PM_EINVAL, "NULL argument");
+    if (K < 1 || K > PM_MAX_ROLLOUTS) return set_err(c, PM_EINVAL, "K=%d out of [1, %d]", K, PM_MAX_ROLLOUTS);
+    if (H < 1 || H > PM_MAX_HORIZON) return set_err(c, PM_EINVAL, "H=%d out of [1, %d]", H, PM_MAX_HORIZON);
+    if (!std::isfinite(dt) || dt < 0.f) return set_err(c, PM_EINVAL, "dt must be finite and >= 0");
+    if (need_lambda && (!std::isfinite(lambda) || !(lambda > 0.f)))
+        return set_err(c, PM_EINVAL, "lambda must be finite and > 0");
+    if (is_device_ptr(sigma)) return set_err(c, PM_EINVAL, "sigma must be host memory");
+    if (!finite_all(sigma, kNJ)) return set_err(c, PM_EINVAL, "sigma has a non-finite entry");
+    for (int j = 0; j < kNJ; ++j)
+        if (sigma[j] < 0.f) return set_err(c, PM_EINVAL, "sigma must be >= 0");
+    if (!is_device_ptr(q0) && !finite_all(q0, kNJ)) return set_err(c, PM_EINVAL, "q0 has a non-finite entry");
+    if (!is_device_ptr(qd0) && !finite_all(qd0, kNJ)) return set_err(c, PM_EINVAL, "qd0 has a non-finite entry");
+    if (!is_device_ptr(T_goal) && !finite_all(T_goal, 12)) return set_err(c, PM_EINVAL, "T_goal has a non-finite entry");
+    return PM_OK;
+}
+
+constexpr int kSlots = 16;
+constexpr int kSlotFloats = 32;
+
+// Resolve q0, qd0, T_goal into device pointers: device inputs are used in
+// place, host inputs are copied through the next pinned staging slot.
+pm_status stage_inputs(pm_ctx *c, cudaStream_t s, const float *q0, const float *qd0,
+                       const float *T_goal, const float *sigma, CallInputs &in)
+{
+    const int k = c->slot;
+    c->slot = (c->slot + 1) % kSlots;
+    if (c->slot_pending[k]) {
+        PM_CUDA(c, cudaEventSynchronize(c->slot_ev[k]));
+        c->slot_pending[k] = false;
+    }
+    float *h = c->h_stage + k * kSlotFloats;
+    float *d = c->d_stage + k * kSlotFloats;
+    bool any_host = false;
+    auto place = [&](const float *src, int n, int off) -> const float * {
+        if (is_device_ptr(src)) return src;
+        std::memcpy(h + off, src, n * sizeof(float));
+        any_host = true;
+        return d + off;
+    };
+    in.q0 = place(q0, kNJ, 0);
+    in.qd0 = place(qd0, kNJ, 8);
+    in.Tg = place(T_goal, 16, 16);
+    for (int j = 0; j < 8; ++j) in.sigma[j] = j < kNJ ? sigma[j] : 0.f;
+    if (any_host) {
+        PM_CUDA(c, cudaMemcpyAsync(d, h, kSlotFloats * sizeof(float), cudaMemcpyHostToDevice, s));
+        PM_CUDA(c, cudaEventRecord(c->slot_ev[k], s));
+        c->slot_pending[k] = true;
+    }
+    return PM_OK;
+}
+
+// Enqueue one iteration kernel.  Ubar/Uout device [H][7]; costs device or null.
+pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, const float *Ubar,
+                           float *Uout, float *costs, int K, int H, float dt, float lambda,
+                           uint64_t seed, uint32_t iter, bool trace, float *trace_out)
+{
+    const TileShape sh = pick_shape(H);
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace);
+    if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d", sh.C, sh.L);
+    const int R = 32 / sh.L;
+    const long long tiles = (static_cast<long long>(K) + R - 1) / R;
+    const long long need = (tiles + kWarps - 1) / kWarps;
+    const long long resident = static_cast<long long>(c->n_sm) * resident_blocks_per_sm(fn);
+    const int nb = static_cast<int>(std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)})));
+    pm_status st = ensure_capacity(c, K, H, nb);
+    if (st != PM_OK) return st;
+    IterArgs a{};
+    a.in = in;
+    a.Ubar = Ubar;
+    a.Uout = Uout;
+    a.costs = costs;
+    a.part = c->d_part;
+    a.counter = c->d_counter;
+    a.c0 = c->d_c0;
+    a.trace = trace_out;
+    a.K = K;
+    a.H = H;
+    a.seed_lo = static_cast<uint32_t>(seed & 0xffffffffu);
+    a.seed_hi = static_cast<uint32_t>(seed >> 32);
+    a.iter = iter;
+    a.dt = dt;
+    a.inv_lambda = trace ? 1.0f : 1.0f / lambda;
+    const bool prof = c->prof && !trace;
+    if (prof) {
+        while (c->prof_ev.size() < c->prof_used + 2) {
+            cudaEvent_t e;
+            PM_CUDA(c, cudaEventCreate(&e));
+            c->prof_ev.push_back(e);
+        }
+        PM_CUDA(c, cudaEventRecord(c->prof_ev[c->prof_used], s));
+    }
+    fn<<<nb, kBlock, 0, s>>>(c->rc, grid_const(c), a);
+    PM_CUDA(c, cudaGetLastError());
+    if (prof) {
+        PM_CUDA(c, cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
+        c->prof_used += 2;
+        c->prof_stream = s;
+    }
+    return PM_OK;
+}
+
+cudaStream_t pick_stream(pm_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+} // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+const char *pm_version(void) { return kVersion; }
+
+const char *pm_last_error(pm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_params *cp,
+                    int device, pm_ctx **out)
+{
+    if (!out) return set_err(nullptr, PM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!rb || !gd || !cp) return set_err(nullptr, PM_EINVAL, "NULL robot, grid or costs");
+    if (rb->n_joints != kNJ)
+        return set_err(nullptr, PM_EINVAL, "n_joints=%d: this build compiles a %d-joint chain", rb->n_joints, kNJ);
+    const int n = rb->n_joints;
+    if (!rb->a || !rb->d || !rb->alpha || !rb->theta_offset || !rb->q_min || !rb->q_max ||
+        !rb->qd_max || !rb->qdd_max)
+        return set_err(nullptr, PM_EINVAL, "NULL robot array");
+    if (!finite_all(rb->a, n) || !finite_all(rb->d, n) || !finite_all(rb->alpha, n) ||
+        !finite_all(rb->theta_offset, n) || !std::isfinite(rb->flange_d) ||
+        !finite_all(rb->q_min, n) || !finite_all(rb->q_max, n) || !finite_all(rb->qd_max, n) ||
+        !finite_all(rb->qdd_max, n))
+        return set_err(nullptr, PM_EINVAL, "non-finite robot parameter");
+    for (int j = 0; j < n; ++j) {
+        if (!(rb->q_min[j] < rb->q_max[j])) return set_err(nullptr, PM_EINVAL, "q_min >= q_max at joint %d", j);
+        if (!(rb->qd_max[j] > 0.f) || !(rb->qdd_max[j] > 0.f))
+            return set_err(nullptr, PM_EINVAL, "qd_max/qdd_max must be > 0 at joint %d", j);
+    }
+    if (rb->n_spheres < 0 || rb->n_spheres > PM_MAX_SPHERES)
+        return set_err(nullptr, PM_EINVAL, "n_spheres=%d out of [0, %d]", rb->n_spheres, PM_MAX_SPHERES);
+    if (rb->n_spheres > 0 && (!rb->sphere_link || !rb->sphere_offset || !rb->sphere_radius))
+        return set_err(nullptr, PM_EINVAL, "NULL sphere array");
+    for (int s = 0; s < rb->n_spheres; ++s) {
+        if (rb->sphere_link[s] < 1 || rb->sphere_link[s] > n)
+            return set_err(nullptr, PM_EINVAL, "sphere_link[%d]=%d out of [1, %d]", s, rb->sphere_link[s], n);
+        if (!finite_all(rb->sphere_offset + 3 * s, 3) || !std::isfinite(rb->sphere_radius[s]) ||
+            rb->sphere_radius[s] < 0.f)
+            return set_err(nullptr, PM_EINVAL, "bad sphere %d", s);
+    }
+    if (rb->n_self_pairs < 0) return set_err(nullptr, PM_EINVAL, "n_self_pairs < 0");
+    if (rb->n_self_pairs > 0 && cp->w_self != 0.f)
+        return set_err(nullptr, PM_EINVAL, "the self-collision term (w_self > 0 with pairs) is not built yet");
+    if (gd->nx < 2 || gd->ny < 2 || gd->nz < 2)
+        return set_err(nullptr, PM_EINVAL, "grid needs >= 2 voxels per axis");
+    const size_t elems = static_cast<size_t>(gd->nx) * gd->ny * gd->nz;
+    if (elems >= (1ull << 31) - 2ull * gd->nx * gd->ny)
+        return set_err(nullptr, PM_EINVAL, "grid too large for 32-bit voxel indexing");
+    if (!std::isfinite(gd->res) || !(gd->res > 0.f) || !finite_all(gd->origin, 3))
+        return set_err(nullptr, PM_EINVAL, "grid res/origin invalid");
+    if (gd->dtype != PM_F32 && gd->dtype != PM_F16 && gd->dtype != PM_BF16)
+        return set_err(nullptr, PM_EINVAL, "grid dtype %d unknown", gd->dtype);
+    if (!cp->q_ref || !finite_all(cp->q_ref, n) || !finite_all(cp->Q, 6) || !finite_all(cp->QH, 6))
+        return set_err(nullptr, PM_EINVAL, "cost params Q/QH/q_ref invalid");
+    const float ws[] = {cp->w_env, cp->d_act, cp->w_self, cp->w_q, cp->w_qd, cp->w_qdd,
+                        cp->margin_frac, cp->w_s, cp->w_ns};
+    for (float w : ws)
+        if (!std::isfinite(w) || w < 0.f) return set_err(nullptr, PM_EINVAL, "cost weights must be finite and >= 0");
+    if (!(cp->margin_frac < 0.5f)) return set_err(nullptr, PM_EINVAL, "margin_frac must be < 0.5");
+
+    pm_ctx *c = new pm_ctx();
+    c->device = device;
+    c->gd = *gd;
+    c->grid_elems = elems;
+    RobotConst &r = c->rc;
+    std::memset(&r, 0, sizeof(r));
+    // spheres ordered by link (stable); the cost sums over spheres
+    std::vector<int> order(rb->n_spheres);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return rb->sphere_link[x] < rb->sphere_link[y]; });
+    r.n_spheres = rb->n_spheres;
+    for (int i = 0; i <= n + 1; ++i) r.link_begin[i] = 0;
+    for (int i = 0; i < rb->n_spheres; ++i) {
+        const int s = order[i];
+        for (int k = 0; k < 3; ++k) r.sph_off[i][k] = rb->sphere_offset[3 * s + k];
+        r.sph_r[i] = rb->sphere_radius[s];
+    }
+    for (int L = 1; L <= n + 1; ++L) {
+        int cnt = 0;
+        for (int s = 0; s < rb->n_spheres; ++s) cnt += (rb->sphere_link[s] < L);
+        r.link_begin[L] = cnt;
+    }
+    for (int j = 0; j < n; ++j) {
+        r.ca[j] = static_cast<float>(std::cos(static_cast<double>(rb->alpha[j])));
+        r.sa[j] = static_cast<float>(std::sin(static_cast<double>(rb->alpha[j])));
+        r.a[j] = rb->a[j];
+        r.d[j] = rb->d[j];
+        r.th0[j] = rb->theta_offset[j];
+        const double mf = cp->margin_frac;
+        const double lo = rb->q_min[j], hi = rb->q_max[j];
+        r.q_lo[j] = static_cast<float>(lo + mf * (hi - lo));
+        r.q_hi[j] = static_cast<float>(hi - mf * (hi - lo));
+        const double v = rb->qd_max[j], acc = rb->qdd_max[j];
+        r.qd_lo[j] = static_cast<float>(-v + mf * 2.0 * v);
+        r.qd_hi[j] = static_cast<float>(v - mf * 2.0 * v);
+        r.qdd_lo[j] = static_cast<float>(-acc + mf * 2.0 * acc);
+        r.qdd_hi[j] = static_cast<float>(acc - mf * 2.0 * acc);
+        r.q_ref[j] = cp->q_ref[j];
+    }
+    r.flange_d = rb->flange_d;
+    for (int i = 0; i < 6; ++i) { r.Q[i] = cp->Q[i]; r.QH[i] = cp->QH[i]; }
+    r.w_env = cp->w_env; r.d_act = cp->d_act; r.w_self = cp->w_self;
+    r.w_q = cp->w_q; r.w_qd = cp->w_qd; r.w_qdd = cp->w_qdd;
+    r.w_s = cp->w_s; r.w_ns = cp->w_ns;
+
+    auto fail = [&](pm_status st) {
+        g_err = c->err;
+        pm_destroy(c);
+        return st;
+    };
+    DeviceGuard dg(device);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        set_err(c, PM_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+        return fail(PM_ECUDA);
+    }
+    auto ck = [&](cudaError_t e2, const char *what) -> bool {
+        if (e2 == cudaSuccess) return true;
+        set_err(c, e2 == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, "%s: %s", what, cudaGetErrorString(e2));
+        return false;
+    };
+    if (!ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device), "SM count") ||
+        !ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream") ||
+        !ck(cudaMalloc(&c->d_grid, elems * dtype_size(gd->dtype)), "grid alloc") ||
+        !ck(cudaMalloc(&c->d_stage, sizeof(float) * kSlots * kSlotFloats), "staging alloc") ||
+        !ck(cudaMallocHost(&c->h_stage, sizeof(float) * kSlots * kSlotFloats), "pinned staging alloc") ||
+        !ck(cudaMallocHost(&c->h_U, sizeof(float) * kMaxHorizon * kNJ), "pinned U") ||
+        !ck(cudaMalloc(&c->d_counter, sizeof(unsigned)), "counter") ||
+        !ck(cudaMemset(c->d_counter, 0, sizeof(unsigned)), "counter zero") ||
+        !ck(cudaMalloc(&c->d_c0, 32 * sizeof(float)), "c0") ||
+        !ck(cudaMemset(c->d_c0, 0, 32 * sizeof(float)), "c0 zero"))
+        return fail(c->err.find("alloc") != std::string::npos ? PM_ENOMEM : PM_ECUDA);
+    for (int k = 0; k < kSlots; ++k)
+        if (!ck(cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming), "event"))
+            return fail(PM_ECUDA);
+    *out = c;
+    return PM_OK;
+}
+
+pm_status pm_set_distance_field(pm_ctx *c, const float *grid, int grid_is_device)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    if (!grid) return set_err(c, PM_EINVAL, "grid is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    if (!grid_is_device) {
+        for (size_t i = 0; i < c->grid_elems; ++i)
+            if (!std::isfinite(grid[i])) return set_err(c, PM_EINVAL, "grid value %zu is not finite", i);
+    }
+    const cudaMemcpyKind kind = grid_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->gd.dtype == PM_F32) {
+        PM_CUDA(c, cudaMemcpyAsync(c->d_grid, grid, c->grid_elems * sizeof(float), kind, c->stream));
+    } else {
+        float *tmp = nullptr;
+        PM_CUDA(c, cudaMalloc(&tmp, c->grid_elems * sizeof(float)));
+        cudaError_t e = cudaMemcpyAsync(tmp, grid, c->grid_elems * sizeof(float), kind, c->stream);
+        if (e == cudaSuccess) {
+            convert_grid_kernel<<<4 * c->n_sm, 256, 0, c->stream>>>(tmp, c->d_grid, c->grid_elems, c->gd.dtype);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        PM_CUDA(c, e);
+    }
+    PM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_grid = true;
+    return PM_OK;
+}
+
+pm_status pm_smpc_iterate(pm_ctx *c, const float *q0, const float *qd0, const float *T_goal,
+                          float *U, int K, int H, float dt, float lambda, const float *sigma,
+                          uint64_t seed, uint32_t iter_index, float *costs_out, void *cuda_stream)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    pm_status st = check_call(c, q0, qd0, T_goal, U, K, H, dt, lambda, sigma, true);
+    if (st != PM_OK) return st;
+    const bool dU = is_device_ptr(U);
+    if (!dU && !finite_all(U, H * kNJ)) return set_err(c, PM_EINVAL, "U has a non-finite entry");
+    const bool dC = costs_out && is_device_ptr(costs_out);
+    cudaStream_t s = pick_stream(c, cuda_stream);
+    st = ensure_capacity(c, K, H, 1);
+    if (st != PM_OK) return st;
+    CallInputs in{};
+    st = stage_inputs(c, s, q0, qd0, T_goal, sigma, in);
+    if (st != PM_OK) return st;
+    float *Ud = U;
+    if (!dU) {
+        std::memcpy(c->h_U, U, sizeof(float) * H * kNJ);
+        PM_CUDA(c, cudaMemcpyAsync(c->d_U, c->h_U, sizeof(float) * H * kNJ, cudaMemcpyHostToDevice, s));
+        Ud = c->d_U;
+    }
+    float *Cd = costs_out ? (dC ? costs_out : c->d_costs) : nullptr;
+    st = launch_iteration(c, s, in, Ud, Ud, Cd, K, H, dt, lambda, seed, iter_index, false, nullptr);
+    if (st != PM_OK) return st;
+    if (!dU) PM_CUDA(c, cudaMemcpyAsync(c->h_U, c->d_U, sizeof(float) * H * kNJ, cudaMemcpyDeviceToHost, s));
+    if (costs_out && !dC)
+        PM_CUDA(c, cudaMemcpyAsync(c->h_out, c->d_costs, sizeof(float) * K, cudaMemcpyDeviceToHost, s));
+    if (!dU || (costs_out && !dC)) {
+        PM_CUDA(c, cudaStreamSynchronize(s));
+        if (!dU) std::memcpy(U, c->h_U, sizeof(float) * H * kNJ);
+        if (costs_out && !dC) std::memcpy(costs_out, c->h_out, sizeof(float) * K);
+    }
+    return PM_OK;
+}
+
+pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *U, int K, int H,
+                    int n_iters, float dt, float lambda, const float *sigma, uint64_t seed,
+                    uint32_t replan_index, float *u0_out, float *best_cost, void *cuda_stream)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    pm_status st = check_call(c, q, qd, T_goal, U, K, H, dt, lambda, sigma, true);
+    if (st != PM_OK) return st;
+    if (n_iters < 1 || n_iters > 1024) return set_err(c, PM_EINVAL, "n_iters=%d out of [1, 1024]", n_iters);
+    const bool dU = is_device_ptr(U);
+    if (!dU && !finite_all(U, H * kNJ)) return set_err(c, PM_EINVAL, "U has a non-finite entry");
+    const bool dq = is_device_ptr(q), dqd = is_device_ptr(qd);
+    const bool du0 = u0_out && is_device_ptr(u0_out), dbest = best_cost && is_device_ptr(best_cost);
+    cudaStream_t s = pick_stream(c, cuda_stream);
+    st = ensure_capacity(c, K, H, 1);
+    if (st != PM_OK) return st;
+    CallInputs in{};
+    st = stage_inputs(c, s, q, qd, T_goal, sigma, in);
+    if (st != PM_OK) return st;
+    float *Ud = U;
+    if (!dU) {
+        std::memcpy(c->h_U, U, sizeof(float) * H * kNJ);
+        PM_CUDA(c, cudaMemcpyAsync(c->d_U, c->h_U, sizeof(float) * H * kNJ, cudaMemcpyHostToDevice, s));
+        Ud = c->d_U;
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        st = launch_iteration(c, s, in, Ud, Ud, nullptr, K, H, dt, lambda, seed,
+                              replan_index * static_cast<uint32_t>(n_iters) + static_cast<uint32_t>(it),
+                              false, nullptr);
+        if (st != PM_OK) return st;
+    }
+    float *small = c->d_c0 + 8;  // [q 8][qd 8][u0 8] device scratch
+    replan_advance_kernel<<<1, 256, 0, s>>>(in.q0, in.qd0, Ud, H, dt, dq ? q : small, dqd ? qd : small + 8,
+                                            u0_out ? (du0 ? u0_out : small + 16) : nullptr, c->d_c0,
+                                            best_cost ? (dbest ? best_cost : c->d_c0 + 2) : nullptr);
+    PM_CUDA(c, cudaGetLastError());
+    const bool host_out = !dU || !dq || !dqd || (u0_out && !du0) || (best_cost && !dbest);
+    if (host_out) {
+        float *h = c->h_out;  // >= 4096 floats
+        PM_CUDA(c, cudaMemcpyAsync(h, small, 24 * sizeof(float), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(c, cudaMemcpyAsync(h + 24, c->d_c0 + 2, sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (!dU) PM_CUDA(c, cudaMemcpyAsync(c->h_U, c->d_U, sizeof(float) * H * kNJ, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(c, cudaStreamSynchronize(s));
+        if (!dq) std::memcpy(q, h, kNJ * sizeof(float));
+        if (!dqd) std::memcpy(qd, h + 8, kNJ * sizeof(float));
+        if (u0_out && !du0) std::memcpy(u0_out, h + 16, kNJ * sizeof(float));
+        if (best_cost && !dbest) *best_cost = h[24];
+        if (!dU) std::memcpy(U, c->h_U, sizeof(float) * H * kNJ);
+    }
+    return PM_OK;
+}
+
+pm_status pm_rollout_trace(pm_ctx *c, const float *q0, const float *qd0, const float *T_goal,
+                           const float *U, int K, int H, float dt, const float *sigma,
+                           uint64_t seed, uint32_t iter_index, float *trace)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    pm_status st = check_call(c, q0, qd0, T_goal, U, K, H, dt, 1.0f, sigma, false);
+    if (st != PM_OK) return st;
+    if (!trace || !is_device_ptr(trace)) return set_err(c, PM_EINVAL, "trace must be device memory");
+    cudaStream_t s = c->stream;
+    st = ensure_capacity(c, K, H, 1);
+    if (st != PM_OK) return st;
+    CallInputs in{};
+    st = stage_inputs(c, s, q0, qd0, T_goal, sigma, in);
+    if (st != PM_OK) return st;
+    const float *Ud = U;
+    if (!is_device_ptr(U)) {
+        std::memcpy(c->h_U, U, sizeof(float) * H * kNJ);
+        PM_CUDA(c, cudaMemcpyAsync(c->d_U, c->h_U, sizeof(float) * H * kNJ, cudaMemcpyHostToDevice, s));
+        Ud = c->d_U;
+    }
+    PM_CUDA(c, cudaMemsetAsync(trace, 0, sizeof(float) * static_cast<size_t>(K) * (H + 1) * kTraceCols, s));
+    st = launch_iteration(c, s, in, Ud, nullptr, nullptr, K, H, dt, 1.0f, seed, iter_index, true, trace);
+    if (st != PM_OK) return st;
+    PM_CUDA(c, cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, size_t n, void *cuda_stream)
+{
+    if (!ctr || !out) return set_err(nullptr, PM_EINVAL, "NULL argument");
+    if (n == 0) return PM_OK;
+    if (!is_device_ptr(ctr) || !is_device_ptr(out)) return set_err(nullptr, PM_EINVAL, "ctr/out must be device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((n + 255) / 256, 65535));
+    philox_words_kernel<<<blocks, 256, 0, s>>>(ctr, static_cast<uint32_t>(key & 0xffffffffu),
+                                               static_cast<uint32_t>(key >> 32), out, n);
+    PM_CUDA(nullptr, cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed, uint32_t iter_index,
+                          float *eps, void *cuda_stream)
+{
+    if (!sigma || !eps) return set_err(nullptr, PM_EINVAL, "NULL argument");
+    if (K < 1 || H < 1 || K > PM_MAX_ROLLOUTS || H > PM_MAX_HORIZON) return set_err(nullptr, PM_EINVAL, "K/H out of range");
+    if (!is_device_ptr(eps)) return set_err(nullptr, PM_EINVAL, "eps must be device memory");
+    if (is_device_ptr(sigma) || !finite_all(sigma, kNJ)) return set_err(nullptr, PM_EINVAL, "sigma must be finite host memory");
+    Sigma sg{};
+    for (int j = 0; j < kNJ; ++j) sg.s[j] = sigma[j];
+    const size_t total = static_cast<size_t>(K) * H;
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((total + 255) / 256, 65535));
+    sample_noise_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        K, H, sg, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), iter_index, eps);
+    PM_CUDA(nullptr, cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_profile_enable(pm_ctx *c, int enable)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->prof = enable != 0;
+    return PM_OK;
+}
+
+pm_status pm_profile_read(pm_ctx *c, double *total_ms, uint64_t *launches, int reset)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    if (!total_ms || !launches) return set_err(c, PM_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+        PM_CUDA(c, cudaEventSynchronize(c->prof_ev[i + 1]));
+        float ms = 0.f;
+        PM_CUDA(c, cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = c->prof_used / 2;
+    if (reset) c->prof_used = 0;
+    return PM_OK;
+}
+
+void pm_destroy(pm_ctx *c)
+{
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_grid);
+        cudaFree(c->d_stage);
+        cudaFreeHost(c->h_stage);
+        cudaFreeHost(c->h_U);
+        cudaFree(c->d_U);
+        cudaFree(c->d_costs);
+        cudaFreeHost(c->h_out);
+        cudaFree(c->d_part);
+        cudaFree(c->d_counter);
+        cudaFree(c->d_c0);
+        for (cudaEvent_t e : c->slot_ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+        if (c->stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+} // extern "C"

@@ -1,0 +1,325 @@
+// Device arithmetic of one SMPC iteration (ParaMaP, arXiv 2512.22575, Sec. IV).
+//
+// Everything here is FP32 except the integer Philox generator.  The pieces:
+//   - Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals (Eq. 19);
+//   - modified-DH forward kinematics kept as three rotation columns and a
+//     translation, updated joint by joint (Eq. 1);
+//   - trilinear lookup of the distance field phi (Eq. 14);
+//   - the SE(3) pose error xi = log(T_g^{-1} T_ee) (Eqs. 8-12) with the
+//     closed form V(theta)^{-1} = I - [w]x/2 + c(theta) [w]x^2,
+//     c(theta) = (1 - (theta/2) cot(theta/2)) / theta^2;
+//   - the tightened joint-limit violation of Eq. 17.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace pm {
+
+constexpr int kNJ = 7;            // joints of the compiled kinematic chain
+constexpr int kMaxSpheres = 64;
+constexpr int kMaxHorizon = 256;
+
+// Arm + cost constants, passed by value as a kernel parameter (constant bank).
+struct RobotConst {
+    int n_spheres;
+    int link_begin[kNJ + 2];      // spheres of frame i (1..n) are [link_begin[i], link_begin[i+1])
+    float ca[kNJ], sa[kNJ];       // cos/sin of alpha_{i-1}
+    float a[kNJ], d[kNJ], th0[kNJ];
+    float flange_d;
+    float q_lo[kNJ], q_hi[kNJ];   // tightened boxes of Eq. 17
+    float qd_lo[kNJ], qd_hi[kNJ];
+    float qdd_lo[kNJ], qdd_hi[kNJ];
+    float sph_off[kMaxSpheres][3];
+    float sph_r[kMaxSpheres];
+    float Q[6], QH[6];
+    float w_env, d_act, w_self;
+    float w_q, w_qd, w_qdd, w_s, w_ns;
+    float q_ref[kNJ];
+};
+
+struct GridConst {
+    const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16
+    int nx, ny, nz;
+    float inv_res;
+    float ox, oy, oz;             // origin
+    float mx, my, mz;             // n - 1 (clamp bound)
+};
+
+// Per-call state as each block holds it in shared memory.
+struct InstanceState {
+    float q0[8], qd0[8];
+    float Rg[9];                  // row-major R_g
+    float tg[3];
+    float sigma[8];
+};
+
+// Per-call inputs: device pointers to q_0, qdot_0 [7] and the row-major goal
+// pose [16]; sigma by value.
+struct CallInputs {
+    const float *q0, *qd0, *Tg;
+    float sigma[8];
+};
+
+// Fill the shared-memory state from the call inputs (threads of one block).
+__device__ __forceinline__ void load_state(const CallInputs &in, float *s_state)
+{
+    InstanceState &st = *reinterpret_cast<InstanceState *>(s_state);
+    const int t = threadIdx.x;
+    if (t < kNJ) {
+        st.q0[t] = in.q0[t];
+        st.qd0[t] = in.qd0[t];
+        st.sigma[t] = in.sigma[t];
+    } else if (t >= 32 && t < 44) {
+        const int i = t - 32, r = i >> 2, c = i & 3;   // rows 0-2 of T_goal
+        if (c < 3) st.Rg[3 * r + c] = in.Tg[4 * r + c];
+        else st.tg[r] = in.Tg[4 * r + 3];
+    }
+}
+constexpr int kStateFloats = sizeof(InstanceState) / sizeof(float);
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32: per round two 32x32 -> 64 bit products, words permuted and
+// xored with the key; the key is bumped by the Weyl constants each round.
+__device__ __forceinline__ void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                              uint32_t &x3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        const uint32_t y0 = hi1 ^ x1 ^ k0;
+        const uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// u = ((x >> 8) + 0.5) 2^-24: exact in FP32, strictly inside (0, 1).
+__device__ __forceinline__ float word_to_uniform(uint32_t x)
+{
+    return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1)
+{
+    const float u0 = word_to_uniform(w0), u1 = word_to_uniform(w1);
+    const float r = sqrtf(-2.0f * logf(u0));
+    float s, c;
+    sincospif(2.0f * u1, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// Standard normals z[0..7] of roll-out m, step k (counter (m, k, b, iter)).
+__device__ __forceinline__ void step_normals(uint32_t seed_lo, uint32_t seed_hi, uint32_t iter,
+                                             uint32_t m, uint32_t k, float z[8])
+{
+#pragma unroll
+    for (uint32_t b = 0; b < 2; ++b) {
+        uint32_t x0 = m, x1 = k, x2 = b, x3 = iter;
+        philox4x32_10(x0, x1, x2, x3, seed_lo, seed_hi);
+        box_muller(x0, x1, z[4 * b + 0], z[4 * b + 1]);
+        box_muller(x2, x3, z[4 * b + 2], z[4 * b + 3]);
+    }
+}
+
+// ------------------------------------------------------------------ vectors
+struct f3 { float x, y, z; };
+
+__device__ __forceinline__ f3 mk(float x, float y, float z) { return f3{x, y, z}; }
+__device__ __forceinline__ f3 scale(float a, f3 x) { return f3{a * x.x, a * x.y, a * x.z}; }
+// a*x + y
+__device__ __forceinline__ f3 axpy(float a, f3 x, f3 y)
+{
+    return f3{fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z)};
+}
+__device__ __forceinline__ f3 sub(f3 a, f3 b) { return f3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ f3 cross(f3 a, f3 b)
+{
+    return f3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Frame as rotation columns c1, c2, c3 and origin t (world coordinates).
+struct Frame { f3 c1, c2, c3, t; };
+
+__device__ __forceinline__ Frame base_frame()
+{
+    return Frame{mk(1.f, 0.f, 0.f), mk(0.f, 1.f, 0.f), mk(0.f, 0.f, 1.f), mk(0.f, 0.f, 0.f)};
+}
+
+// T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d)  (modified DH, Eq. 1).
+__device__ __forceinline__ void dh_step(Frame &F, float ca, float sa, float a, float d,
+                                        float theta)
+{
+    F.t = axpy(a, F.c1, F.t);                       // TransX(a); RotX keeps the x axis
+    const f3 x2 = axpy(sa, F.c3, scale(ca, F.c2));  // RotX(alpha): y' = ca y + sa z
+    const f3 x3 = axpy(-sa, F.c2, scale(ca, F.c3)); //              z' = -sa y + ca z
+    float s, c;
+    sincosf(theta, &s, &c);
+    const f3 y1 = axpy(s, x2, scale(c, F.c1));      // RotZ(theta): x'' = c x + s y'
+    const f3 y2 = axpy(-s, F.c1, scale(c, x2));     //              y'' = -s x + c y'
+    F.c1 = y1;
+    F.c2 = y2;
+    F.c3 = x3;
+    F.t = axpy(d, x3, F.t);                         // TransZ(d)
+}
+
+// Point o given in frame F, in world coordinates: R o + t.
+__device__ __forceinline__ f3 frame_point(const Frame &F, float ox, float oy, float oz)
+{
+    return axpy(oz, F.c3, axpy(oy, F.c2, axpy(ox, F.c1, F.t)));
+}
+
+// ------------------------------------------------------------ distance field
+template <typename T> __device__ __forceinline__ float grid_load(const T *p);
+template <> __device__ __forceinline__ float grid_load<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float grid_load<__half>(const __half *p)
+{
+    return __half2float(__ldg(p));
+}
+template <> __device__ __forceinline__ float grid_load<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+
+// Clamp a grid coordinate into [0, n-1] and split it into a cell index in
+// [0, n-2] and a fraction in [0, 1].
+__device__ __forceinline__ int cell(float g, float gmax, int n, float &f)
+{
+    g = fminf(fmaxf(g, 0.0f), gmax);                // NaN maps to 0 (fmaxf)
+    const int i = min(static_cast<int>(g), n - 2);  // g >= 0: truncation is floor
+    f = g - static_cast<float>(i);
+    return i;
+}
+
+// phi(p): trilinear interpolation of the voxel-centre samples (Eq. 14).
+template <typename T>
+__device__ __forceinline__ float phi_trilinear(const GridConst &g, f3 p)
+{
+    float fx, fy, fz;
+    const int ix = cell((p.x - g.ox) * g.inv_res - 0.5f, g.mx, g.nx, fx);
+    const int iy = cell((p.y - g.oy) * g.inv_res - 0.5f, g.my, g.ny, fy);
+    const int iz = cell((p.z - g.oz) * g.inv_res - 0.5f, g.mz, g.nz, fz);
+    const int sy = g.nx, sz = g.nx * g.ny;
+    const T *b = static_cast<const T *>(g.phi) + (iz * sz + iy * sy + ix);
+    const float c000 = grid_load(b), c100 = grid_load(b + 1);
+    const float c010 = grid_load(b + sy), c110 = grid_load(b + sy + 1);
+    const float c001 = grid_load(b + sz), c101 = grid_load(b + sz + 1);
+    const float c011 = grid_load(b + sz + sy), c111 = grid_load(b + sz + sy + 1);
+    const float c00 = fmaf(fx, c100 - c000, c000), c10 = fmaf(fx, c110 - c010, c010);
+    const float c01 = fmaf(fx, c101 - c001, c001), c11 = fmaf(fx, c111 - c011, c011);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    return fmaf(fz, c1 - c0, c0);
+}
+
+// ----------------------------------------------------------------- SE(3)
+// xi = [v; w] = log(T_g^{-1} T) for T = (F.c1 F.c2 F.c3 | t), Eqs. 8-12.
+// Rg row-major, tg: goal pose.
+__device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 c1, f3 c2,
+                                           f3 c3, f3 t, float xi[6])
+{
+    // columns of R_g (rows of R_g^T)
+    const f3 g0 = mk(Rg[0], Rg[3], Rg[6]);
+    const f3 g1 = mk(Rg[1], Rg[4], Rg[7]);
+    const f3 g2 = mk(Rg[2], Rg[5], Rg[8]);
+    // R_delta = R_g^T R,  t_delta = R_g^T (t - t_g)
+    const float r00 = dot(g0, c1), r01 = dot(g0, c2), r02 = dot(g0, c3);
+    const float r10 = dot(g1, c1), r11 = dot(g1, c2), r12 = dot(g1, c3);
+    const float r20 = dot(g2, c1), r21 = dot(g2, c2), r22 = dot(g2, c3);
+    const f3 dt = sub(t, mk(tg[0], tg[1], tg[2]));
+    const f3 td = mk(dot(g0, dt), dot(g1, dt), dot(g2, dt));
+
+    const f3 vee = mk(r21 - r12, r02 - r20, r10 - r01);  // 2 sin(th) a
+    const float nv = sqrtf(dot(vee, vee));
+    const float cth = 0.5f * (r00 + r11 + r22 - 1.0f);   // cos(th)
+    const float th = atan2f(0.5f * nv, cth);
+    f3 w;
+    if (th < 1e-4f) {
+        w = scale(0.5f + th * th * (1.0f / 12.0f), vee);
+    } else if (th < CUDART_PI_F - 0.05f) {
+        w = scale(th / nv, vee);
+    } else {
+        // Near pi: (R + R^T)/2 = cos(th) I + (1 - cos(th)) a a^T; take the axis
+        // from the column with the largest diagonal, the sign from vee.
+        const float inv = 1.0f / (1.0f - cth);
+        const float b00 = (r00 - cth) * inv, b11 = (r11 - cth) * inv, b22 = (r22 - cth) * inv;
+        const float b01 = 0.5f * (r01 + r10) * inv, b02 = 0.5f * (r02 + r20) * inv;
+        const float b12 = 0.5f * (r12 + r21) * inv;
+        f3 ax;
+        if (b00 >= b11 && b00 >= b22) {
+            const float s = sqrtf(fmaxf(b00, 0.0f));
+            ax = mk(s, b01 / s, b02 / s);
+        } else if (b11 >= b22) {
+            const float s = sqrtf(fmaxf(b11, 0.0f));
+            ax = mk(b01 / s, s, b12 / s);
+        } else {
+            const float s = sqrtf(fmaxf(b22, 0.0f));
+            ax = mk(b02 / s, b12 / s, s);
+        }
+        ax = scale(rsqrtf(dot(ax, ax)), ax);
+        const float dv = dot(ax, vee);
+        float sgn;
+        if (dv != 0.0f) {
+            sgn = dv > 0.0f ? 1.0f : -1.0f;
+        } else {
+            const float big = fabsf(ax.x) >= fabsf(ax.y) && fabsf(ax.x) >= fabsf(ax.z) ? ax.x
+                              : (fabsf(ax.y) >= fabsf(ax.z) ? ax.y : ax.z);
+            sgn = big >= 0.0f ? 1.0f : -1.0f;
+        }
+        w = scale(sgn * th, ax);
+    }
+    // v = V(th)^{-1} t_delta
+    float cc;
+    if (th < 1e-2f) {
+        cc = (1.0f / 12.0f) + th * th * (1.0f / 720.0f);
+    } else {
+        const float h = 0.5f * th;
+        float sh, ch;
+        sincosf(h, &sh, &ch);
+        cc = (1.0f - h * ch / sh) / (th * th);
+    }
+    const f3 wxt = cross(w, td);
+    const f3 wwxt = cross(w, wxt);
+    const f3 v = axpy(cc, wwxt, axpy(-0.5f, wxt, td));
+    xi[0] = v.x; xi[1] = v.y; xi[2] = v.z;
+    xi[3] = w.x; xi[4] = w.y; xi[5] = w.z;
+}
+
+// 1/2 xi^T diag(Q) xi  (Eqs. 13, 22).
+__device__ __forceinline__ float quad_cost(const float xi[6], const float *Q)
+{
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s = fmaf(Q[i] * xi[i], xi[i], s);
+    return 0.5f * s;
+}
+
+// delta(x) of Eq. 17 on the tightened box [lo, hi].
+__device__ __forceinline__ float limit_violation(float x, float lo, float hi)
+{
+    return fmaxf(x - hi, 0.0f) + fminf(x - lo, 0.0f);
+}
+
+// ------------------------------------------------------ compensated sums
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
+{
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+} // namespace pm

@@ -1,0 +1,418 @@
+// The SMPC iteration kernel (ParaMaP, arXiv 2512.22575, Algorithm 1).
+//
+// Work decomposition.  A warp tile holds R = 32 / L roll-outs; each roll-out
+// occupies L lanes and each lane owns C consecutive time steps
+// k = l*C .. l*C + C-1 (H <= C*L).  Because the dynamics of Eq. 2 are a
+// double integrator over the sampled accelerations, the states are prefix
+// sums over k:
+//     qd_{k+1} = qd_0 + dt A_{k+1},             A_k = sum_{i<k} u_i
+//     q_{k+1}  = q_0 + (k+1) dt qd_0 + dt^2 B_{k+1},  B_k = sum_{i=1..k} A_i,
+// computed with two segmented warp scans, so every (m, k) step is
+// independent afterwards.  Lane step k evaluates the control terms of u_k
+// (Eqs. 18, 20) and the state terms of q_{k+1}, qd_{k+1} (Eqs. 13, 16, 18,
+// 21) or, for k+1 = H, the terminal cost (Eq. 22).  The state terms of
+// k = 0 depend only on (q_0, qd_0) and are the same for every roll-out: one
+// warp computes them once and they are added to S at the end; they cancel
+// in the weights of Eq. 25.
+//
+// Soft-min (Eqs. 25-26).  Each warp keeps a running minimum m, sum
+// z = sum exp(-(S - m)/lambda) and accumulator sum exp(-(S - m)/lambda) eps,
+// rescaled when m drops (the eps of a roll-out never leave registers).
+// Warps merge into a block partial; the last block to finish (atomic ticket
+// after a fence, no waiting) merges the block partials in block order and
+// writes U* = Ubar + acc / z.
+#pragma once
+
+#include "smpc_device.cuh"
+
+namespace pm {
+
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxBlocks = 2048;
+constexpr int kTraceCols = 8;   // pose, env, self, lim_q, lim_qd, lim_qdd, smooth, ns
+
+struct IterArgs {
+    CallInputs in;              // q0, qd0, T_goal (device), sigma
+    const float *Ubar;          // [H][7]
+    float *Uout;                // [H][7], may alias Ubar
+    float *costs;               // [K] or null
+    float *part;                // [gridDim.x][2 + H*7]
+    unsigned *counter;          // zero between launches
+    float *c0;                  // [0] = k = 0 state terms, [1] = min S
+    float *trace;               // [K][H+1][8] (trace kernels only)
+    int K, H;
+    uint32_t seed_lo, seed_hi, iter;
+    float dt, inv_lambda;
+};
+
+// ------------------------------------------------------------ cost terms
+// Control terms at step k (Eqs. 18, 20): w_qdd delta(qdd)^2 + w_s qdd^2.
+template <bool TRACE>
+__device__ __forceinline__ float control_cost(const RobotConst &rc, const float *u, float *tr)
+{
+    float lim = 0.f, sm = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNJ; ++j) {
+        const float dl = limit_violation(u[j], rc.qdd_lo[j], rc.qdd_hi[j]);
+        lim = fmaf(dl, dl, lim);
+        sm = fmaf(u[j], u[j], sm);
+    }
+    lim *= rc.w_qdd;
+    sm *= rc.w_s;
+    if (TRACE) { tr[5] = lim; tr[6] = sm; }
+    return lim + sm;
+}
+
+// State terms at a step (Eqs. 13, 16, 18, 21), or the terminal cost (Eq. 22).
+// Forward kinematics runs frame by frame; the spheres of each frame are
+// looked up as soon as it is known.
+template <typename GT, bool TRACE>
+__device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
+                                            const InstanceState &st, const float *q,
+                                            const float *qd, bool terminal, float *tr)
+{
+    Frame F = base_frame();
+    float env = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNJ; ++j) {
+        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
+        if (!terminal) {
+            for (int s = rc.link_begin[j + 1]; s < rc.link_begin[j + 2]; ++s) {
+                const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+                const float dl = fmaxf(rc.d_act - (phi_trilinear<GT>(g, p) - rc.sph_r[s]), 0.f);
+                env = fmaf(dl, dl, env);
+            }
+        }
+    }
+    const f3 tee = axpy(rc.flange_d, F.c3, F.t);
+    float xi[6];
+    pose_error(st.Rg, st.tg, F.c1, F.c2, F.c3, tee, xi);
+    if (terminal) {
+        const float c = quad_cost(xi, rc.QH);
+        if (TRACE) tr[0] = c;
+        return c;
+    }
+    const float pose = quad_cost(xi, rc.Q);
+    float lq = 0.f, lqd = 0.f, ns = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNJ; ++j) {
+        const float a = limit_violation(q[j], rc.q_lo[j], rc.q_hi[j]);
+        const float b = limit_violation(qd[j], rc.qd_lo[j], rc.qd_hi[j]);
+        const float e = q[j] - rc.q_ref[j];
+        lq = fmaf(a, a, lq);
+        lqd = fmaf(b, b, lqd);
+        ns = fmaf(e, e, ns);
+    }
+    env *= rc.w_env;
+    lq *= rc.w_q;
+    lqd *= rc.w_qd;
+    ns *= rc.w_ns;
+    if (TRACE) { tr[0] = pose; tr[1] = env; tr[3] = lq; tr[4] = lqd; tr[7] = ns; }
+    return pose + env + lq + lqd + ns;
+}
+
+// k = 0 state terms, computed by one warp: lane p takes spheres p, p+32;
+// lane 0 adds the pose, joint-limit and null-space terms.
+template <typename GT>
+__device__ void initial_state_cost_warp(const RobotConst &rc, const GridConst &g,
+                                        const InstanceState &st, float *out)
+{
+    const int lane = threadIdx.x & 31;
+    Frame F = base_frame();
+    float env = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNJ; ++j) {
+        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], st.q0[j] + rc.th0[j]);
+        for (int s = rc.link_begin[j + 1]; s < rc.link_begin[j + 2]; ++s) {
+            if ((s & 31) != lane) continue;
+            const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+            const float dl = fmaxf(rc.d_act - (phi_trilinear<GT>(g, p) - rc.sph_r[s]), 0.f);
+            env = fmaf(dl, dl, env);
+        }
+    }
+    float v = rc.w_env * env;
+    if (lane == 0) {
+        const f3 tee = axpy(rc.flange_d, F.c3, F.t);
+        float xi[6];
+        pose_error(st.Rg, st.tg, F.c1, F.c2, F.c3, tee, xi);
+        float lq = 0.f, lqd = 0.f, ns = 0.f;
+        for (int j = 0; j < kNJ; ++j) {
+            const float a = limit_violation(st.q0[j], rc.q_lo[j], rc.q_hi[j]);
+            const float b = limit_violation(st.qd0[j], rc.qd_lo[j], rc.qd_hi[j]);
+            const float e = st.q0[j] - rc.q_ref[j];
+            lq = fmaf(a, a, lq);
+            lqd = fmaf(b, b, lqd);
+            ns = fmaf(e, e, ns);
+        }
+        v += quad_cost(xi, rc.Q) + rc.w_q * lq + rc.w_qd * lqd + rc.w_ns * ns;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) *out = v;
+}
+
+// ---------------------------------------------------------- warp scans
+// Exclusive prefix sum over the L lanes of each segment, for 7 values.
+template <int L>
+__device__ __forceinline__ void seg_exclusive_scan(const float *x, float *ex, int sl)
+{
+#pragma unroll
+    for (int j = 0; j < kNJ; ++j) {
+        float v = x[j];
+#pragma unroll
+        for (int d = 1; d < L; d <<= 1) {
+            const float t = __shfl_up_sync(0xffffffffu, v, d, L);
+            if (sl >= d) v += t;
+        }
+        const float e = __shfl_up_sync(0xffffffffu, v, 1, L);
+        ex[j] = (sl == 0) ? 0.f : e;
+    }
+}
+
+__device__ __forceinline__ float weight_factor(float m_from, float m_to, float inv_lambda)
+{
+    return (m_from == CUDART_INF_F) ? 0.f : expf((m_to - m_from) * inv_lambda);
+}
+
+// ------------------------------------------------------------------ kernel
+template <int C, int L, typename GT, bool TRACE>
+__global__ void __launch_bounds__(kBlock, 2)
+smpc_iteration_kernel(const RobotConst rc, const GridConst g, const IterArgs a)
+{
+    static_assert(32 % L == 0 && C >= 1, "tile shape");
+    constexpr int R = 32 / L;
+    __shared__ float s_state[kStateFloats];
+    __shared__ float s_wm[kWarps], s_wz[kWarps];
+    __shared__ float s_acc[C * L * kNJ];
+    __shared__ float s_f[kMaxBlocks];
+    __shared__ float s_red[kWarps];
+    __shared__ unsigned s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int seg = lane / L, sl = lane % L;
+    const int H = a.H;
+    static_assert(kBlock >= 44, "state loader needs 44 threads");
+    load_state(a.in, s_state);
+    for (int i = tid; i < C * L * kNJ; i += kBlock) s_acc[i] = 0.f;
+    __syncthreads();
+    const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
+
+    if (!TRACE && blockIdx.x == 0 && warp == 0) initial_state_cost_warp<GT>(rc, g, st, a.c0);
+
+    float run_m = CUDART_INF_F, run_z = 0.f;
+    float acc[C][kNJ];
+#pragma unroll
+    for (int s = 0; s < C; ++s)
+#pragma unroll
+        for (int j = 0; j < kNJ; ++j) acc[s][j] = 0.f;
+
+    const int n_tiles = (a.K + R - 1) / R;
+    for (int tile = blockIdx.x * kWarps + warp; tile < n_tiles; tile += gridDim.x * kWarps) {
+        const int m = tile * R + seg;
+        const bool active = m < a.K;
+
+        // Alg. 1 lines 3-4: eps ~ D, u = ubar + eps
+        float eps[C][kNJ], u[C][kNJ];
+#pragma unroll
+        for (int s = 0; s < C; ++s) {
+            const int k = sl * C + s;
+            if (active && k < H) {
+                float z[8];
+                step_normals(a.seed_lo, a.seed_hi, a.iter, static_cast<uint32_t>(m),
+                             static_cast<uint32_t>(k), z);
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) {
+                    eps[s][j] = st.sigma[j] * z[j];
+                    u[s][j] = __ldg(a.Ubar + k * kNJ + j) + eps[s][j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) { eps[s][j] = 0.f; u[s][j] = 0.f; }
+            }
+        }
+
+        // Alg. 1 line 5: roll-out by two segmented prefix scans
+        float A0[kNJ], B0[kNJ];
+        {
+            float T[kNJ], TB[kNJ];
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) {
+                float run = 0.f;
+#pragma unroll
+                for (int s = 0; s < C; ++s) run += u[s][j];
+                T[j] = run;
+            }
+            seg_exclusive_scan<L>(T, A0, sl);
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) {
+                float run = 0.f, tb = 0.f;
+#pragma unroll
+                for (int s = 0; s < C; ++s) { run += u[s][j]; tb += run; }
+                TB[j] = fmaf(static_cast<float>(C), A0[j], tb);
+            }
+            seg_exclusive_scan<L>(TB, B0, sl);
+        }
+
+        // Alg. 1 lines 6-7: kinematics and costs of each of my steps
+        float lsum = 0.f, lcomp = 0.f;
+        float runU[kNJ], runB[kNJ];
+#pragma unroll
+        for (int j = 0; j < kNJ; ++j) { runU[j] = 0.f; runB[j] = B0[j]; }
+#pragma unroll
+        for (int s = 0; s < C; ++s) {
+            const int k = sl * C + s;
+            float q[kNJ], qd[kNJ];
+            const float kp_dt = static_cast<float>(k + 1) * a.dt;
+            const float dt2 = a.dt * a.dt;
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) {
+                runU[j] += u[s][j];
+                const float A = A0[j] + runU[j];           // A_{k+1}
+                runB[j] += A;                               // B_{k+1}
+                qd[j] = fmaf(a.dt, A, st.qd0[j]);
+                q[j] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
+            }
+            if (active && k < H) {
+                float *tr_u = nullptr, *tr_x = nullptr;
+                if (TRACE) {
+                    tr_u = a.trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
+                    tr_x = tr_u + kTraceCols;
+                }
+                float step = control_cost<TRACE>(rc, u[s], tr_u);
+                step += state_cost<GT, TRACE>(rc, g, st, q, qd, k + 1 == H, tr_x);
+                kahan_add(lsum, lcomp, step);
+            }
+        }
+
+        // S'^(m): compensated sum over the segment's lanes
+        float ssum = lsum, serr = -lcomp;
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, ssum, off);
+            const float oe = __shfl_xor_sync(0xffffffffu, serr, off);
+            float ns, e;
+            two_sum(ssum, os, ns, e);
+            serr = serr + oe + e;
+            ssum = ns;
+        }
+        const float S = ssum + serr;
+        if (TRACE) continue;
+        if (active && sl == 0 && a.costs) a.costs[m] = S;
+
+        // online soft-min accumulation (Eqs. 25-26)
+        if (active) {
+            const float nm = fminf(run_m, S);
+            const float f_old = weight_factor(run_m, nm, a.inv_lambda);
+            const float f_new = expf((nm - S) * a.inv_lambda);
+            run_z = fmaf(run_z, f_old, f_new);
+#pragma unroll
+            for (int s = 0; s < C; ++s)
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) acc[s][j] = fmaf(acc[s][j], f_old, f_new * eps[s][j]);
+            run_m = nm;
+        }
+    }
+    if (TRACE) return;
+
+    // merge the R segments of the warp (they hold the same k slots)
+#pragma unroll
+    for (int off = L; off < 32; off <<= 1) {
+        const float om = __shfl_xor_sync(0xffffffffu, run_m, off);
+        const float oz = __shfl_xor_sync(0xffffffffu, run_z, off);
+        const float nm = fminf(run_m, om);
+        const float fa = weight_factor(run_m, nm, a.inv_lambda);
+        const float fb = weight_factor(om, nm, a.inv_lambda);
+        run_z = run_z * fa + oz * fb;
+#pragma unroll
+        for (int s = 0; s < C; ++s)
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) {
+                const float o = __shfl_xor_sync(0xffffffffu, acc[s][j], off);
+                acc[s][j] = acc[s][j] * fa + o * fb;
+            }
+        run_m = nm;
+    }
+
+    // block partial, warps merged in warp order
+    if (lane == 0) { s_wm[warp] = run_m; s_wz[warp] = run_z; }
+    __syncthreads();
+    float Mb = CUDART_INF_F;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) Mb = fminf(Mb, s_wm[w]);
+    const float fw = weight_factor(run_m, Mb, a.inv_lambda);
+    for (int w = 0; w < kWarps; ++w) {
+        if (warp == w && seg == 0) {
+#pragma unroll
+            for (int s = 0; s < C; ++s) {
+                const int k = sl * C + s;
+                if (k < H) {
+#pragma unroll
+                    for (int j = 0; j < kNJ; ++j)
+                        s_acc[k * kNJ + j] = fmaf(fw, acc[s][j], s_acc[k * kNJ + j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int stride = 2 + H * kNJ;
+    float *P = a.part + static_cast<size_t>(blockIdx.x) * stride;
+    if (tid == 0) {
+        float zb = 0.f;
+        for (int w = 0; w < kWarps; ++w) zb += s_wz[w] * weight_factor(s_wm[w], Mb, a.inv_lambda);
+        P[0] = Mb;
+        P[1] = zb;
+    }
+    for (int i = tid; i < H * kNJ; i += kBlock) P[2 + i] = s_acc[i];
+
+    // last block to arrive merges the partials (no block waits for another)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    const int nb = gridDim.x;
+    float lm = CUDART_INF_F;
+    for (int b = tid; b < nb; b += kBlock) lm = fminf(lm, __ldcg(a.part + static_cast<size_t>(b) * stride));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
+    if (lane == 0) s_red[warp] = lm;
+    __syncthreads();
+    float M = CUDART_INF_F;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) M = fminf(M, s_red[w]);
+    __syncthreads();
+
+    float lz = 0.f;
+    for (int b = tid; b < nb; b += kBlock) {
+        const float *Pb = a.part + static_cast<size_t>(b) * stride;
+        const float f = weight_factor(__ldcg(Pb), M, a.inv_lambda);
+        s_f[b] = f;
+        lz = fmaf(f, __ldcg(Pb + 1), lz);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lz += __shfl_xor_sync(0xffffffffu, lz, off);
+    if (lane == 0) s_red[warp] = lz;
+    __syncthreads();
+    float Z = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) Z += s_red[w];
+    const float invZ = 1.0f / Z;
+
+    for (int i = tid; i < H * kNJ; i += kBlock) {
+        float s = 0.f;
+        for (int b = 0; b < nb; ++b)
+            s = fmaf(s_f[b], __ldcg(a.part + static_cast<size_t>(b) * stride + 2 + i), s);
+        a.Uout[i] = a.Ubar[i] + s * invZ;
+    }
+
+    const float c0 = __ldcg(a.c0);
+    if (tid == 0) a.c0[1] = M + c0;
+    if (a.costs)
+        for (int i = tid; i < a.K; i += kBlock) a.costs[i] = __ldcg(a.costs + i) + c0;
+    if (tid == 0) *a.counter = 0u;
+}
+
+} // namespace pm

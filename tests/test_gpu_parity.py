@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; tolerances from parity_common: Philox words
+bit-exact, costs 1e-4 relative, U* 1e-5 absolute (and 1e-6 for the
+reduction alone).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from parity_common import (NOISE_ABS, NOISE_REL, S_REL, SIGMA, U_ABS, U_ISO, Scene,
+                           first_order_bound, fp64_update_from_costs)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU only with -m gpu
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2512_22575_b300 as pm  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return {s: Scene(f"cfg1_seed{s}") for s in range(10)}
+
+
+# ------------------------------------------------------------------ sampler
+def test_philox_words_bit_exact():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [255, 31, 1, 7]]
+    for key in (0, 0x1234_5678_9ABC_DEF0, 2**64 - 1):
+        c = torch.from_numpy(ctr.view(np.int32).copy()).view(torch.uint32).to(DEV)
+        out = torch.empty_like(c)
+        pm.philox4x32_10(c, key, out)
+        torch.cuda.synchronize()
+        gpu = out.cpu().view(torch.int32).numpy().view(np.uint32)
+        ref = oracle.philox(ctr, [key & 0xFFFFFFFF, key >> 32])
+        assert np.array_equal(gpu, ref)
+
+
+@pytest.mark.parametrize("K,H,it", [(64, 32, 0), (33, 17, 5), (3, 256, 2**32 - 1)])
+def test_noise_matches_oracle(K, H, it):
+    sigma = np.array([0.5, 0.1, 1.0, 2.0, 0.25, 0.75, 1.5], dtype=np.float32)
+    eps = torch.empty((K, H, 7), dtype=torch.float32, device=DEV)
+    pm.sample_noise(K, H, sigma, 0xABCDEF, it, eps)
+    torch.cuda.synchronize()
+    ref = oracle.eps_tensor(0xABCDEF, it, K, H, sigma)
+    err = np.abs(eps.cpu().numpy() - ref)
+    assert np.all(err <= NOISE_ABS + NOISE_REL * np.abs(ref))
+
+
+# ------------------------------------------------------- one SMPC iteration
+def run_both(scene, K, H, seed, it, U=None, lam=0.05, sigma=SIGMA, dt=0.02, n_threads=0):
+    U = np.zeros((H, 7), dtype=np.float32) if U is None else U.astype(np.float32)
+    p = scene.planner()
+    Ug = U.copy()
+    Sg = np.empty(K, dtype=np.float32)
+    p.smpc_iterate(scene.q0, scene.qd0, scene.T, Ug, K, dt, lam, sigma, seed, it, costs_out=Sg)
+    Uo, So, wo = scene.oracle_iterate(U, K, dt, lam, sigma, seed, it, n_threads=n_threads)
+    p.close()
+    return Ug, Sg, Uo, So, wo
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cfg1_costs_and_update(cfg1, seed):
+    """K=256, H=32 single iteration on each cfg1 scene."""
+    sc = cfg1[seed]
+    K, H, lam = 256, 32, 0.05
+    Ug, Sg, Uo, So, wo = run_both(sc, K, H, 1000 + seed, 3 * seed)
+    rel = np.abs(Sg - So) / np.abs(So)
+    assert rel.max() <= S_REL, f"max rel cost error {rel.max():.2e}"
+    bound = first_order_bound(Sg, So, SIGMA, lam)
+    err = np.abs(Ug - Uo).max()
+    assert err <= U_ABS, f"|U*-U*_ref| = {err:.2e} (first-order bound {bound:.2e})"
+    eps = oracle.eps_tensor(1000 + seed, 3 * seed, K, H, SIGMA)
+    Uiso, _ = fp64_update_from_costs(Sg, eps, np.zeros((H, 7)), lam)
+    assert np.abs(Ug - Uiso).max() <= U_ISO
+
+
+@pytest.mark.parametrize("K,H", [(1, 16), (37, 16), (300, 16), (5, 5), (70, 48), (129, 64),
+                                 (50, 100), (9, 200), (2, 256), (513, 32), (1000, 33)])
+def test_tiles_and_ragged_shapes(cfg1, K, H):
+    """Every instantiated tile shape, ragged K and H, several tiles per warp."""
+    sc = cfg1[1]
+    rng = np.random.default_rng(K * 1000 + H)
+    U = (rng.normal(size=(H, 7)) * 0.3).astype(np.float32)
+    Ug, Sg, Uo, So, wo = run_both(sc, K, H, 77, 1, U=U)
+    assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL
+    assert np.abs(Ug - Uo).max() <= U_ABS
+
+
+def test_zero_sigma_returns_nominal(cfg1):
+    sc = cfg1[2]
+    K, H = 100, 32
+    U = (np.random.default_rng(1).normal(size=(H, 7)) * 0.2).astype(np.float32)
+    Ug, Sg, Uo, So, _ = run_both(sc, K, H, 5, 0, U=U, sigma=np.zeros(7, np.float32))
+    assert np.array_equal(Ug, U)
+    assert np.all(Sg == Sg[0])
+    assert abs(Sg[0] - So[0]) <= S_REL * abs(So[0])
+
+
+def test_small_lambda_selects_gpu_argmin(cfg1):
+    """lambda -> 0: U* = Ubar + eps of the minimum-cost roll-out.  Which roll-out
+    is the minimum is decided in FP32 by the GPU; its cost must match the
+    oracle's minimum within tolerance and U* must be that roll-out's eps."""
+    sc = cfg1[3]
+    K, H = 256, 32
+    Ug, Sg, Uo, So, _ = run_both(sc, K, H, 11, 4, lam=1e-12)
+    m = int(np.argmin(Sg))
+    assert abs(So[m] - So.min()) <= S_REL * abs(So.min())
+    eps = oracle.eps_tensor(11, 4, K, H, SIGMA)
+    assert np.abs(Ug - eps[m]).max() <= 1e-6
+
+
+def test_large_lambda_averages(cfg1):
+    sc = cfg1[4]
+    K, H = 256, 32
+    Ug, Sg, Uo, So, _ = run_both(sc, K, H, 12, 0, lam=1e12)
+    eps = oracle.eps_tensor(12, 0, K, H, SIGMA)
+    assert np.abs(Ug - eps.mean(0)).max() <= 1e-6
+
+
+def test_costs_independent_of_K(cfg1):
+    sc = cfg1[5]
+    p = sc.planner()
+    H = 32
+    S1 = np.empty(256, np.float32)
+    S2 = np.empty(1024, np.float32)
+    p.smpc_iterate(sc.q0, sc.qd0, sc.T, np.zeros((H, 7), np.float32), 256, 0.02, 0.05, SIGMA, 9, 0, costs_out=S1)
+    p.smpc_iterate(sc.q0, sc.qd0, sc.T, np.zeros((H, 7), np.float32), 1024, 0.02, 0.05, SIGMA, 9, 0, costs_out=S2)
+    p.close()
+    assert np.array_equal(S1, S2[:256])
+
+
+def test_host_and_device_buffers_agree(cfg1):
+    sc = cfg1[6]
+    p = sc.planner()
+    K, H = 512, 32
+    U = (np.random.default_rng(2).normal(size=(H, 7)) * 0.2).astype(np.float32)
+    Uh = U.copy()
+    Sh = np.empty(K, np.float32)
+    p.smpc_iterate(sc.q0, sc.qd0, sc.T, Uh, K, 0.02, 0.05, SIGMA, 3, 1, costs_out=Sh)
+    Ud = torch.from_numpy(U).to(DEV)
+    Sd = torch.empty(K, dtype=torch.float32, device=DEV)
+    q0 = torch.from_numpy(sc.q0).to(DEV)
+    qd0 = torch.from_numpy(sc.qd0).to(DEV)
+    Td = torch.from_numpy(sc.T.ravel().copy()).to(DEV)
+    p.smpc_iterate(q0, qd0, Td, Ud, K, 0.02, 0.05, SIGMA, 3, 1, costs_out=Sd)
+    torch.cuda.synchronize()
+    p.close()
+    assert np.array_equal(Ud.cpu().numpy(), Uh)
+    assert np.array_equal(Sd.cpu().numpy(), Sh)
+
+
+def test_repeat_calls_are_deterministic(cfg1):
+    sc = cfg1[7]
+    p = sc.planner()
+    outs = []
+    for _ in range(3):
+        U = np.zeros((64, 7), np.float32)
+        p.smpc_iterate(sc.q0, sc.qd0, sc.T, U, 2048, 0.02, 0.05, SIGMA, 4, 2)
+        outs.append(U)
+    p.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_invalid_arguments_leave_U_untouched(cfg1):
+    sc = cfg1[8]
+    p = sc.planner()
+    U = np.ones((32, 7), np.float32)
+    bad_q = sc.q0.copy()
+    bad_q[2] = np.nan
+    cases = [dict(K=0), dict(K=-3), dict(lam=0.0), dict(lam=float("nan")), dict(q0=bad_q),
+             dict(sigma=np.full(7, -1.0, np.float32))]
+    for c in cases:
+        args = dict(q0=sc.q0, qd0=sc.qd0, T=sc.T, U=U, K=64, dt=0.02, lam=0.05, sigma=SIGMA)
+        args.update(c)
+        with pytest.raises(pm.PmError) as e:
+            p.smpc_iterate(args["q0"], args["qd0"], args["T"], args["U"], args["K"], args["dt"],
+                           args["lam"], args["sigma"], 1, 0)
+        assert e.value.name == "PM_EINVAL"
+    with pytest.raises(pm.PmError):
+        p.smpc_iterate(sc.q0, sc.qd0, sc.T, np.ones((257, 7), np.float32), 8, 0.02, 0.05, SIGMA, 1, 0)
+    p.close()
+    assert np.all(U == 1.0)
+
+
+def test_missing_field_is_an_error(cfg1):
+    sc = cfg1[0]
+    p = pm.Planner(sc.robot, sc.grid_desc, sc.cp)
+    with pytest.raises(pm.PmError) as e:
+        p.smpc_iterate(sc.q0, sc.qd0, sc.T, np.zeros((8, 7), np.float32), 4, 0.02, 0.05, SIGMA, 1, 0)
+    assert e.value.name == "PM_EINVAL"
+    p.close()
+
+
+def test_trace_matches_oracle_terms(cfg1):
+    """Per-step cost terms of a few roll-outs (debugging aid for the parity)."""
+    sc = cfg1[1]
+    K, H = 8, 32
+    p = sc.planner()
+    tr = torch.zeros((K, H + 1, 8), dtype=torch.float32, device=DEV)
+    U = np.zeros((H, 7), np.float32)
+    p.rollout_trace(sc.q0, sc.qd0, sc.T, U, K, 0.02, SIGMA, 21, 0, tr)
+    p.close()
+    tr = tr.cpu().numpy()
+    eps = oracle.eps_tensor(21, 0, K, H, SIGMA)
+    for m in range(K):
+        _, ref = oracle.rollout_cost(sc.R, sc.G, sc.C, sc.q0, sc.qd0, sc.T, U + eps[m], 0.02,
+                                     trace=True)
+        ref = ref.copy()
+        ref[0, [0, 1, 2, 3, 4, 7]] = 0.0  # k = 0 state terms are not per roll-out
+        assert np.allclose(tr[m], ref, rtol=1e-4, atol=1e-7)
+
+
+# ------------------------------------------------------------ full-size cfg2
+@pytest.fixture(scope="module")
+def cfg2():
+    return Scene("cfg2")
+
+
+def test_cfg2_full_size_iteration(cfg2):
+    """K=4096, H=64 on the 160x160x120 grid, in the bench's launch shape."""
+    K, H = cfg2.sc["K"], cfg2.sc["H"]
+    rng = np.random.default_rng(3)
+    U = (rng.normal(size=(H, 7)) * 0.2).astype(np.float32)
+    Ug, Sg, Uo, So, wo = run_both(cfg2, K, H, 100, 0, U=U)
+    assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL
+    assert np.abs(Ug - Uo).max() <= U_ABS
+
+
+def test_cfg2_one_replan(cfg2):
+    """pm_replan (8 iterations + execute + shift) against the oracle's replan."""
+    K, H, iters = cfg2.sc["K"], cfg2.sc["H"], cfg2.sc["iters"]
+    p = cfg2.planner()
+    q, qd = cfg2.q0.copy(), cfg2.qd0.copy()
+    U = np.zeros((H, 7), np.float32)
+    u0 = np.empty(7, np.float32)
+    best = np.empty(1, np.float32)
+    p.replan(q, qd, cfg2.T, U, K, iters, 0.02, 0.05, SIGMA, 100, 0, u0_out=u0, best_cost=best)
+    p.close()
+    qo, qdo, Uo, u0o, besto = oracle.replan(cfg2.R, cfg2.G, cfg2.C, cfg2.q0, cfg2.qd0, cfg2.T,
+                                            np.zeros((H, 7)), K, 0.02, 0.05, SIGMA, 100, 0, iters,
+                                            n_threads=0)
+    # errors of one iteration enter the next one's nominal sequence
+    assert np.abs(U - Uo).max() <= iters * U_ABS
+    assert np.abs(u0 - u0o).max() <= iters * U_ABS
+    assert np.abs(qd - qdo).max() <= 1e-6 and np.abs(q - qo).max() <= 1e-6
+    assert abs(best[0] - besto) <= S_REL * abs(besto)
