@@ -3,12 +3,12 @@
  *
  * One SMPC iteration (ParaMaP, arXiv 2512.22575, Algorithm 1 and Sec. IV-C)
  * over a batch of K candidate roll-outs of a 7-DoF arm: Gaussian
- * perturbations of the nominal joint-acceleration sequence (Eq. 19),
- * Euler roll-out (Eq. 2), forward kinematics (Eq. 1), collision-sphere
- * clearance from a dense distance field (Eqs. 14-16), SE(3) pose error
- * (Eqs. 8-13), joint-limit, smoothness, null-space and terminal costs
- * (Eqs. 17-22), soft-min weights (Eq. 25) and the weighted-mean update of
- * the nominal sequence (Eq. 26).  All of it runs in the library's CUDA
+ * perturbations of the nominal joint-acceleration sequence (Eq. 27),
+ * Euler roll-out (Eq. 7), forward kinematics (Eq. 6), collision-sphere
+ * clearance from a dense distance field (Eqs. 17-20), SE(3) pose error
+ * (Eqs. 11-16), joint-limit, smoothness, null-space and terminal costs
+ * (Eqs. 21-25), soft-min weights (Eq. 29) and the weighted-mean update of
+ * the nominal sequence (Eq. 30).  All of it runs in the library's CUDA
  * kernels on one GPU.
  *
  * Conventions shared by every entry point:
@@ -63,7 +63,7 @@ typedef enum {
 typedef enum { PM_F32 = 0, PM_F16 = 1, PM_BF16 = 2 } pm_dtype;
 
 /*
- * Arm description (Sec. IV-A, Eq. 1; sphere model of Sec. IV-B-2, Fig. 2).
+ * Arm description (Sec. IV-A, Eq. 6; sphere model of Sec. IV-B-2, Fig. 2).
  * Modified (Craig) DH per joint i = 1..n, stored at index i-1:
  *   T_i = T_{i-1} RotX(alpha[i-1]) TransX(a[i-1]) RotZ(q_i + theta_offset[i-1])
  *         TransZ(d[i-1]),
@@ -71,7 +71,7 @@ typedef enum { PM_F32 = 0, PM_F16 = 1, PM_BF16 = 2 } pm_dtype;
  * Sphere s is centred at R^{L} sphere_offset[s] + t^{L} with L =
  * sphere_link[s] in 1..n (frame index) and has radius sphere_radius[s].
  * self_pairs lists sphere index pairs (i, j) of the self-collision set S of
- * Eq. 15 (may be empty; n_self_pairs = 0).
+ * Eq. 18 (may be empty; n_self_pairs = 0).
  */
 typedef struct {
     int n_joints;
@@ -88,7 +88,7 @@ typedef struct {
 } pm_robot;
 
 /*
- * Dense distance field phi of Eq. 14 (unsigned Euclidean distance in metres
+ * Dense distance field phi of Eq. 17 (unsigned Euclidean distance in metres
  * to the nearest occupied voxel centre, 0 inside obstacles).  Voxel (i, j, l)
  * has centre origin + (i + 0.5, j + 0.5, l + 0.5) * res; each axis needs at
  * least 2 voxels.  phi(p) is the trilinear interpolation of the centre
@@ -105,10 +105,10 @@ typedef struct {
 
 /*
  * Cost weights (Sec. IV-B).  Q and QH are the diagonals of Q_k (k < H) and
- * Q_H acting on xi = [v; omega] (Eqs. 13, 22).  w_env, d_act: Eq. 16;
- * w_self: Eq. 16 over self_pairs; w_q, w_qd, w_qdd with the box tightened by
- * margin_frac * (max - min) per joint: Eqs. 17-18; w_s: Eq. 20; w_ns with
- * q_ref[n_joints]: Eq. 21.
+ * Q_H acting on xi = [v; omega] (Eqs. 16, 25).  w_env, d_act: Eqs. 19-20;
+ * w_self: Eqs. 19-20 over self_pairs; w_q, w_qd, w_qdd with the box tightened by
+ * margin_frac * (max - min) per joint: Eqs. 21-22; w_s: Eq. 23; w_ns with
+ * q_ref[n_joints]: Eq. 24.
  */
 typedef struct {
     float Q[6], QH[6];
@@ -138,21 +138,21 @@ pm_status pm_create(const pm_robot *robot, const pm_grid_desc *grid,
 pm_status pm_set_distance_field(pm_ctx *ctx, const float *grid, int grid_is_device);
 
 /*
- * One SMPC iteration (Algorithm 1; Eqs. 19-26).
+ * One SMPC iteration (Algorithm 1; Eqs. 27-30).
  *   q0, qd0   [7]     start state q_0, qdot_0 (host or device)
  *   T_goal    [16]    target pose T_g, row-major (host or device)
- *   U         [H][7]  in: nominal sequence Ubar; out: U* of Eq. 26
+ *   U         [H][7]  in: nominal sequence Ubar; out: U* of Eq. 30
  *                     (host or device; device buffers are updated in place)
  *   K                 number of roll-outs M, 1..PM_MAX_ROLLOUTS
  *   H                 horizon, 1..PM_MAX_HORIZON
- *   dt                integration step of Eq. 2 (semi-implicit Euler:
+ *   dt                integration step of Eq. 7 (semi-implicit Euler:
  *                     qd_{k+1} = qd_k + dt u_k, q_{k+1} = q_k + dt qd_{k+1})
- *   lambda            temperature of Eq. 25, > 0
+ *   lambda            temperature of Eq. 29, > 0
  *   sigma     [7]     per-joint standard deviation of D (host)
  *   seed, iter_index  noise of roll-out m at step k is Philox4x32-10 with
  *                     key (seed lo, seed hi) and counter (m, k, b, iter_index)
  *                     mapped by Box-Muller (b = 0: joints 0-3, b = 1: 4-6)
- *   costs_out [K]     S^(m) of Eq. 24, or NULL (host or device)
+ *   costs_out [K]     S^(m) of Eq. 28, or NULL (host or device)
  *   cuda_stream       cudaStream_t to run on, or NULL for the context's own
  * Errors: PM_EINVAL (range, NaN in q0/qd0/T_goal/sigma, no field set; U is
  * left untouched), PM_ENOMEM, PM_ECUDA.
@@ -184,10 +184,10 @@ pm_status pm_replan(pm_ctx *ctx, float *q, float *qd, const float *T_goal, float
  * Diagnostics used by the parity tests (same device code as the hot path).
  *
  * pm_philox4x32_10: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key) for
- *   i < n, as the sampler computes it (Salmon et al., SC'11; Eq. 19).
+ *   i < n, as the sampler computes it (Salmon et al., SC'11; Eq. 27).
  *   ctr, out: device memory, uint32[n][4].  Enqueued on cuda_stream.
  * pm_sample_noise: eps[m][k][j] = sigma_j z_j(m, k) for m < K, k < H, j < 7
- *   (Alg. 1 line 3).  eps: device float[K][H][7].  Enqueued on cuda_stream.
+ *   (sampling step of Algorithm 1).  eps: device float[K][H][7].  Enqueued on cuda_stream.
  * pm_rollout_trace: per-step cost terms of roll-outs 0..K-1 of the iteration
  *   pm_smpc_iterate would run with the same arguments; trace: device
  *   float[K][H+1][8] with columns (pose, env, self, lim_q, lim_qd, lim_qdd,

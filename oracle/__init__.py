@@ -171,7 +171,7 @@ def normals(seed, it, m, k):
 
 
 def eps_tensor(seed, it, K, H, sigma, n=7):
-    """eps[m, k, j] = sigma_j z_j(m, k) of Alg. 1 line 3 (FP64)."""
+    """eps[m, k, j] = sigma_j z_j(m, k) of the sampling step of Algorithm 1 (FP64)."""
     sigma = np.asarray(sigma, dtype=np.float64)
     out = np.empty((K, H, n))
     z = np.empty(8)
@@ -228,7 +228,7 @@ def integrate(q0, qd0, u, dt):
 
 
 def rollout_cost(robot, grid, cost, q0, qd0, Tg, u, dt, trace=False):
-    """S of Eq. 24 for one control sequence u [H][n]; optionally per-step terms."""
+    """S of Eq. 28 for one control sequence u [H][n]; optionally per-step terms."""
     u = _f64(u)
     H = u.shape[0]
     tr = np.empty((H + 1, T_COLS)) if trace else None

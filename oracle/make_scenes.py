@@ -5,7 +5,7 @@ configurations, target poses) need forward kinematics for their rejection
 tests: obstacles may not touch the start configuration's spheres (+2 cm) or
 the base column, and the target configuration must be collision-free, keep
 its flange inside the grid, and differ from the start by a rotation well
-below pi (the SE(3) log is discontinuous at pi, Eq. 9).  This script calls
+below pi (the SE(3) log is discontinuous at pi, Eq. 12).  This script calls
 only the oracle and the seeded generators in ``workloads``; every stored
 number is float32-exact, so both sides read identical inputs.
 

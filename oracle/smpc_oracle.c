@@ -9,22 +9,23 @@
  * baseline may load it.
  *
  * Readings of the paper that this file fixes (the paper is silent on them):
- *  - Sampling distribution D (Alg. 1, Eq. 19): independent Gaussians with
+ *  - Sampling distribution D (Alg. 1, Eq. 27): independent Gaussians with
  *    per-joint standard deviation sigma_j, drawn from Philox4x32-10 (Salmon
  *    et al., SC'11) with key = (seed lo, seed hi) and counter
  *    (m, k, b, iter); block b = 0 gives joints 0-3, b = 1 joints 4-7.
- *    Words map to uniforms u = ((x >> 8) + 0.5) 2^-24 and pairs of uniforms
- *    to normals by Box-Muller.
- *  - Dynamics (Eq. 2 with u = joint acceleration): semi-implicit Euler,
+ *    Words map to uniforms u = ((x >> 9) + 0.5) 2^-23 (23 random bits; the
+ *    value is exact in FP32 as well as FP64, so both precisions draw the
+ *    same uniform) and pairs of uniforms to normals by Box-Muller.
+ *  - Dynamics (Eq. 7 with u = joint acceleration): semi-implicit Euler,
  *    qd_{k+1} = qd_k + dt u_k, q_{k+1} = q_k + dt qd_{k+1}, qdd_k = u_k.
- *    The process noise of Eq. 2 is read as the sampling perturbation.
- *  - Forward kinematics (Eq. 1): modified (Craig) DH,
+ *    The process noise of Eq. 7 is read as the sampling perturbation.
+ *  - Forward kinematics (Eq. 6): modified (Craig) DH,
  *    T_i = T_{i-1} RotX(alpha_{i-1}) TransX(a_{i-1}) RotZ(q_i) TransZ(d_i),
  *    and the end effector is the flange, T_n TransZ(flange_d).
- *  - phi in the collision cost (Eq. 14) is the unsigned distance field,
+ *  - phi in the collision cost (Eq. 17) is the unsigned distance field,
  *    sampled by trilinear interpolation between voxel centres, clamped to
  *    the grid (edge replication outside).
- *  - Q_k and Q_H (Eqs. 13, 22) are diagonal.
+ *  - Q_k and Q_H (Eqs. 16, 25) are diagonal.
  */
 #include "smpc_oracle.h"
 
@@ -66,10 +67,10 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 
 double or_word_to_uniform(uint32_t x)
 {
-    return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0);
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-/* Normals for rollout m, step k: z[0..7] (Alg. 1 line 3, Eq. 19). */
+/* Normals for rollout m, step k: z[0..7] (sampling step of Algorithm 1, Eq. 27). */
 void or_normals(uint64_t seed, uint32_t iter, uint32_t m, uint32_t k, double z[8])
 {
     const uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
@@ -126,7 +127,7 @@ static void trans(double x, double y, double z, double M[4][4])
     M[0][3] = x; M[1][3] = y; M[2][3] = z;
 }
 
-/* Link poses T^0..T^n and the flange T^{n+1} (Eq. 1, Sec. IV-A). */
+/* Link poses T^0..T^n and the flange T^{n+1} (Eq. 6, Sec. IV-A). */
 void or_fk(const or_robot *rb, const double *q, double T[][4][4])
 {
     const int n = rb->n_joints;
@@ -173,7 +174,7 @@ static void cell_coord(double p, double origin, double res, int n, int *i0, doub
     *f = x - (double)i;
 }
 
-/* phi(p): trilinear interpolation of the voxel-centre samples (Eq. 14). */
+/* phi(p): trilinear interpolation of the voxel-centre samples (Eq. 17). */
 double or_phi(const or_grid *g, const double p[3])
 {
     int i, j, l;
@@ -191,7 +192,7 @@ double or_phi(const or_grid *g, const double p[3])
 }
 
 /* ---------------------------------------------------------------- SE(3) */
-/* omega with R = exp([omega]x), the principal logarithm (Eq. 9). */
+/* omega with R = exp([omega]x), the principal logarithm (Eq. 12). */
 static void so3_log(const double R[3][3], double w[3])
 {
     double vee[3] = { R[2][1] - R[1][2], R[0][2] - R[2][0], R[1][0] - R[0][1] };
@@ -232,7 +233,7 @@ static double det3(const double M[3][3])
          + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
 }
 
-/* xi = [v; omega] = log(T) (Eqs. 9-12): omega = log R, and v solves
+/* xi = [v; omega] = log(T) (Eqs. 12-15): omega = log R, and v solves
  * t = V(theta) v with V(theta) = I + (1-cos)/th^2 [w]x + (th-sin)/th^3 [w]x^2,
  * solved by Cramer's rule. */
 void or_se3_log(const double T[4][4], double xi[6])
@@ -274,7 +275,7 @@ void or_se3_log(const double T[4][4], double xi[6])
     xi[3] = w[0]; xi[4] = w[1]; xi[5] = w[2];
 }
 
-/* Delta T = T_g^{-1} T_ee (Eq. 8), then xi = log(Delta T). */
+/* Delta T = T_g^{-1} T_ee (Eq. 11), then xi = log(Delta T). */
 void or_pose_error(const double Tg[4][4], const double Tee[4][4], double xi[6])
 {
     double D[4][4];
@@ -300,7 +301,7 @@ static double pose_cost(const double Q[6], const double xi[6])
     return 0.5 * s;
 }
 
-/* delta_i(x) of Eq. 17 on the tightened box [lo + eps, hi - eps]. */
+/* delta_i(x) of Eq. 21 on the tightened box [lo + eps, hi - eps]. */
 static double limit_violation(double x, double lo, double hi, double margin_frac)
 {
     double e = margin_frac * (hi - lo);
@@ -308,7 +309,7 @@ static double limit_violation(double x, double lo, double hi, double margin_frac
     return (up > 0.0 ? up : 0.0) + (dn < 0.0 ? dn : 0.0);
 }
 
-/* Semi-implicit Euler roll-out of Eq. 2: q, qd of size (H+1) x n. */
+/* Semi-implicit Euler roll-out of Eq. 7: q, qd of size (H+1) x n. */
 void or_integrate(int n, int H, double dt, const double *q0, const double *qd0,
                   const double *u, double *q, double *qd)
 {
@@ -320,8 +321,8 @@ void or_integrate(int n, int H, double dt, const double *q0, const double *qd0,
         }
 }
 
-/* S^{(m)} of Eq. 24 for one control sequence u [H][n]: running costs
- * (Eqs. 13, 16, 18, 20, 21) at k = 0..H-1 plus the terminal cost (Eq. 22)
+/* S^{(m)} of Eq. 28 for one control sequence u [H][n]: running costs
+ * (Eqs. 16, 19-20, 22, 23, 24) at k = 0..H-1 plus the terminal cost (Eq. 25)
  * at k = H.  If trace != NULL it receives (H+1) x OR_T_COLS per-step terms
  * (the terminal cost in row H, column OR_T_POSE). */
 double or_rollout(const or_robot *rb, const or_grid *g, const or_cost *c,
@@ -388,7 +389,7 @@ double or_rollout(const or_robot *rb, const or_grid *g, const or_cost *c,
 
 /* ------------------------------------------------------------ Algorithm 1 */
 /* One SMPC iteration.  U [H][n] holds the nominal sequence on entry and the
- * update U* of Eq. 26 on return.  costs/weights (length K) may be NULL. */
+ * update U* of Eq. 30 on return.  costs/weights (length K) may be NULL. */
 int or_smpc_iterate(const or_robot *rb, const or_grid *g, const or_cost *c,
                     const double *q0, const double *qd0, const double Tg[4][4],
                     double *U, int K, int H, double dt, double lambda,
@@ -409,25 +410,25 @@ int or_smpc_iterate(const or_robot *rb, const or_grid *g, const or_cost *c,
     for (int m = 0; m < K; ++m) {
         double *e = eps + (size_t)m * H * n;
         double *um = (double *)malloc(sizeof(double) * (size_t)H * n);
-        for (int k = 0; k < H; ++k) {                       /* line 3 */
+        for (int k = 0; k < H; ++k) {                       /* sample eps */
             double z[8];
             or_normals(seed, iter_index, (uint32_t)m, (uint32_t)k, z);
             for (int j = 0; j < n; ++j) {
                 e[k * n + j] = sigma[j] * z[j];
-                um[k * n + j] = U[k * n + j] + e[k * n + j];  /* line 4 */
+                um[k * n + j] = U[k * n + j] + e[k * n + j];  /* perturb */
             }
         }
-        S[m] = or_rollout(rb, g, c, q0, qd0, Tg, um, H, dt, NULL);  /* lines 5-7 */
+        S[m] = or_rollout(rb, g, c, q0, qd0, Tg, um, H, dt, NULL);  /* roll out, FK, cost */
         free(um);
     }
     (void)n_threads;
 
-    double Smin = S[0];                                      /* line 9 */
+    double Smin = S[0];                                      /* minimum cost */
     for (int m = 1; m < K; ++m) if (S[m] < Smin) Smin = S[m];
-    double Z = 0.0;                                          /* lines 10-12, Eq. 25 */
+    double Z = 0.0;                                          /* weights, Eq. 29 */
     for (int m = 0; m < K; ++m) { w[m] = exp(-(S[m] - Smin) / lambda); Z += w[m]; }
     for (int m = 0; m < K; ++m) w[m] /= Z;
-    for (int k = 0; k < H; ++k)                              /* line 13, Eq. 26 */
+    for (int k = 0; k < H; ++k)                              /* update, Eq. 30 */
         for (int j = 0; j < n; ++j) {
             double acc = 0.0;
             for (int m = 0; m < K; ++m) acc += w[m] * eps[((size_t)m * H + k) * n + j];

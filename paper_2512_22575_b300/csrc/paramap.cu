@@ -41,9 +41,11 @@ struct pm_ctx {
     size_t cap_costs = 0;
     float *h_out = nullptr;             // pinned: costs / small outputs
     size_t cap_h_out = 0;
-    float *d_part = nullptr;
+    float *d_part = nullptr;            // block partials
     size_t cap_part = 0;
-    unsigned *d_counter = nullptr;
+    float *d_gpart = nullptr;           // group partials
+    size_t cap_gpart = 0;
+    unsigned *d_counter = nullptr;      // [1 + kMaxGroups], zero between launches
     float *d_c0 = nullptr;              // [c0, best, q(8), qd(8), u0(8)]
     bool prof = false;                  // bracket iteration kernels with events
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, end)
@@ -129,15 +131,23 @@ IterKernel lookup_kernel(int dtype, TileShape s, bool trace)
     }
 }
 
-int resident_blocks_per_sm(IterKernel fn)
+// Resident blocks per SM of an iteration kernel; on first use also raises
+// its dynamic shared memory limit to what its tile shape needs.
+int resident_blocks_per_sm(IterKernel fn, size_t smem)
 {
     static std::mutex mu;
     static std::unordered_map<const void *, int> cache;
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(reinterpret_cast<const void *>(fn));
     if (it != cache.end()) return it->second;
+    if (cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, smem) != cudaSuccess) {
         cudaGetLastError();
         n = 1;
     }
@@ -231,14 +241,24 @@ pm_status ensure_capacity(pm_ctx *c, int K, int H, int nb)
         PM_CUDA(c, cudaMallocHost(&c->h_out, cap * sizeof(float)));
         c->cap_h_out = cap;
     }
-    const size_t needP = static_cast<size_t>(nb) * (2 + static_cast<size_t>(H) * kNJ);
+    const size_t stride = 2 + static_cast<size_t>(H) * kNJ;
+    const size_t needP = static_cast<size_t>(nb) * stride;
     if (needP > c->cap_part) {
-        size_t cap = std::max(needP, static_cast<size_t>(kMaxBlocks) * (2 + 64 * kNJ));
+        size_t cap = std::max(needP, static_cast<size_t>(1024) * (2 + 64 * kNJ));
         if (c->d_part) cudaFree(c->d_part);
         c->d_part = nullptr;
         c->cap_part = 0;
         PM_CUDA(c, cudaMalloc(&c->d_part, cap * sizeof(float)));
         c->cap_part = cap;
+    }
+    const size_t needG = static_cast<size_t>((nb + kGroup - 1) / kGroup) * stride;
+    if (needG > c->cap_gpart) {
+        size_t cap = std::max(needG, static_cast<size_t>(32) * (2 + 64 * kNJ));
+        if (c->d_gpart) cudaFree(c->d_gpart);
+        c->d_gpart = nullptr;
+        c->cap_gpart = 0;
+        PM_CUDA(c, cudaMalloc(&c->d_gpart, cap * sizeof(float)));
+        c->cap_gpart = cap;
     }
     return PM_OK;
 }
@@ -324,7 +344,10 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
     const int R = 32 / sh.L;
     const long long tiles = (static_cast<long long>(K) + R - 1) / R;
     const long long need = (tiles + kWarps - 1) / kWarps;
-    const long long resident = static_cast<long long>(c->n_sm) * resident_blocks_per_sm(fn);
+    const size_t smem = iteration_smem_bytes(sh.C);
+    const int per_sm = resident_blocks_per_sm(fn, smem);
+    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
+    const long long resident = static_cast<long long>(c->n_sm) * per_sm;
     const int nb = static_cast<int>(std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)})));
     pm_status st = ensure_capacity(c, K, H, nb);
     if (st != PM_OK) return st;
@@ -334,7 +357,8 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
     a.Uout = Uout;
     a.costs = costs;
     a.part = c->d_part;
-    a.counter = c->d_counter;
+    a.gpart = c->d_gpart;
+    a.counters = c->d_counter;
     a.c0 = c->d_c0;
     a.trace = trace_out;
     a.K = K;
@@ -353,7 +377,7 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
         }
         PM_CUDA(c, cudaEventRecord(c->prof_ev[c->prof_used], s));
     }
-    fn<<<nb, kBlock, 0, s>>>(c->rc, grid_const(c), a);
+    fn<<<nb, kBlock, smem, s>>>(c->rc, grid_const(c), a);
     PM_CUDA(c, cudaGetLastError());
     if (prof) {
         PM_CUDA(c, cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
@@ -495,8 +519,8 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         !ck(cudaMalloc(&c->d_stage, sizeof(float) * kSlots * kSlotFloats), "staging alloc") ||
         !ck(cudaMallocHost(&c->h_stage, sizeof(float) * kSlots * kSlotFloats), "pinned staging alloc") ||
         !ck(cudaMallocHost(&c->h_U, sizeof(float) * kMaxHorizon * kNJ), "pinned U") ||
-        !ck(cudaMalloc(&c->d_counter, sizeof(unsigned)), "counter") ||
-        !ck(cudaMemset(c->d_counter, 0, sizeof(unsigned)), "counter zero") ||
+        !ck(cudaMalloc(&c->d_counter, sizeof(unsigned) * (1 + kMaxGroups)), "counter alloc") ||
+        !ck(cudaMemset(c->d_counter, 0, sizeof(unsigned) * (1 + kMaxGroups)), "counter zero") ||
         !ck(cudaMalloc(&c->d_c0, 32 * sizeof(float)), "c0") ||
         !ck(cudaMemset(c->d_c0, 0, 32 * sizeof(float)), "c0 zero"))
         return fail(c->err.find("alloc") != std::string::npos ? PM_ENOMEM : PM_ECUDA);
@@ -728,6 +752,7 @@ void pm_destroy(pm_ctx *c)
         cudaFree(c->d_costs);
         cudaFreeHost(c->h_out);
         cudaFree(c->d_part);
+        cudaFree(c->d_gpart);
         cudaFree(c->d_counter);
         cudaFree(c->d_c0);
         for (cudaEvent_t e : c->slot_ev)

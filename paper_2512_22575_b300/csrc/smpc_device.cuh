@@ -1,14 +1,14 @@
 // Device arithmetic of one SMPC iteration (ParaMaP, arXiv 2512.22575, Sec. IV).
 //
 // Everything here is FP32 except the integer Philox generator.  The pieces:
-//   - Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals (Eq. 19);
+//   - Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals (Eq. 27);
 //   - modified-DH forward kinematics kept as three rotation columns and a
-//     translation, updated joint by joint (Eq. 1);
-//   - trilinear lookup of the distance field phi (Eq. 14);
-//   - the SE(3) pose error xi = log(T_g^{-1} T_ee) (Eqs. 8-12) with the
+//     translation, updated joint by joint (Eq. 6);
+//   - trilinear lookup of the distance field phi (Eq. 17);
+//   - the SE(3) pose error xi = log(T_g^{-1} T_ee) (Eqs. 11-15) with the
 //     closed form V(theta)^{-1} = I - [w]x/2 + c(theta) [w]x^2,
 //     c(theta) = (1 - (theta/2) cot(theta/2)) / theta^2;
-//   - the tightened joint-limit violation of Eq. 17.
+//   - the tightened joint-limit violation of Eq. 21.
 #pragma once
 
 #include <cstdint>
@@ -30,7 +30,7 @@ struct RobotConst {
     float ca[kNJ], sa[kNJ];       // cos/sin of alpha_{i-1}
     float a[kNJ], d[kNJ], th0[kNJ];
     float flange_d;
-    float q_lo[kNJ], q_hi[kNJ];   // tightened boxes of Eq. 17
+    float q_lo[kNJ], q_hi[kNJ];   // tightened boxes of Eq. 21
     float qd_lo[kNJ], qd_hi[kNJ];
     float qdd_lo[kNJ], qdd_hi[kNJ];
     float sph_off[kMaxSpheres][3];
@@ -99,10 +99,11 @@ __device__ __forceinline__ void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32
     }
 }
 
-// u = ((x >> 8) + 0.5) 2^-24: exact in FP32, strictly inside (0, 1).
+// u = ((x >> 9) + 0.5) 2^-23: a 23-bit integer plus one half fits the 24-bit
+// significand, so u is exact in FP32 and strictly inside (0, 1).
 __device__ __forceinline__ float word_to_uniform(uint32_t x)
 {
-    return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    return (static_cast<float>(x >> 9) + 0.5f) * 1.1920928955078125e-7f;
 }
 
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1)
@@ -153,7 +154,7 @@ __device__ __forceinline__ Frame base_frame()
     return Frame{mk(1.f, 0.f, 0.f), mk(0.f, 1.f, 0.f), mk(0.f, 0.f, 1.f), mk(0.f, 0.f, 0.f)};
 }
 
-// T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d)  (modified DH, Eq. 1).
+// T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d)  (modified DH, Eq. 6).
 __device__ __forceinline__ void dh_step(Frame &F, float ca, float sa, float a, float d,
                                         float theta)
 {
@@ -198,28 +199,53 @@ __device__ __forceinline__ int cell(float g, float gmax, int n, float &f)
     return i;
 }
 
-// phi(p): trilinear interpolation of the voxel-centre samples (Eq. 14).
-template <typename T>
-__device__ __forceinline__ float phi_trilinear(const GridConst &g, f3 p)
+// Cell of a point: base voxel offset and fractions (clamped, Eq. 17 lookup).
+struct Cell { int base; float fx, fy, fz; };
+
+__device__ __forceinline__ Cell locate(const GridConst &g, f3 p)
 {
-    float fx, fy, fz;
-    const int ix = cell((p.x - g.ox) * g.inv_res - 0.5f, g.mx, g.nx, fx);
-    const int iy = cell((p.y - g.oy) * g.inv_res - 0.5f, g.my, g.ny, fy);
-    const int iz = cell((p.z - g.oz) * g.inv_res - 0.5f, g.mz, g.nz, fz);
+    Cell c;
+    const int ix = cell((p.x - g.ox) * g.inv_res - 0.5f, g.mx, g.nx, c.fx);
+    const int iy = cell((p.y - g.oy) * g.inv_res - 0.5f, g.my, g.ny, c.fy);
+    const int iz = cell((p.z - g.oz) * g.inv_res - 0.5f, g.mz, g.nz, c.fz);
+    c.base = (iz * g.ny + iy) * g.nx + ix;
+    return c;
+}
+
+// The 8 corner samples of a cell, in the order (x, y, z) = 000, 100, 010,
+// 110, 001, 101, 011, 111.
+template <typename T>
+__device__ __forceinline__ void corners(const GridConst &g, int base, float v[8])
+{
     const int sy = g.nx, sz = g.nx * g.ny;
-    const T *b = static_cast<const T *>(g.phi) + (iz * sz + iy * sy + ix);
-    const float c000 = grid_load(b), c100 = grid_load(b + 1);
-    const float c010 = grid_load(b + sy), c110 = grid_load(b + sy + 1);
-    const float c001 = grid_load(b + sz), c101 = grid_load(b + sz + 1);
-    const float c011 = grid_load(b + sz + sy), c111 = grid_load(b + sz + sy + 1);
-    const float c00 = fmaf(fx, c100 - c000, c000), c10 = fmaf(fx, c110 - c010, c010);
-    const float c01 = fmaf(fx, c101 - c001, c001), c11 = fmaf(fx, c111 - c011, c011);
+    const T *b = static_cast<const T *>(g.phi) + base;
+    v[0] = grid_load(b);          v[1] = grid_load(b + 1);
+    v[2] = grid_load(b + sy);     v[3] = grid_load(b + sy + 1);
+    v[4] = grid_load(b + sz);     v[5] = grid_load(b + sz + 1);
+    v[6] = grid_load(b + sz + sy); v[7] = grid_load(b + sz + sy + 1);
+}
+
+// Trilinear interpolation in x, then y, then z.
+__device__ __forceinline__ float interpolate(const float v[8], float fx, float fy, float fz)
+{
+    const float c00 = fmaf(fx, v[1] - v[0], v[0]), c10 = fmaf(fx, v[3] - v[2], v[2]);
+    const float c01 = fmaf(fx, v[5] - v[4], v[4]), c11 = fmaf(fx, v[7] - v[6], v[6]);
     const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
     return fmaf(fz, c1 - c0, c0);
 }
 
+// phi(p): trilinear interpolation of the voxel-centre samples (Eq. 17).
+template <typename T>
+__device__ __forceinline__ float phi_trilinear(const GridConst &g, f3 p)
+{
+    const Cell c = locate(g, p);
+    float v[8];
+    corners<T>(g, c.base, v);
+    return interpolate(v, c.fx, c.fy, c.fz);
+}
+
 // ----------------------------------------------------------------- SE(3)
-// xi = [v; w] = log(T_g^{-1} T) for T = (F.c1 F.c2 F.c3 | t), Eqs. 8-12.
+// xi = [v; w] = log(T_g^{-1} T) for T = (F.c1 F.c2 F.c3 | t), Eqs. 11-15.
 // Rg row-major, tg: goal pose.
 __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 c1, f3 c2,
                                            f3 c3, f3 t, float xi[6])
@@ -291,7 +317,7 @@ __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 
     xi[3] = w.x; xi[4] = w.y; xi[5] = w.z;
 }
 
-// 1/2 xi^T diag(Q) xi  (Eqs. 13, 22).
+// 1/2 xi^T diag(Q) xi  (Eqs. 16, 25).
 __device__ __forceinline__ float quad_cost(const float xi[6], const float *Q)
 {
     float s = 0.0f;
@@ -300,7 +326,7 @@ __device__ __forceinline__ float quad_cost(const float xi[6], const float *Q)
     return 0.5f * s;
 }
 
-// delta(x) of Eq. 17 on the tightened box [lo, hi].
+// delta(x) of Eq. 21 on the tightened box [lo, hi].
 __device__ __forceinline__ float limit_violation(float x, float lo, float hi)
 {
     return fmaxf(x - hi, 0.0f) + fminf(x - lo, 0.0f);

@@ -16,6 +16,8 @@ struct TileShape { int C, L; };
 // Shapes with an instantiated kernel, in order of preference for a horizon.
 constexpr TileShape kShapes[] = {{1, 16}, {1, 32}, {3, 16}, {2, 32}, {4, 32}, {8, 32}};
 
+// Kernel for a tile shape and storage type, with its dynamic shared memory
+// limit raised to iteration_smem_bytes(C) (done once per kernel).
 IterKernel iteration_kernel_f32(int C, int L, bool trace);
 IterKernel iteration_kernel_f16(int C, int L, bool trace);
 IterKernel iteration_kernel_bf16(int C, int L, bool trace);

@@ -2,43 +2,61 @@
 //
 // Work decomposition.  A warp tile holds R = 32 / L roll-outs; each roll-out
 // occupies L lanes and each lane owns C consecutive time steps
-// k = l*C .. l*C + C-1 (H <= C*L).  Because the dynamics of Eq. 2 are a
+// k = l*C .. l*C + C-1 (H <= C*L).  Because the dynamics of Eq. 7 are a
 // double integrator over the sampled accelerations, the states are prefix
 // sums over k:
 //     qd_{k+1} = qd_0 + dt A_{k+1},             A_k = sum_{i<k} u_i
 //     q_{k+1}  = q_0 + (k+1) dt qd_0 + dt^2 B_{k+1},  B_k = sum_{i=1..k} A_i,
 // computed with two segmented warp scans, so every (m, k) step is
 // independent afterwards.  Lane step k evaluates the control terms of u_k
-// (Eqs. 18, 20) and the state terms of q_{k+1}, qd_{k+1} (Eqs. 13, 16, 18,
-// 21) or, for k+1 = H, the terminal cost (Eq. 22).  The state terms of
+// (Eqs. 22, 23) and the state terms of q_{k+1}, qd_{k+1} (Eqs. 16, 19-20, 22,
+// 24) or, for k+1 = H, the terminal cost (Eq. 25).  The state terms of
 // k = 0 depend only on (q_0, qd_0) and are the same for every roll-out: one
 // warp computes them once and they are added to S at the end; they cancel
-// in the weights of Eq. 25.
+// in the weights of Eq. 29.
 //
-// Soft-min (Eqs. 25-26).  Each warp keeps a running minimum m, sum
+// The sampled perturbations of a lane's steps are kept in shared memory
+// ([warp][step][joint][lane], conflict-free) from sampling to the weighted
+// sum, so the per-step body is not unrolled over C; the spheres of a link
+// are looked up four at a time so their 32 gathers are in flight together.
+//
+// Soft-min (Eqs. 29-30).  Each warp keeps a running minimum m, sum
 // z = sum exp(-(S - m)/lambda) and accumulator sum exp(-(S - m)/lambda) eps,
-// rescaled when m drops (the eps of a roll-out never leave registers).
-// Warps merge into a block partial; the last block to finish (atomic ticket
-// after a fence, no waiting) merges the block partials in block order and
-// writes U* = Ubar + acc / z.
+// rescaled when m drops.  Warps merge into a block partial.  Blocks form
+// groups of kGroup; the last block of a group to finish (atomic ticket after
+// a fence) merges the group's partials, and the last group to finish merges
+// the group partials and writes U* = Ubar + acc / z.  No block ever waits
+// for another, and the merge order is fixed, so results are deterministic
+// for a given launch shape.
 #pragma once
 
 #include "smpc_device.cuh"
 
 namespace pm {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 128;
 constexpr int kWarps = kBlock / 32;
-constexpr int kMaxBlocks = 2048;
+constexpr int kGroup = 32;                 // blocks per first-level merge
+constexpr int kMaxBlocks = 4096;
+constexpr int kMaxGroups = kMaxBlocks / kGroup;
 constexpr int kTraceCols = 8;   // pose, env, self, lim_q, lim_qd, lim_qdd, smooth, ns
+constexpr int kSphereBatch = 4;
+
+// Dynamic shared memory of an iteration kernel with C steps per lane: the
+// perturbations and the soft-min accumulators, [kWarps][C][7][32] each.
+constexpr size_t iteration_smem_bytes(int C)
+{
+    return 2u * kWarps * C * kNJ * 32 * sizeof(float);
+}
 
 struct IterArgs {
     CallInputs in;              // q0, qd0, T_goal (device), sigma
     const float *Ubar;          // [H][7]
     float *Uout;                // [H][7], may alias Ubar
     float *costs;               // [K] or null
-    float *part;                // [gridDim.x][2 + H*7]
-    unsigned *counter;          // zero between launches
+    float *part;                // block partials [gridDim.x][2 + H*7]
+    float *gpart;               // group partials [groups][2 + H*7]
+    unsigned *counters;         // [0] = groups done, [1 + g] = blocks done in group g
     float *c0;                  // [0] = k = 0 state terms, [1] = min S
     float *trace;               // [K][H+1][8] (trace kernels only)
     int K, H;
@@ -47,7 +65,7 @@ struct IterArgs {
 };
 
 // ------------------------------------------------------------ cost terms
-// Control terms at step k (Eqs. 18, 20): w_qdd delta(qdd)^2 + w_s qdd^2.
+// Control terms at step k (Eqs. 22, 23): w_qdd delta(qdd)^2 + w_s qdd^2.
 template <bool TRACE>
 __device__ __forceinline__ float control_cost(const RobotConst &rc, const float *u, float *tr)
 {
@@ -64,7 +82,35 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
     return lim + sm;
 }
 
-// State terms at a step (Eqs. 13, 16, 18, 21), or the terminal cost (Eq. 22).
+// sum over spheres s in [b, e) of frame F of max(0, d_act - (phi(p_s) - r_s))^2
+// (Eqs. 17, 19), four spheres per batch with all gathers issued together.
+template <typename GT>
+__device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
+                                          const Frame &F, int b, int e)
+{
+    float env = 0.f;
+    for (int s0 = b; s0 < e; s0 += kSphereBatch) {
+        Cell c[kSphereBatch];
+#pragma unroll
+        for (int i = 0; i < kSphereBatch; ++i) {
+            const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
+            c[i] = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
+        }
+        float v[kSphereBatch][8];
+#pragma unroll
+        for (int i = 0; i < kSphereBatch; ++i) corners<GT>(g, c[i].base, v[i]);
+#pragma unroll
+        for (int i = 0; i < kSphereBatch; ++i) {
+            const int s = min(s0 + i, e - 1);
+            const float phi = interpolate(v[i], c[i].fx, c[i].fy, c[i].fz);
+            const float dl = fmaxf(rc.d_act - (phi - rc.sph_r[s]), 0.f);
+            env = (s0 + i < e) ? fmaf(dl, dl, env) : env;
+        }
+    }
+    return env;
+}
+
+// State terms at a step (Eqs. 16, 19-20, 22, 24), or the terminal cost (Eq. 25).
 // Forward kinematics runs frame by frame; the spheres of each frame are
 // looked up as soon as it is known.
 template <typename GT, bool TRACE>
@@ -77,13 +123,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
 #pragma unroll
     for (int j = 0; j < kNJ; ++j) {
         dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
-        if (!terminal) {
-            for (int s = rc.link_begin[j + 1]; s < rc.link_begin[j + 2]; ++s) {
-                const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-                const float dl = fmaxf(rc.d_act - (phi_trilinear<GT>(g, p) - rc.sph_r[s]), 0.f);
-                env = fmaf(dl, dl, env);
-            }
-        }
+        if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2]);
     }
     const f3 tee = axpy(rc.flange_d, F.c3, F.t);
     float xi[6];
@@ -115,7 +155,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
 // k = 0 state terms, computed by one warp: lane p takes spheres p, p+32;
 // lane 0 adds the pose, joint-limit and null-space terms.
 template <typename GT>
-__device__ void initial_state_cost_warp(const RobotConst &rc, const GridConst &g,
+__device__ __noinline__ static void initial_state_cost_warp(const RobotConst &rc, const GridConst &g,
                                         const InstanceState &st, float *out)
 {
     const int lane = threadIdx.x & 31;
@@ -175,114 +215,143 @@ __device__ __forceinline__ float weight_factor(float m_from, float m_to, float i
     return (m_from == CUDART_INF_F) ? 0.f : expf((m_to - m_from) * inv_lambda);
 }
 
+// Merge n partials (m, z, acc[na]) at src + i*stride (i < n) into dst with a
+// common minimum; the whole block calls this.  Deterministic order over i.
+__device__ __noinline__ static void merge_partials(const float *src, int n, int stride, int na, float inv_lambda,
+                               float *s_f, float *s_red, float *dst_m, float *dst_z,
+                               float *dst_acc)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float lm = CUDART_INF_F;
+    for (int i = tid; i < n; i += kBlock) lm = fminf(lm, __ldcg(src + static_cast<size_t>(i) * stride));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
+    if (lane == 0) s_red[warp] = lm;
+    __syncthreads();
+    float M = CUDART_INF_F;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) M = fminf(M, s_red[w]);
+    __syncthreads();
+    for (int i = tid; i < n; i += kBlock) {
+        const float *P = src + static_cast<size_t>(i) * stride;
+        s_f[i] = weight_factor(__ldcg(P), M, inv_lambda);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float z = 0.f;
+        for (int i = 0; i < n; ++i) z = fmaf(s_f[i], __ldcg(src + static_cast<size_t>(i) * stride + 1), z);
+        *dst_m = M;
+        *dst_z = z;
+    }
+    for (int t = tid; t < na; t += kBlock) {
+        float acc = 0.f;
+        for (int i = 0; i < n; ++i) acc = fmaf(s_f[i], __ldcg(src + static_cast<size_t>(i) * stride + 2 + t), acc);
+        dst_acc[t] = acc;
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ kernel
 template <int C, int L, typename GT, bool TRACE>
-__global__ void __launch_bounds__(kBlock, 2)
-smpc_iteration_kernel(const RobotConst rc, const GridConst g, const IterArgs a)
+__global__ void __launch_bounds__(kBlock, 5)
+smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
+                      const __grid_constant__ IterArgs a)
 {
     static_assert(32 % L == 0 && C >= 1, "tile shape");
     constexpr int R = 32 / L;
+    extern __shared__ float s_dyn[];
+    typedef float PerWarp[C][kNJ][32];
+    PerWarp *s_eps = reinterpret_cast<PerWarp *>(s_dyn);
+    PerWarp *s_acc = reinterpret_cast<PerWarp *>(s_dyn + kWarps * C * kNJ * 32);
     __shared__ float s_state[kStateFloats];
+    __shared__ float s_blk[C * L * kNJ];
     __shared__ float s_wm[kWarps], s_wz[kWarps];
-    __shared__ float s_acc[C * L * kNJ];
-    __shared__ float s_f[kMaxBlocks];
+    __shared__ float s_f[kGroup > kMaxGroups ? kGroup : kMaxGroups];
     __shared__ float s_red[kWarps];
-    __shared__ unsigned s_last;
+    __shared__ float s_mz[2];
+    __shared__ unsigned s_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int seg = lane / L, sl = lane % L;
     const int H = a.H;
     static_assert(kBlock >= 44, "state loader needs 44 threads");
     load_state(a.in, s_state);
-    for (int i = tid; i < C * L * kNJ; i += kBlock) s_acc[i] = 0.f;
+    for (int i = tid; i < C * L * kNJ; i += kBlock) s_blk[i] = 0.f;
+#pragma unroll
+    for (int s = 0; s < C; ++s)
+#pragma unroll
+        for (int j = 0; j < kNJ; ++j) s_acc[warp][s][j][lane] = 0.f;
     __syncthreads();
     const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
 
     if (!TRACE && blockIdx.x == 0 && warp == 0) initial_state_cost_warp<GT>(rc, g, st, a.c0);
 
     float run_m = CUDART_INF_F, run_z = 0.f;
-    float acc[C][kNJ];
-#pragma unroll
-    for (int s = 0; s < C; ++s)
-#pragma unroll
-        for (int j = 0; j < kNJ; ++j) acc[s][j] = 0.f;
-
+    const float dt = a.dt, dt2 = a.dt * a.dt;
     const int n_tiles = (a.K + R - 1) / R;
     for (int tile = blockIdx.x * kWarps + warp; tile < n_tiles; tile += gridDim.x * kWarps) {
         const int m = tile * R + seg;
         const bool active = m < a.K;
 
-        // Alg. 1 lines 3-4: eps ~ D, u = ubar + eps
-        float eps[C][kNJ], u[C][kNJ];
+        // sample and perturb (Algorithm 1, Eq. 27): eps ~ D, u = ubar + eps;
+        // chunk sums T = sum_s u_s and TB = sum_s sum_{s'<=s} u_s' for the scans
+        float T[kNJ], TB[kNJ];
 #pragma unroll
+        for (int j = 0; j < kNJ; ++j) { T[j] = 0.f; TB[j] = 0.f; }
+#pragma unroll 1
         for (int s = 0; s < C; ++s) {
             const int k = sl * C + s;
-            if (active && k < H) {
-                float z[8];
+            float z[8];
+            const bool live = active && k < H;
+            if (live) {
                 step_normals(a.seed_lo, a.seed_hi, a.iter, static_cast<uint32_t>(m),
                              static_cast<uint32_t>(k), z);
+            }
 #pragma unroll
-                for (int j = 0; j < kNJ; ++j) {
-                    eps[s][j] = st.sigma[j] * z[j];
-                    u[s][j] = __ldg(a.Ubar + k * kNJ + j) + eps[s][j];
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kNJ; ++j) { eps[s][j] = 0.f; u[s][j] = 0.f; }
+            for (int j = 0; j < kNJ; ++j) {
+                const float e = live ? st.sigma[j] * z[j] : 0.f;
+                const float u = live ? __ldg(a.Ubar + k * kNJ + j) + e : 0.f;
+                s_eps[warp][s][j][lane] = e;
+                T[j] += u;
+                TB[j] += T[j];
             }
         }
 
-        // Alg. 1 line 5: roll-out by two segmented prefix scans
+        // roll-out (Eq. 7) by two segmented prefix scans
         float A0[kNJ], B0[kNJ];
-        {
-            float T[kNJ], TB[kNJ];
+        seg_exclusive_scan<L>(T, A0, sl);
 #pragma unroll
-            for (int j = 0; j < kNJ; ++j) {
-                float run = 0.f;
-#pragma unroll
-                for (int s = 0; s < C; ++s) run += u[s][j];
-                T[j] = run;
-            }
-            seg_exclusive_scan<L>(T, A0, sl);
-#pragma unroll
-            for (int j = 0; j < kNJ; ++j) {
-                float run = 0.f, tb = 0.f;
-#pragma unroll
-                for (int s = 0; s < C; ++s) { run += u[s][j]; tb += run; }
-                TB[j] = fmaf(static_cast<float>(C), A0[j], tb);
-            }
-            seg_exclusive_scan<L>(TB, B0, sl);
-        }
+        for (int j = 0; j < kNJ; ++j) TB[j] = fmaf(static_cast<float>(C), A0[j], TB[j]);
+        seg_exclusive_scan<L>(TB, B0, sl);
 
-        // Alg. 1 lines 6-7: kinematics and costs of each of my steps
+        // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25)
         float lsum = 0.f, lcomp = 0.f;
         float runU[kNJ], runB[kNJ];
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) { runU[j] = 0.f; runB[j] = B0[j]; }
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < C; ++s) {
             const int k = sl * C + s;
-            float q[kNJ], qd[kNJ];
-            const float kp_dt = static_cast<float>(k + 1) * a.dt;
-            const float dt2 = a.dt * a.dt;
+            if (!(active && k < H)) break;
+            float u[kNJ], q[kNJ], qd[kNJ];
+            const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                runU[j] += u[s][j];
+                u[j] = __ldg(a.Ubar + k * kNJ + j) + s_eps[warp][s][j][lane];
+                runU[j] += u[j];
                 const float A = A0[j] + runU[j];           // A_{k+1}
                 runB[j] += A;                               // B_{k+1}
-                qd[j] = fmaf(a.dt, A, st.qd0[j]);
+                qd[j] = fmaf(dt, A, st.qd0[j]);
                 q[j] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
             }
-            if (active && k < H) {
-                float *tr_u = nullptr, *tr_x = nullptr;
-                if (TRACE) {
-                    tr_u = a.trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
-                    tr_x = tr_u + kTraceCols;
-                }
-                float step = control_cost<TRACE>(rc, u[s], tr_u);
-                step += state_cost<GT, TRACE>(rc, g, st, q, qd, k + 1 == H, tr_x);
-                kahan_add(lsum, lcomp, step);
+            float *tr_u = nullptr, *tr_x = nullptr;
+            if (TRACE) {
+                tr_u = a.trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
+                tr_x = tr_u + kTraceCols;
             }
+            float step = control_cost<TRACE>(rc, u, tr_u);
+            step += state_cost<GT, TRACE>(rc, g, st, q, qd, k + 1 == H, tr_x);
+            kahan_add(lsum, lcomp, step);
         }
 
         // S'^(m): compensated sum over the segment's lanes
@@ -300,16 +369,18 @@ smpc_iteration_kernel(const RobotConst rc, const GridConst g, const IterArgs a)
         if (TRACE) continue;
         if (active && sl == 0 && a.costs) a.costs[m] = S;
 
-        // online soft-min accumulation (Eqs. 25-26)
+        // online soft-min accumulation (Eqs. 29-30)
         if (active) {
             const float nm = fminf(run_m, S);
             const float f_old = weight_factor(run_m, nm, a.inv_lambda);
             const float f_new = expf((nm - S) * a.inv_lambda);
             run_z = fmaf(run_z, f_old, f_new);
-#pragma unroll
+#pragma unroll 1
             for (int s = 0; s < C; ++s)
 #pragma unroll
-                for (int j = 0; j < kNJ; ++j) acc[s][j] = fmaf(acc[s][j], f_old, f_new * eps[s][j]);
+                for (int j = 0; j < kNJ; ++j)
+                    s_acc[warp][s][j][lane] = fmaf(s_acc[warp][s][j][lane], f_old,
+                                                   f_new * s_eps[warp][s][j][lane]);
             run_m = nm;
         }
     }
@@ -324,12 +395,13 @@ smpc_iteration_kernel(const RobotConst rc, const GridConst g, const IterArgs a)
         const float fa = weight_factor(run_m, nm, a.inv_lambda);
         const float fb = weight_factor(om, nm, a.inv_lambda);
         run_z = run_z * fa + oz * fb;
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < C; ++s)
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                const float o = __shfl_xor_sync(0xffffffffu, acc[s][j], off);
-                acc[s][j] = acc[s][j] * fa + o * fb;
+                const float mine = s_acc[warp][s][j][lane];
+                const float o = __shfl_xor_sync(0xffffffffu, mine, off);
+                s_acc[warp][s][j][lane] = mine * fa + o * fb;
             }
         run_m = nm;
     }
@@ -343,19 +415,19 @@ smpc_iteration_kernel(const RobotConst rc, const GridConst g, const IterArgs a)
     const float fw = weight_factor(run_m, Mb, a.inv_lambda);
     for (int w = 0; w < kWarps; ++w) {
         if (warp == w && seg == 0) {
-#pragma unroll
             for (int s = 0; s < C; ++s) {
                 const int k = sl * C + s;
                 if (k < H) {
 #pragma unroll
                     for (int j = 0; j < kNJ; ++j)
-                        s_acc[k * kNJ + j] = fmaf(fw, acc[s][j], s_acc[k * kNJ + j]);
+                        s_blk[k * kNJ + j] = fmaf(fw, s_acc[warp][s][j][lane], s_blk[k * kNJ + j]);
                 }
             }
         }
         __syncthreads();
     }
-    const int stride = 2 + H * kNJ;
+    const int na = H * kNJ;
+    const int stride = 2 + na;
     float *P = a.part + static_cast<size_t>(blockIdx.x) * stride;
     if (tid == 0) {
         float zb = 0.f;
@@ -363,56 +435,42 @@ smpc_iteration_kernel(const RobotConst rc, const GridConst g, const IterArgs a)
         P[0] = Mb;
         P[1] = zb;
     }
-    for (int i = tid; i < H * kNJ; i += kBlock) P[2 + i] = s_acc[i];
+    for (int i = tid; i < na; i += kBlock) P[2 + i] = s_blk[i];
 
-    // last block to arrive merges the partials (no block waits for another)
+    // first level: the last block of the group merges the group's partials
+    const int grp = blockIdx.x / kGroup;
+    const int g0 = grp * kGroup;
+    const int gn = min(kGroup, static_cast<int>(gridDim.x) - g0);
+    const int n_groups = (gridDim.x + kGroup - 1) / kGroup;
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    if (tid == 0) s_flag = (atomicAdd(a.counters + 1 + grp, 1u) == static_cast<unsigned>(gn - 1)) ? 1u : 0u;
     __syncthreads();
-    if (!s_last) return;
+    if (!s_flag) return;
     __threadfence();
+    float *G = a.gpart + static_cast<size_t>(grp) * stride;
+    merge_partials(a.part + static_cast<size_t>(g0) * stride, gn, stride, na, a.inv_lambda, s_f,
+                   s_red, G, G + 1, G + 2);
+    if (tid == 0) a.counters[1 + grp] = 0u;
 
-    const int nb = gridDim.x;
-    float lm = CUDART_INF_F;
-    for (int b = tid; b < nb; b += kBlock) lm = fminf(lm, __ldcg(a.part + static_cast<size_t>(b) * stride));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
-    if (lane == 0) s_red[warp] = lm;
+    // second level: the last group merges the group partials into U*
+    __threadfence();
     __syncthreads();
-    float M = CUDART_INF_F;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) M = fminf(M, s_red[w]);
+    if (tid == 0) s_flag = (atomicAdd(a.counters, 1u) == static_cast<unsigned>(n_groups - 1)) ? 1u : 0u;
     __syncthreads();
-
-    float lz = 0.f;
-    for (int b = tid; b < nb; b += kBlock) {
-        const float *Pb = a.part + static_cast<size_t>(b) * stride;
-        const float f = weight_factor(__ldcg(Pb), M, a.inv_lambda);
-        s_f[b] = f;
-        lz = fmaf(f, __ldcg(Pb + 1), lz);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lz += __shfl_xor_sync(0xffffffffu, lz, off);
-    if (lane == 0) s_red[warp] = lz;
-    __syncthreads();
-    float Z = 0.f;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) Z += s_red[w];
-    const float invZ = 1.0f / Z;
-
-    for (int i = tid; i < H * kNJ; i += kBlock) {
-        float s = 0.f;
-        for (int b = 0; b < nb; ++b)
-            s = fmaf(s_f[b], __ldcg(a.part + static_cast<size_t>(b) * stride + 2 + i), s);
-        a.Uout[i] = a.Ubar[i] + s * invZ;
-    }
-
+    if (!s_flag) return;
+    __threadfence();
+    merge_partials(a.gpart, n_groups, stride, na, a.inv_lambda, s_f, s_red, &s_mz[0], &s_mz[1],
+                   s_blk);
+    const float invZ = 1.0f / s_mz[1];
+    for (int i = tid; i < na; i += kBlock) a.Uout[i] = a.Ubar[i] + s_blk[i] * invZ;
     const float c0 = __ldcg(a.c0);
-    if (tid == 0) a.c0[1] = M + c0;
+    if (tid == 0) {
+        a.c0[1] = s_mz[0] + c0;
+        a.counters[0] = 0u;
+    }
     if (a.costs)
         for (int i = tid; i < a.K; i += kBlock) a.costs[i] = __ldcg(a.costs + i) + c0;
-    if (tid == 0) *a.counter = 0u;
 }
 
 } // namespace pm

@@ -2,7 +2,7 @@
 
 Tolerances (written once, used by every parity test):
   S_REL   per-roll-out costs S^(m), relative            1e-4
-  U_ABS   updated controls U* (Eq. 26), absolute          1e-5
+  U_ABS   updated controls U* (Eq. 30), absolute          1e-5
   NOISE   normals / eps, |gpu - oracle| <= NOISE_ABS + NOISE_REL |oracle|
   U_ISO   U* recomputed in FP64 from the GPU's own FP32 costs vs the GPU U*;
           this isolates the soft-min reduction from the cost arithmetic  1e-6
@@ -51,7 +51,7 @@ class Scene:
 
 
 def fp64_update_from_costs(S, eps, Ubar, lam):
-    """Eqs. 25-26 in FP64 from given costs (used to isolate the reduction)."""
+    """Eqs. 29-30 in FP64 from given costs (used to isolate the reduction)."""
     S = np.asarray(S, dtype=np.float64)
     w = np.exp(-(S - S.min()) / lam)
     w /= w.sum()

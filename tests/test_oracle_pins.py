@@ -90,10 +90,16 @@ def test_philox_matches_triton_interpreter():
         assert np.array_equal(tri, orc), f"seed {seed:#x}"
 
 
-def test_uniform_map_endpoints():
-    assert oracle.word_to_uniform(0) == 2.0**-25
-    assert oracle.word_to_uniform(0xFFFFFFFF) == 1.0 - 2.0**-25
-    assert oracle.word_to_uniform(0x80000000) == 0.5 + 2.0**-25
+def test_uniform_map_endpoints_and_fp32_exactness():
+    assert oracle.word_to_uniform(0) == 2.0**-24
+    assert oracle.word_to_uniform(0xFFFFFFFF) == 1.0 - 2.0**-24
+    assert oracle.word_to_uniform(0x80000000) == 0.5 + 2.0**-24
+    # every value is a float32 number, so an FP32 implementation draws it exactly
+    xs = np.random.default_rng(0).integers(0, 2**32, 20000, dtype=np.uint64).tolist()
+    xs += [0, 1, 2**31 - 1, 2**31, 2**32 - 512, 2**32 - 1]
+    for x in xs:
+        u = oracle.word_to_uniform(x)
+        assert float(np.float32(u)) == u and 0.0 < u < 1.0
 
 
 def test_box_muller_invariants():

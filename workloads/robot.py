@@ -3,7 +3,7 @@
 The kinematic chain is the one the workloads are specified on (a Panda-class
 arm): per joint i = 1..7 the modified-DH tuple (a_{i-1}, d_i, alpha_{i-1}) and
 a fixed flange translation of 0.107 m along the last z axis.  The paper gives
-the chain only in words (forward kinematics, Sec. IV-A, Eq. 1); the numbers
+the chain only in words (forward kinematics, Sec. IV-A, Eq. 6); the numbers
 below are the workload's.
 
 The sphere model (Sec. IV-B-2, Fig. 2: n_s spheres with centres fixed in link
@@ -122,7 +122,7 @@ def default_cost_params(q_ref):
     with q_ref = start pose.
 
     The pose weights set the cost scale against the temperature lambda = 0.05
-    of Eq. 25: at this scale the weights keep an effective sample size of
+    of Eq. 29: at this scale the weights keep an effective sample size of
     roughly 20-75 % of K, and the FP32 rounding of S moves U* by well under
     1e-5 (ten times larger pose weights make the update an argmin and push
     FP32 rounding of S above that).
