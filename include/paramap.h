@@ -181,6 +181,31 @@ pm_status pm_replan(pm_ctx *ctx, float *q, float *qd, const float *T_goal, float
                     float *u0_out, float *best_cost, void *cuda_stream);
 
 /*
+ * pm_smpc_iterate without any allocation (the paper has no counterpart; this
+ * serves callers that may not allocate device memory while running, such as
+ * a fixed-rate control loop that forbids allocation after start-up or a
+ * process whose device memory another allocator has fully reserved).
+ * Same arguments and result as pm_smpc_iterate, except that q0, qd0, T_goal,
+ * U and costs_out (if not NULL) must be device memory; sigma is host memory.
+ * Only enqueues work on the stream.
+ * Scratch: the soft-min merge partials and counters live in one 2 MiB
+ * static device array that every GPU loading the library holds until exit.
+ * The array's device address is resolved with cudaGetSymbolAddress on the
+ * first call on each device, with that device current; make that first call
+ * before any stream capture.  Every call shares the array and the merge
+ * counters are cleared at the start of each call, so calls must not overlap
+ * on the GPU (calls on different streams, or from different contexts, that
+ * run concurrently race on the array).  The launch uses fewer blocks when
+ * the partials of the usual grid do not fit the array (for H above about
+ * 128); H up to PM_MAX_HORIZON is accepted.
+ * Errors: PM_EINVAL (as pm_smpc_iterate, or a host pointer), PM_ECUDA.
+ */
+pm_status pm_smpc_iterate_noalloc(pm_ctx *ctx, const float *q0, const float *qd0,
+                                  const float *T_goal, float *U, int K, int H, float dt,
+                                  float lambda, const float *sigma, uint64_t seed,
+                                  uint32_t iter_index, float *costs_out, void *cuda_stream);
+
+/*
  * Diagnostics used by the parity tests (same device code as the hot path).
  *
  * pm_philox4x32_10: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key) for

@@ -20,7 +20,8 @@ from ._abi import (PM_BF16, PM_F16, PM_F32, PmCostParams, PmError, PmGridDesc, P
 
 __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
-    "create", "set_distance_field", "smpc_iterate", "replan", "philox4x32_10",
+    "create", "set_distance_field", "smpc_iterate", "smpc_iterate_noalloc", "replan",
+    "philox4x32_10",
     "sample_noise", "rollout_trace", "profile_enable", "profile_read", "destroy",
     "last_error", "Planner",
 ]
@@ -147,6 +148,21 @@ def smpc_iterate(ctx, q0, qd0, T_goal, U, K, dt, lam, sigma, seed, iter_index,
                                  _stream(stream)), ctx)
 
 
+def smpc_iterate_noalloc(ctx, q0, qd0, T_goal, U, K, dt, lam, sigma, seed, iter_index,
+                         costs_out=None, stream=None):
+    """pm_smpc_iterate_noalloc: as smpc_iterate with every array in device memory
+    and the merge scratch in the library's static device array, for callers
+    that may not allocate device memory while running.  Enqueues only."""
+    H = int(U.shape[0])
+    sigma = _f32(sigma, 7)
+    _check(lib().pm_smpc_iterate_noalloc(ctx, _ptr(q0, n=7), _ptr(qd0, n=7), _ptr(T_goal, n=16),
+                                         _ptr(U, n=7 * H, writable=True), int(K), H, float(dt),
+                                         float(lam), _ptr(sigma), C.c_uint64(int(seed)),
+                                         C.c_uint32(int(iter_index)),
+                                         _ptr(costs_out, n=int(K), writable=True),
+                                         _stream(stream)), ctx)
+
+
 def replan(ctx, q, qd, T_goal, U, K, n_iters, dt, lam, sigma, seed, replan_index,
            u0_out=None, best_cost=None, stream=None):
     """pm_replan: q, qd advanced and U shifted in place."""
@@ -222,6 +238,9 @@ class Planner:
 
     def smpc_iterate(self, *a, **kw):
         smpc_iterate(self.ctx, *a, **kw)
+
+    def smpc_iterate_noalloc(self, *a, **kw):
+        smpc_iterate_noalloc(self.ctx, *a, **kw)
 
     def replan(self, *a, **kw):
         replan(self.ctx, *a, **kw)

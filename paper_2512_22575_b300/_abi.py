@@ -45,6 +45,8 @@ SIGNATURES = {
     "pm_set_distance_field": (C.c_int, [_V, _V, C.c_int]),
     "pm_smpc_iterate": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_float, C.c_float, _V,
                                   C.c_uint64, C.c_uint32, _V, _V]),
+    "pm_smpc_iterate_noalloc": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_float,
+                                          C.c_float, _V, C.c_uint64, C.c_uint32, _V, _V]),
     "pm_replan": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
                             _V, C.c_uint64, C.c_uint32, _V, _V, _V]),
     "pm_philox4x32_10": (C.c_int, [_V, C.c_uint64, _V, C.c_size_t, _V]),

@@ -764,3 +764,114 @@ void pm_destroy(pm_ctx *c)
 }
 
 } // extern "C"
+
+// ============================================================ no-allocation
+// pm_smpc_iterate_noalloc: the same iteration kernel, with its scratch
+// (block and group partials of the soft-min merge, merge counters, the
+// k = 0 state term) in one file-scope device array instead of memory the
+// context allocates on demand.  It is for callers that must not allocate
+// device memory once they are running -- for instance a fixed-rate control
+// loop that forbids allocation after start-up, or a process whose device
+// memory is fully reserved by another allocator.
+namespace {
+
+constexpr size_t kStaticScratchFloats = 512 * 1024;   // 2 MiB, held by every GPU that loads us
+constexpr size_t kStaticHeaderFloats = 256;           // c0 [0, 32), counters [32, 32 + 1 + kMaxGroups)
+static_assert(32 + 1 + kMaxGroups <= kStaticHeaderFloats, "static scratch header");
+
+static __device__ __align__(256) float g_static_scratch[kStaticScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on `device` (the caller made it current).
+// Resolved once per device and cached.
+pm_status static_scratch(pm_ctx *c, int device, float **out)
+{
+    if (device < 0 || device >= kMaxDevices) return set_err(c, PM_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return set_err(c, PM_ECUDA, "cudaGetSymbolAddress(static scratch) on device %d: %s", device,
+                           cudaGetErrorString(e));
+        g_static_addr[device] = static_cast<float *>(p);
+    }
+    *out = g_static_addr[device];
+    return PM_OK;
+}
+
+} // namespace
+
+extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const float *qd0,
+                                             const float *T_goal, float *U, int K, int H, float dt,
+                                             float lambda, const float *sigma, uint64_t seed,
+                                             uint32_t iter_index, float *costs_out, void *cuda_stream)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    pm_status st = check_call(c, q0, qd0, T_goal, U, K, H, dt, lambda, sigma, true);
+    if (st != PM_OK) return st;
+    if (!is_device_ptr(q0) || !is_device_ptr(qd0) || !is_device_ptr(T_goal) || !is_device_ptr(U) ||
+        (costs_out && !is_device_ptr(costs_out)))
+        return set_err(c, PM_EINVAL, "pm_smpc_iterate_noalloc needs q0, qd0, T_goal, U and costs_out in device memory");
+    float *scratch = nullptr;
+    st = static_scratch(c, c->device, &scratch);
+    if (st != PM_OK) return st;
+
+    const TileShape sh = pick_shape(H);
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
+    if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d", sh.C, sh.L);
+    const size_t smem = iteration_smem_bytes(sh.C);
+    const int per_sm = resident_blocks_per_sm(fn, smem);
+    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
+    const int R = 32 / sh.L;
+    const long long tiles = (static_cast<long long>(K) + R - 1) / R;
+    const long long need = (tiles + kWarps - 1) / kWarps;
+    const long long resident = static_cast<long long>(c->n_sm) * per_sm;
+    long long nb = std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)}));
+    // fewer, longer-running blocks when the partials would not fit the array
+    const size_t stride = 2 + static_cast<size_t>(H) * kNJ;
+    auto fits = [&](long long n) {
+        const size_t groups = static_cast<size_t>((n + kGroup - 1) / kGroup);
+        return kStaticHeaderFloats + (groups + static_cast<size_t>(n)) * stride <= kStaticScratchFloats;
+    };
+    while (nb > 1 && !fits(nb)) --nb;
+    if (!fits(nb))
+        return set_err(c, PM_EINVAL, "H=%d needs more than the %zu-float static scratch", H, kStaticScratchFloats);
+
+    cudaStream_t s = pick_stream(c, cuda_stream);
+    float *c0 = scratch;
+    unsigned *counters = reinterpret_cast<unsigned *>(scratch + 32);
+    float *gpart = scratch + kStaticHeaderFloats;
+    float *part = gpart + static_cast<size_t>((nb + kGroup - 1) / kGroup) * stride;
+    // the array keeps the previous call's contents: the merge counters must start at zero
+    PM_CUDA(c, cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + kMaxGroups), s));
+
+    IterArgs a{};
+    a.in.q0 = q0;
+    a.in.qd0 = qd0;
+    a.in.Tg = T_goal;
+    for (int j = 0; j < 8; ++j) a.in.sigma[j] = j < kNJ ? sigma[j] : 0.f;
+    a.Ubar = U;
+    a.Uout = U;
+    a.costs = costs_out;
+    a.part = part;
+    a.gpart = gpart;
+    a.counters = counters;
+    a.c0 = c0;
+    a.trace = nullptr;
+    a.K = K;
+    a.H = H;
+    a.seed_lo = static_cast<uint32_t>(seed & 0xffffffffu);
+    a.seed_hi = static_cast<uint32_t>(seed >> 32);
+    a.iter = iter_index;
+    a.dt = dt;
+    a.inv_lambda = 1.0f / lambda;
+    fn<<<static_cast<int>(nb), kBlock, smem, s>>>(c->rc, grid_const(c), a);
+    PM_CUDA(c, cudaGetLastError());
+    return PM_OK;
+}

@@ -1,0 +1,69 @@
+"""pm_smpc_iterate_noalloc against pm_smpc_iterate, through the C ABI.
+
+The no-allocation entry point serves callers that may not allocate device
+memory once they are running (a fixed-rate control loop that forbids
+allocation after start-up, or a process whose device memory another
+allocator has fully reserved).  Its scratch is a static device array shared
+by every call, so these tests check two calls in a row: leftover contents of
+the array from the first call must not change the second.  They run last
+(file name) and also pass on their own in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from parity_common import S_REL, SIGMA, U_ABS, Scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2512_22575_b300 as pm  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return Scene("cfg1_seed4")
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+def _run(p, entry, sc, U0, K, seed, it):
+    U = _dev(U0)
+    S = torch.empty(K, dtype=torch.float32, device=DEV)
+    entry(_dev(sc.q0), _dev(sc.qd0), _dev(sc.T.ravel()), U, K, 0.02, 0.05, SIGMA, seed, it,
+          costs_out=S)
+    torch.cuda.synchronize()
+    return U.cpu().numpy(), S.cpu().numpy()
+
+
+@pytest.mark.parametrize("K,H", [(256, 32), (4096, 64), (300, 200)])
+def test_noalloc_matches_iterate_on_two_calls_in_a_row(scene, K, H):
+    p = scene.planner()
+    rng = np.random.default_rng(K + H)
+    U0 = (rng.normal(size=(H, 7)) * 0.2).astype(np.float32)
+    # first call: same inputs on both entry points
+    Ur1, Sr1 = _run(p, p.smpc_iterate, scene, U0, K, 31, 0)
+    Un1, Sn1 = _run(p, p.smpc_iterate_noalloc, scene, U0, K, 31, 0)
+    # second call right after, from the first call's result
+    Ur2, Sr2 = _run(p, p.smpc_iterate, scene, Ur1, K, 31, 1)
+    Un2, Sn2 = _run(p, p.smpc_iterate_noalloc, scene, Ur1, K, 31, 1)
+    p.close()
+    for Ur, Un, Sr, Sn in ((Ur1, Un1, Sr1, Sn1), (Ur2, Un2, Sr2, Sn2)):
+        assert np.abs(Un - Ur).max() <= U_ABS
+        assert (np.abs(Sn - Sr) / np.abs(Sr)).max() <= S_REL
+
+
+def test_noalloc_rejects_host_buffers(scene):
+    p = scene.planner()
+    U = np.ones((32, 7), np.float32)
+    with pytest.raises(pm.PmError) as e:
+        p.smpc_iterate_noalloc(scene.q0, scene.qd0, scene.T, U, 64, 0.02, 0.05, SIGMA, 1, 0)
+    assert e.value.name == "PM_EINVAL"
+    assert np.all(U == 1.0)
+    p.close()
