@@ -31,13 +31,16 @@ sys.path.insert(0, ROOT)
 METRIC = "rollout-steps/s; replan p50/p99 ms served vs per-request plain, same GPU"
 UNIT = "rollout-steps/s"
 EPISODE = 200
-# Algorithmic FP32 operations of one roll-out step (FMA = 2; transcendental
-# calls, integer Philox work and loads not counted), from the kernel's
-# source-level arithmetic: sampling 46, roll-out scans 128, control costs 66,
-# kinematics 349, 28 sphere lookups 1736, SE(3) pose error 135, state limits
-# and null space 127, accumulation 5.  The terminal step (no spheres or
+# Algorithmic FP32 operations (FMA = 2; transcendental calls, integer Philox
+# work and loads not counted), from the kernel's source-level arithmetic.
+# A roll-out step: sampling 46, roll-out scans 128, control costs 66,
+# kinematics 349, pose error 135, state limits and null space 127,
+# accumulation 5 (856 in all) plus, per sphere, its centre 18, cell location
+# 18 and the skip test 1 (28 x 37).  A sphere whose cell is not skipped adds
+# its trilinear interpolation and cost, 26.  The terminal step (no spheres or
 # state limits) is 729.
-FLOPS_STEP = 2592
+FLOPS_STEP = 856 + 28 * 37
+FLOPS_GATHER = 26
 FLOPS_TERMINAL = 729
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2032.0
@@ -252,7 +255,7 @@ def run_ours(args, rank, world, local):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    planner.profile_enable(True)
+    planner.profile_enable(pm.PM_PROFILE_TIME)
     planner.profile_read(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -272,7 +275,19 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     kernel_ms, launches = planner.profile_read(reset=True)
-    planner.profile_enable(False)
+    # gathers per launch, counted on an untimed re-run of the first replans
+    n_count = min(args.steps, 25)
+    planner.profile_enable(pm.PM_PROFILE_GATHERS)
+    planner.profile_gathers(reset=True)
+    with torch.cuda.stream(stream):
+        for i in range(n_count):
+            r = args.warmup + i
+            episode_reset(r)
+            planner.replan(q, qd, Ts[r], U, K, iters, dt, lam, sigma, seed, r % EPISODE,
+                           u0_out=u0, best_cost=best, stream=stream)
+    torch.cuda.synchronize()
+    gathers_per_launch = planner.profile_gathers(reset=True) / (n_count * iters)
+    planner.profile_enable(0)
     step_ms = np.array([s.elapsed_time(e) for s, e in ev])
     total_ms = float(step_ms.sum())
     if world > 1:
@@ -312,14 +327,15 @@ def run_ours(args, rank, world, local):
     d2h = 25 * 4 + H * 7 * 4                # q, qd, u0, best + U
 
     # roofline of the iteration kernel (algorithmic FP32 flops / event-timed duration)
-    flops_launch = K * ((H - 1) * FLOPS_STEP + FLOPS_TERMINAL)
+    flops_launch = K * ((H - 1) * FLOPS_STEP + FLOPS_TERMINAL) + FLOPS_GATHER * gathers_per_launch
     avg_kernel_s = kernel_ms / 1e3 / max(launches, 1)
     achieved = flops_launch / avg_kernel_s / 1e12
     props = torch.cuda.get_device_properties(dev)
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "smpc_iteration_kernel<C=2,L=32,float>",
+                "kernel": "smpc_iteration_kernel<C=1,L=32,P=2,float>",
+                "gathered_fraction": gathers_per_launch / (K * (H - 1) * 28),
                 "kernel_ms_per_launch": avg_kernel_s * 1e3, "launches_timed": launches,
                 "flops_per_launch": flops_launch,
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
@@ -340,6 +356,39 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
     }
     planner.close()
+
+    # reduced-precision variants (field and noise in FP16 / BF16) on the same
+    # workload: device time of the replan and of the iteration kernel
+    variants = {}
+    for dt_name in ("f16", "bf16"):
+        pv = pm.Planner(w["robot"], sc["grid"], w["cp"], device=local, dtype=dt_name)
+        pv.set_distance_field(w["phi"])
+        pv.set_noise_dtype(dt_name)
+        n_v = min(args.steps, 200)
+        qv, qdv, Uv = q0.clone(), qd0.clone(), torch.zeros((H, 7), dtype=torch.float32, device=dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_v)]
+        with torch.cuda.stream(stream):
+            for r in range(3):
+                pv.replan(qv, qdv, Ts[r], Uv, K, iters, dt, lam, sigma, seed, r, stream=stream)
+            qv.copy_(q0); qdv.copy_(qd0); Uv.zero_()
+        torch.cuda.synchronize()
+        pv.profile_enable(pm.PM_PROFILE_TIME)
+        pv.profile_read(reset=True)
+        with torch.cuda.stream(stream):
+            for i in range(n_v):
+                evs[i][0].record(stream)
+                pv.replan(qv, qdv, Ts[i], Uv, K, iters, dt, lam, sigma, seed, i, stream=stream)
+                evs[i][1].record(stream)
+                flush.zero_()
+        torch.cuda.synchronize()
+        kms, kn = pv.profile_read(reset=True)
+        pv.close()
+        vms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
+        variants[dt_name] = {"value": K * H * iters * n_v / (vms / 1e3), "unit": UNIT,
+                             "ms_per_step": vms / n_v, "kernel_ms_per_launch": kms / max(kn, 1),
+                             "replans": n_v}
+    line["precision_variants"] = variants
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

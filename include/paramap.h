@@ -188,16 +188,17 @@ pm_status pm_replan(pm_ctx *ctx, float *q, float *qd, const float *T_goal, float
  * Same arguments and result as pm_smpc_iterate, except that q0, qd0, T_goal,
  * U and costs_out (if not NULL) must be device memory; sigma is host memory.
  * Only enqueues work on the stream.
- * Scratch: the soft-min merge partials and counters live in one 2 MiB
- * static device array that every GPU loading the library holds until exit.
- * The array's device address is resolved with cudaGetSymbolAddress on the
- * first call on each device, with that device current; make that first call
- * before any stream capture.  Every call shares the array and the merge
- * counters are cleared at the start of each call, so calls must not overlap
- * on the GPU (calls on different streams, or from different contexts, that
- * run concurrently race on the array).  The launch uses fewer blocks when
- * the partials of the usual grid do not fit the array (for H above about
- * 128); H up to PM_MAX_HORIZON is accepted.
+ * Scratch: the soft-min merge partials live in one 2 MiB static device
+ * array that every GPU loading the library holds until exit.  The array's
+ * device address is resolved with cudaGetSymbolAddress on the first call on
+ * each device, with that device current; make that first call before any
+ * stream capture.  Every call shares the array and keeps what the previous
+ * call left there; each call writes every word it reads before reading it,
+ * so nothing needs clearing, but calls must not overlap on the GPU (calls on
+ * different streams, or from different contexts, that run concurrently race
+ * on the array).  The launch uses fewer blocks when the partials of the
+ * usual grid do not fit the array (for H above about 128); H up to
+ * PM_MAX_HORIZON is accepted.
  * Errors: PM_EINVAL (as pm_smpc_iterate, or a host pointer), PM_ECUDA.
  */
 pm_status pm_smpc_iterate_noalloc(pm_ctx *ctx, const float *q0, const float *qd0,
@@ -230,15 +231,48 @@ pm_status pm_rollout_trace(pm_ctx *ctx, const float *q0, const float *qd0,
                            float *trace);
 
 /*
- * Kernel timing (observability; no counterpart in the paper).  While enabled,
- * every SMPC iteration kernel the context launches is bracketed by a pair of
- * CUDA events recorded on the stream it runs on.  pm_profile_read waits for
- * the context's last stream, returns the summed kernel time in milliseconds
- * and the number of timed launches, and clears the record if reset != 0.
+ * Kernel observability (no counterpart in the paper).  pm_profile_enable
+ * takes a mask of PM_PROFILE_TIME and PM_PROFILE_GATHERS (0 turns both off).
+ * PM_PROFILE_TIME brackets every SMPC iteration kernel the context launches
+ * with a pair of CUDA events recorded on the stream it runs on;
+ * pm_profile_read waits for them, returns the summed kernel time in
+ * milliseconds and the number of timed launches, and clears the record if
+ * reset != 0.  PM_PROFILE_GATHERS counts the sphere lookups that needed the
+ * 8-corner interpolation (the others are skipped because the cell's corner
+ * minimum proves their collision term is 0); pm_profile_gathers waits for
+ * the device and returns the count since the last reset.
  * Errors: PM_EINVAL (NULL ctx / outputs), PM_ECUDA.
  */
-pm_status pm_profile_enable(pm_ctx *ctx, int enable);
+#define PM_PROFILE_TIME 1
+#define PM_PROFILE_GATHERS 2
+pm_status pm_profile_enable(pm_ctx *ctx, int flags);
 pm_status pm_profile_read(pm_ctx *ctx, double *total_ms, uint64_t *launches, int reset);
+pm_status pm_profile_gathers(pm_ctx *ctx, uint64_t *gathers, int reset);
+
+/*
+ * Precision of the sampled perturbations (the reduced-precision variant).
+ * With PM_F16 or PM_BF16 every eps = sigma_j z of Eq. 27 is rounded to that
+ * format (round to nearest even) right after sampling, and the rounded value
+ * is used both in the roll-out and in the update of Eq. 30 -- the values a
+ * kernel would read back had it stored the noise in that format.  FK, costs
+ * and reductions stay FP32.  Default PM_F32 (no rounding).  Applies to later
+ * calls on ctx.  Errors: PM_EINVAL (unknown dtype).
+ */
+pm_status pm_set_noise_dtype(pm_ctx *ctx, int dtype);
+
+/*
+ * Work decomposition of the iteration kernel (no counterpart in the paper).
+ * A roll-out of H steps is mapped onto P warps (P = 1 or 2) of L lanes
+ * (L = 16 or 32, 32/L roll-outs per warp when P = 1), each lane owning C
+ * consecutive steps; C*L*P must be >= H.  Instantiated shapes (C, L, P):
+ * (1,16,1) (1,32,1) (3,16,1) (2,32,1) (4,32,1) (8,32,1) (1,32,2) (2,32,2)
+ * (4,32,2).  pm_set_tile_shape forces one for all later calls on ctx (an
+ * autotuner's hook); (0, 0, 0) restores the default per horizon (H <= 16:
+ * (1,16,1); <= 32: (1,32,1); <= 64: (1,32,2); <= 128: (2,32,2); else
+ * (4,32,2)).  A call whose H exceeds the forced shape's C*L*P fails with
+ * PM_EINVAL.  Errors: PM_EINVAL (unknown shape).
+ */
+pm_status pm_set_tile_shape(pm_ctx *ctx, int C, int L, int P);
 
 /* Release every resource of the context (NULL is a no-op). */
 void pm_destroy(pm_ctx *ctx);

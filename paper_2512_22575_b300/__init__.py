@@ -22,7 +22,8 @@ __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
     "create", "set_distance_field", "smpc_iterate", "smpc_iterate_noalloc", "replan",
     "philox4x32_10",
-    "sample_noise", "rollout_trace", "profile_enable", "profile_read", "destroy",
+    "sample_noise", "rollout_trace", "profile_enable", "profile_read", "profile_gathers",
+    "set_tile_shape", "set_noise_dtype", "PM_PROFILE_TIME", "PM_PROFILE_GATHERS", "destroy",
     "last_error", "Planner",
 ]
 
@@ -201,9 +202,29 @@ def sample_noise(K, H, sigma, seed, iter_index, eps, stream=None):
                                  _stream(stream)))
 
 
-def profile_enable(ctx, enable=True):
-    """pm_profile_enable: bracket iteration kernels with CUDA events."""
-    _check(lib().pm_profile_enable(ctx, int(bool(enable))), ctx)
+PM_PROFILE_TIME, PM_PROFILE_GATHERS = 1, 2
+
+
+def profile_enable(ctx, flags=PM_PROFILE_TIME):
+    """pm_profile_enable: PM_PROFILE_TIME | PM_PROFILE_GATHERS (0 = off)."""
+    _check(lib().pm_profile_enable(ctx, int(flags)), ctx)
+
+
+def profile_gathers(ctx, reset=True):
+    """pm_profile_gathers: 8-corner lookups performed since the last reset."""
+    n = C.c_uint64()
+    _check(lib().pm_profile_gathers(ctx, C.byref(n), int(bool(reset))), ctx)
+    return n.value
+
+
+def set_noise_dtype(ctx, dtype="f32"):
+    """pm_set_noise_dtype: round the sampled perturbations to f16 / bf16."""
+    _check(lib().pm_set_noise_dtype(ctx, _DTYPES[dtype]), ctx)
+
+
+def set_tile_shape(ctx, C_steps=0, L=0, P=0):
+    """pm_set_tile_shape: force (C, L, P) for later calls; (0, 0, 0) = default."""
+    _check(lib().pm_set_tile_shape(ctx, int(C_steps), int(L), int(P)), ctx)
 
 
 def profile_read(ctx, reset=True):
@@ -248,8 +269,17 @@ class Planner:
     def rollout_trace(self, *a, **kw):
         rollout_trace(self.ctx, *a, **kw)
 
-    def profile_enable(self, enable=True):
-        profile_enable(self.ctx, enable)
+    def profile_enable(self, flags=PM_PROFILE_TIME):
+        profile_enable(self.ctx, flags)
+
+    def profile_gathers(self, reset=True):
+        return profile_gathers(self.ctx, reset)
+
+    def set_noise_dtype(self, dtype="f32"):
+        set_noise_dtype(self.ctx, dtype)
+
+    def set_tile_shape(self, C_steps=0, L=0, P=0):
+        set_tile_shape(self.ctx, C_steps, L, P)
 
     def profile_read(self, reset=True):
         return profile_read(self.ctx, reset)

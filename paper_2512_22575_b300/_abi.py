@@ -55,6 +55,9 @@ SIGNATURES = {
                                    C.c_uint64, C.c_uint32, _V]),
     "pm_profile_enable": (C.c_int, [_V, C.c_int]),
     "pm_profile_read": (C.c_int, [_V, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
+    "pm_profile_gathers": (C.c_int, [_V, C.POINTER(C.c_uint64), C.c_int]),
+    "pm_set_tile_shape": (C.c_int, [_V, C.c_int, C.c_int, C.c_int]),
+    "pm_set_noise_dtype": (C.c_int, [_V, C.c_int]),
     "pm_destroy": (None, [_V]),
     "pm_last_error": (C.c_char_p, [_V]),
     "pm_version": (C.c_char_p, []),

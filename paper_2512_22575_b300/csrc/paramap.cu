@@ -24,6 +24,7 @@ struct pm_ctx {
     pm_grid_desc gd{};
     size_t grid_elems = 0;
     void *d_grid = nullptr;
+    float *d_cmin = nullptr;            // per-cell corner minimum of the stored field
     bool has_grid = false;
     cudaStream_t stream = nullptr;
     // Ring of staging slots for host inputs: slot i holds q0 [0..7], qd0
@@ -43,10 +44,12 @@ struct pm_ctx {
     size_t cap_h_out = 0;
     float *d_part = nullptr;            // block partials
     size_t cap_part = 0;
-    float *d_gpart = nullptr;           // group partials
-    size_t cap_gpart = 0;
-    unsigned *d_counter = nullptr;      // [1 + kMaxGroups], zero between launches
+
     float *d_c0 = nullptr;              // [c0, best, q(8), qd(8), u0(8)]
+    TileShape forced{0, 0, 0};          // tile shape set by pm_set_tile_shape (0 = default)
+    unsigned long long *d_gathers = nullptr;  // 8-corner lookups, counted while enabled
+    bool count_gathers = false;
+    int noise_dtype = PM_F32;           // rounding of the sampled perturbations
     bool prof = false;                  // bracket iteration kernels with events
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, end)
     size_t prof_used = 0;               // events recorded since the last reset
@@ -114,21 +117,41 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-TileShape pick_shape(int H)
-{
-    for (const TileShape &s : kShapes)
-        if (s.C * s.L >= H) return s;
-    return kShapes[sizeof(kShapes) / sizeof(kShapes[0]) - 1];
-}
-
 IterKernel lookup_kernel(int dtype, TileShape s, bool trace)
 {
     switch (dtype) {
-    case PM_F32: return iteration_kernel_f32(s.C, s.L, trace);
-    case PM_F16: return iteration_kernel_f16(s.C, s.L, trace);
-    case PM_BF16: return iteration_kernel_bf16(s.C, s.L, trace);
+    case PM_F32: return iteration_kernel_f32(s.C, s.L, s.P, trace);
+    case PM_F16: return iteration_kernel_f16(s.C, s.L, s.P, trace);
+    case PM_BF16: return iteration_kernel_bf16(s.C, s.L, s.P, trace);
     default: return nullptr;
     }
+}
+
+bool shape_known(TileShape t)
+{
+    for (const TileShape &s : kShapes)
+        if (s.C == t.C && s.L == t.L && s.P == t.P) return true;
+    return false;
+}
+
+// The context's shape for horizon H: the forced one if set, else the default.
+pm_status pick_shape(pm_ctx *c, int H, TileShape &out)
+{
+    out = c->forced.C ? c->forced : default_shape(H);
+    if (out.C * out.L * out.P < H)
+        return set_err(c, PM_EINVAL, "tile shape C=%d L=%d P=%d holds %d steps < H=%d", out.C, out.L,
+                       out.P, out.C * out.L * out.P, H);
+    return PM_OK;
+}
+
+// Blocks of a launch: enough warps for every tile (P warps per tile of R
+// roll-outs), at most what stays resident, at most kMaxBlocks.
+long long launch_blocks(long long K, TileShape sh, long long resident)
+{
+    const int R = 32 / sh.L;
+    const long long tiles = (K + R - 1) / R;
+    const long long need = (tiles * sh.P + kWarps - 1) / kWarps;
+    return std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)}));
 }
 
 // Resident blocks per SM of an iteration kernel; on first use also raises
@@ -168,6 +191,35 @@ __global__ void convert_grid_kernel(const float *src, void *dst, size_t n, int d
     }
 }
 
+// cmin[l][j][i] = min of the 8 corners (i..i+1, j..j+1, l..l+1) of the
+// stored field (cells with a base on the last plane of an axis are never
+// looked up and get 0, i.e. never skipped).
+template <typename T>
+__global__ void cell_min_kernel(const T *phi, float *cmin, int nx, int ny, int nz)
+{
+    const size_t n = static_cast<size_t>(nx) * ny * nz;
+    for (size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; id < n;
+         id += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(id % nx);
+        const int j = static_cast<int>((id / nx) % ny);
+        const int l = static_cast<int>(id / (static_cast<size_t>(nx) * ny));
+        if (i >= nx - 1 || j >= ny - 1 || l >= nz - 1) {
+            cmin[id] = 0.f;
+            continue;
+        }
+        const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
+        float m = grid_load(phi + id);
+        m = fminf(m, grid_load(phi + id + 1));
+        m = fminf(m, grid_load(phi + id + sy));
+        m = fminf(m, grid_load(phi + id + sy + 1));
+        m = fminf(m, grid_load(phi + id + sz));
+        m = fminf(m, grid_load(phi + id + sz + 1));
+        m = fminf(m, grid_load(phi + id + sz + sy));
+        m = fminf(m, grid_load(phi + id + sz + sy + 1));
+        cmin[id] = m;
+    }
+}
+
 __global__ void philox_words_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                     size_t n)
 {
@@ -192,6 +244,50 @@ __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint3
         step_normals(s_lo, s_hi, iter, m, k, z);
         for (int j = 0; j < kNJ; ++j) eps[i * kNJ + j] = sg.s[j] * z[j];
     }
+}
+
+// Soft-min merge (Eqs. 29-30) of the iteration kernel's nb block partials
+// (m [nb], z [nb], acc [na][nb]): one warp per output t of U*.  Every warp
+// forms M = min_b m_b and Z = sum_b f_b z_b, f_b = exp((M - m_b)/lambda), the
+// same way (lane-strided sums in ascending b, then a fixed butterfly, lane
+// 0's value), then U*[t] = Ubar[t] + sum_b f_b acc_b[t] / Z.  Block 0 also
+// writes min S = M + c0 and adds the k = 0 terms c0 to the costs.
+constexpr int kMergeWarps = 8;
+
+__device__ __forceinline__ float warp_sum_lane0(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__global__ void __launch_bounds__(32 * kMergeWarps)
+softmin_merge_kernel(const float *part, int nb, int na, const float *Ubar, float *Uout,
+                     float inv_lambda, float *c0, float *costs, int K)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float *pm_ = part, *pz = part + nb, *pacc = part + 2 * static_cast<size_t>(nb);
+    float lm = CUDART_INF_F;
+    for (int b = lane; b < nb; b += 32) lm = fminf(lm, __ldg(pm_ + b));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
+    const float M = lm;
+    float lz = 0.f;
+    for (int b = lane; b < nb; b += 32) lz = fmaf(weight_factor(__ldg(pm_ + b), M, inv_lambda), __ldg(pz + b), lz);
+    const float Z = warp_sum_lane0(lz);
+    const int t = blockIdx.x * kMergeWarps + warp;
+    if (t < na) {
+        const float *row = pacc + static_cast<size_t>(t) * nb;
+        float la = 0.f;
+        for (int b = lane; b < nb; b += 32) la = fmaf(weight_factor(__ldg(pm_ + b), M, inv_lambda), __ldg(row + b), la);
+        const float acc = warp_sum_lane0(la);
+        if (lane == 0) Uout[t] = Ubar[t] + acc / Z;
+    }
+    const float k0 = __ldg(c0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c0[1] = M + k0;
+    if (costs)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x)
+            costs[i] += k0;
 }
 
 // Receding-horizon step (Sec. IV-C): execute u0* for one integrator step and
@@ -251,15 +347,6 @@ pm_status ensure_capacity(pm_ctx *c, int K, int H, int nb)
         PM_CUDA(c, cudaMalloc(&c->d_part, cap * sizeof(float)));
         c->cap_part = cap;
     }
-    const size_t needG = static_cast<size_t>((nb + kGroup - 1) / kGroup) * stride;
-    if (needG > c->cap_gpart) {
-        size_t cap = std::max(needG, static_cast<size_t>(32) * (2 + 64 * kNJ));
-        if (c->d_gpart) cudaFree(c->d_gpart);
-        c->d_gpart = nullptr;
-        c->cap_gpart = 0;
-        PM_CUDA(c, cudaMalloc(&c->d_gpart, cap * sizeof(float)));
-        c->cap_gpart = cap;
-    }
     return PM_OK;
 }
 
@@ -267,6 +354,7 @@ GridConst grid_const(const pm_ctx *c)
 {
     GridConst g;
     g.phi = c->d_grid;
+    g.cmin = c->d_cmin;
     g.nx = c->gd.nx; g.ny = c->gd.ny; g.nz = c->gd.nz;
     g.inv_res = 1.0f / c->gd.res;
     g.ox = c->gd.origin[0]; g.oy = c->gd.origin[1]; g.oz = c->gd.origin[2];
@@ -334,33 +422,22 @@ pm_status stage_inputs(pm_ctx *c, cudaStream_t s, const float *q0, const float *
 }
 
 // Enqueue one iteration kernel.  Ubar/Uout device [H][7]; costs device or null.
-pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, const float *Ubar,
-                           float *Uout, float *costs, int K, int H, float dt, float lambda,
-                           uint64_t seed, uint32_t iter, bool trace, float *trace_out)
+// Enqueue the iteration kernel on nb blocks and, unless tracing, the merge.
+pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, size_t smem,
+                            const CallInputs &in, const float *Ubar, float *Uout, float *costs,
+                            float *part, float *c0, int K, int H, float dt, float lambda,
+                            uint64_t seed, uint32_t iter, bool trace, float *trace_out,
+                            unsigned long long *gathers)
 {
-    const TileShape sh = pick_shape(H);
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace);
-    if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d", sh.C, sh.L);
-    const int R = 32 / sh.L;
-    const long long tiles = (static_cast<long long>(K) + R - 1) / R;
-    const long long need = (tiles + kWarps - 1) / kWarps;
-    const size_t smem = iteration_smem_bytes(sh.C);
-    const int per_sm = resident_blocks_per_sm(fn, smem);
-    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
-    const long long resident = static_cast<long long>(c->n_sm) * per_sm;
-    const int nb = static_cast<int>(std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)})));
-    pm_status st = ensure_capacity(c, K, H, nb);
-    if (st != PM_OK) return st;
     IterArgs a{};
     a.in = in;
     a.Ubar = Ubar;
-    a.Uout = Uout;
     a.costs = costs;
-    a.part = c->d_part;
-    a.gpart = c->d_gpart;
-    a.counters = c->d_counter;
-    a.c0 = c->d_c0;
+    a.part = part;
+    a.c0 = c0;
     a.trace = trace_out;
+    a.gathers = gathers;
+    a.noise_dtype = c->noise_dtype;
     a.K = K;
     a.H = H;
     a.seed_lo = static_cast<uint32_t>(seed & 0xffffffffu);
@@ -384,7 +461,35 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
         c->prof_used += 2;
         c->prof_stream = s;
     }
+    if (!trace) {
+        const int na = H * kNJ;
+        softmin_merge_kernel<<<(na + kMergeWarps - 1) / kMergeWarps, 32 * kMergeWarps, 0, s>>>(
+            part, nb, na, Ubar, Uout, a.inv_lambda, c0, costs, K);
+        PM_CUDA(c, cudaGetLastError());
+    }
     return PM_OK;
+}
+
+pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, const float *Ubar,
+                           float *Uout, float *costs, int K, int H, float dt, float lambda,
+                           uint64_t seed, uint32_t iter, bool trace, float *trace_out)
+{
+    TileShape sh;
+    pm_status pst = pick_shape(c, H, sh);
+    if (pst != PM_OK) return pst;
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace);
+    if (!fn) return set_err(c, trace ? PM_EINVAL : PM_EINTERNAL, "no %s kernel for C=%d L=%d P=%d",
+                            trace ? "trace" : "iteration", sh.C, sh.L, sh.P);
+    const size_t smem = iteration_smem_bytes(sh.C);
+    const int per_sm = resident_blocks_per_sm(fn, smem);
+    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
+    const long long resident = static_cast<long long>(c->n_sm) * per_sm;
+    const int nb = static_cast<int>(launch_blocks(K, sh, resident));
+    pm_status st = ensure_capacity(c, K, H, nb);
+    if (st != PM_OK) return st;
+    return enqueue_iteration(c, s, fn, nb, smem, in, Ubar, Uout, costs, c->d_part, c->d_c0, K, H, dt,
+                             lambda, seed, iter, trace, trace_out,
+                             (c->count_gathers && !trace) ? c->d_gathers : nullptr);
 }
 
 cudaStream_t pick_stream(pm_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
@@ -468,6 +573,8 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         const int s = order[i];
         for (int k = 0; k < 3; ++k) r.sph_off[i][k] = rb->sphere_offset[3 * s + k];
         r.sph_r[i] = rb->sphere_radius[s];
+        const double thr = (static_cast<double>(cp->d_act) + rb->sphere_radius[s]) * (1.0 + 1e-6) + 1e-6;
+        r.sph_skip[i] = std::nextafter(static_cast<float>(thr), INFINITY);
     }
     for (int L = 1; L <= n + 1; ++L) {
         int cnt = 0;
@@ -516,11 +623,13 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     if (!ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device), "SM count") ||
         !ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream") ||
         !ck(cudaMalloc(&c->d_grid, elems * dtype_size(gd->dtype)), "grid alloc") ||
+        !ck(cudaMalloc(&c->d_cmin, elems * sizeof(float)), "cell-minimum alloc") ||
         !ck(cudaMalloc(&c->d_stage, sizeof(float) * kSlots * kSlotFloats), "staging alloc") ||
         !ck(cudaMallocHost(&c->h_stage, sizeof(float) * kSlots * kSlotFloats), "pinned staging alloc") ||
         !ck(cudaMallocHost(&c->h_U, sizeof(float) * kMaxHorizon * kNJ), "pinned U") ||
-        !ck(cudaMalloc(&c->d_counter, sizeof(unsigned) * (1 + kMaxGroups)), "counter alloc") ||
-        !ck(cudaMemset(c->d_counter, 0, sizeof(unsigned) * (1 + kMaxGroups)), "counter zero") ||
+
+        !ck(cudaMalloc(&c->d_gathers, sizeof(unsigned long long)), "counter alloc") ||
+        !ck(cudaMemset(c->d_gathers, 0, sizeof(unsigned long long)), "counter zero") ||
         !ck(cudaMalloc(&c->d_c0, 32 * sizeof(float)), "c0") ||
         !ck(cudaMemset(c->d_c0, 0, 32 * sizeof(float)), "c0 zero"))
         return fail(c->err.find("alloc") != std::string::npos ? PM_ENOMEM : PM_ECUDA);
@@ -556,6 +665,17 @@ pm_status pm_set_distance_field(pm_ctx *c, const float *grid, int grid_is_device
         cudaFree(tmp);
         PM_CUDA(c, e);
     }
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((c->grid_elems + 255) / 256, 8u * c->n_sm));
+    if (c->gd.dtype == PM_F32)
+        cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->d_grid), c->d_cmin,
+                                                      c->gd.nx, c->gd.ny, c->gd.nz);
+    else if (c->gd.dtype == PM_F16)
+        cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const __half *>(c->d_grid), c->d_cmin,
+                                                      c->gd.nx, c->gd.ny, c->gd.nz);
+    else
+        cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const __nv_bfloat16 *>(c->d_grid),
+                                                      c->d_cmin, c->gd.nx, c->gd.ny, c->gd.nz);
+    PM_CUDA(c, cudaGetLastError());
     PM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->has_grid = true;
     return PM_OK;
@@ -711,11 +831,49 @@ pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed, uint3
     return PM_OK;
 }
 
-pm_status pm_profile_enable(pm_ctx *c, int enable)
+pm_status pm_profile_enable(pm_ctx *c, int flags)
 {
     if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
-    c->prof = enable != 0;
+    c->prof = (flags & PM_PROFILE_TIME) != 0;
+    c->count_gathers = (flags & PM_PROFILE_GATHERS) != 0;
+    return PM_OK;
+}
+
+pm_status pm_profile_gathers(pm_ctx *c, uint64_t *gathers, int reset)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    if (!gathers) return set_err(c, PM_EINVAL, "NULL output");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    unsigned long long v = 0;
+    PM_CUDA(c, cudaMemcpy(&v, c->d_gathers, sizeof(v), cudaMemcpyDeviceToHost));
+    *gathers = v;
+    if (reset) PM_CUDA(c, cudaMemset(c->d_gathers, 0, sizeof(unsigned long long)));
+    return PM_OK;
+}
+
+pm_status pm_set_noise_dtype(pm_ctx *c, int dtype)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    if (dtype != PM_F32 && dtype != PM_F16 && dtype != PM_BF16)
+        return set_err(c, PM_EINVAL, "noise dtype %d unknown", dtype);
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->noise_dtype = dtype;
+    return PM_OK;
+}
+
+pm_status pm_set_tile_shape(pm_ctx *c, int C, int L, int P)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    const TileShape t{C, L, P};
+    if (C == 0 && L == 0 && P == 0) {
+        c->forced = t;
+        return PM_OK;
+    }
+    if (!shape_known(t)) return set_err(c, PM_EINVAL, "no kernel for tile shape C=%d L=%d P=%d", C, L, P);
+    c->forced = t;
     return PM_OK;
 }
 
@@ -745,6 +903,7 @@ void pm_destroy(pm_ctx *c)
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         cudaFree(c->d_grid);
+        cudaFree(c->d_cmin);
         cudaFree(c->d_stage);
         cudaFreeHost(c->h_stage);
         cudaFreeHost(c->h_U);
@@ -752,9 +911,9 @@ void pm_destroy(pm_ctx *c)
         cudaFree(c->d_costs);
         cudaFreeHost(c->h_out);
         cudaFree(c->d_part);
-        cudaFree(c->d_gpart);
-        cudaFree(c->d_counter);
+
         cudaFree(c->d_c0);
+        cudaFree(c->d_gathers);
         for (cudaEvent_t e : c->slot_ev)
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
@@ -767,8 +926,7 @@ void pm_destroy(pm_ctx *c)
 
 // ============================================================ no-allocation
 // pm_smpc_iterate_noalloc: the same iteration kernel, with its scratch
-// (block and group partials of the soft-min merge, merge counters, the
-// k = 0 state term) in one file-scope device array instead of memory the
+// (the block partials of the soft-min merge and the k = 0 state term) in one file-scope device array instead of memory the
 // context allocates on demand.  It is for callers that must not allocate
 // device memory once they are running -- for instance a fixed-rate control
 // loop that forbids allocation after start-up, or a process whose device
@@ -776,8 +934,7 @@ void pm_destroy(pm_ctx *c)
 namespace {
 
 constexpr size_t kStaticScratchFloats = 512 * 1024;   // 2 MiB, held by every GPU that loads us
-constexpr size_t kStaticHeaderFloats = 256;           // c0 [0, 32), counters [32, 32 + 1 + kMaxGroups)
-static_assert(32 + 1 + kMaxGroups <= kStaticHeaderFloats, "static scratch header");
+constexpr size_t kStaticHeaderFloats = 64;            // c0 [0, 2); partials start 256-B aligned
 
 static __device__ __align__(256) float g_static_scratch[kStaticScratchFloats];
 
@@ -822,56 +979,34 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
     st = static_scratch(c, c->device, &scratch);
     if (st != PM_OK) return st;
 
-    const TileShape sh = pick_shape(H);
+    TileShape sh;
+    st = pick_shape(c, H, sh);
+    if (st != PM_OK) return st;
     IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
-    if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d", sh.C, sh.L);
+    if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
     const size_t smem = iteration_smem_bytes(sh.C);
     const int per_sm = resident_blocks_per_sm(fn, smem);
     if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
-    const int R = 32 / sh.L;
-    const long long tiles = (static_cast<long long>(K) + R - 1) / R;
-    const long long need = (tiles + kWarps - 1) / kWarps;
     const long long resident = static_cast<long long>(c->n_sm) * per_sm;
-    long long nb = std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)}));
+    long long nb = launch_blocks(K, sh, resident);
     // fewer, longer-running blocks when the partials would not fit the array
-    const size_t stride = 2 + static_cast<size_t>(H) * kNJ;
-    auto fits = [&](long long n) {
-        const size_t groups = static_cast<size_t>((n + kGroup - 1) / kGroup);
-        return kStaticHeaderFloats + (groups + static_cast<size_t>(n)) * stride <= kStaticScratchFloats;
-    };
+    const size_t per_block = 2 + static_cast<size_t>(H) * kNJ;
+    auto fits = [&](long long n) { return kStaticHeaderFloats + static_cast<size_t>(n) * per_block <= kStaticScratchFloats; };
     while (nb > 1 && !fits(nb)) --nb;
     if (!fits(nb))
         return set_err(c, PM_EINVAL, "H=%d needs more than the %zu-float static scratch", H, kStaticScratchFloats);
 
     cudaStream_t s = pick_stream(c, cuda_stream);
-    float *c0 = scratch;
-    unsigned *counters = reinterpret_cast<unsigned *>(scratch + 32);
-    float *gpart = scratch + kStaticHeaderFloats;
-    float *part = gpart + static_cast<size_t>((nb + kGroup - 1) / kGroup) * stride;
-    // the array keeps the previous call's contents: the merge counters must start at zero
-    PM_CUDA(c, cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + kMaxGroups), s));
-
-    IterArgs a{};
-    a.in.q0 = q0;
-    a.in.qd0 = qd0;
-    a.in.Tg = T_goal;
-    for (int j = 0; j < 8; ++j) a.in.sigma[j] = j < kNJ ? sigma[j] : 0.f;
-    a.Ubar = U;
-    a.Uout = U;
-    a.costs = costs_out;
-    a.part = part;
-    a.gpart = gpart;
-    a.counters = counters;
-    a.c0 = c0;
-    a.trace = nullptr;
-    a.K = K;
-    a.H = H;
-    a.seed_lo = static_cast<uint32_t>(seed & 0xffffffffu);
-    a.seed_hi = static_cast<uint32_t>(seed >> 32);
-    a.iter = iter_index;
-    a.dt = dt;
-    a.inv_lambda = 1.0f / lambda;
-    fn<<<static_cast<int>(nb), kBlock, smem, s>>>(c->rc, grid_const(c), a);
-    PM_CUDA(c, cudaGetLastError());
-    return PM_OK;
+    CallInputs in{};
+    in.q0 = q0;
+    in.qd0 = qd0;
+    in.Tg = T_goal;
+    for (int j = 0; j < 8; ++j) in.sigma[j] = j < kNJ ? sigma[j] : 0.f;
+    // every word of the array that the kernels read is written earlier in the
+    // same call (partials by the iteration kernel, c0 by its first warp), so
+    // nothing has to be cleared between calls
+    return enqueue_iteration(c, s, fn, static_cast<int>(nb), smem, in, U, U, costs_out,
+                             scratch + kStaticHeaderFloats, scratch, K, H, dt, lambda, seed,
+                             iter_index, false, nullptr, nullptr);
 }
+

@@ -35,6 +35,11 @@ struct RobotConst {
     float qdd_lo[kNJ], qdd_hi[kNJ];
     float sph_off[kMaxSpheres][3];
     float sph_r[kMaxSpheres];
+    // A sphere whose cell has all 8 corners above sph_skip[s] has
+    // d_act - (phi - r) < 0 for every point of the cell, even after FP32
+    // rounding of the interpolation: its collision term is exactly 0.
+    // sph_skip[s] = (d_act + r_s)(1 + 1e-6) + 1e-6, rounded up.
+    float sph_skip[kMaxSpheres];
     float Q[6], QH[6];
     float w_env, d_act, w_self;
     float w_q, w_qd, w_qdd, w_s, w_ns;
@@ -43,6 +48,8 @@ struct RobotConst {
 
 struct GridConst {
     const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16
+    const float *cmin;            // [nz][ny][nx]: min of the 8 corners of the cell
+                                  // with base voxel (i, j, l), as the lookup reads them
     int nx, ny, nz;
     float inv_res;
     float ox, oy, oz;             // origin

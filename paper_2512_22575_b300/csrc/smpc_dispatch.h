@@ -10,36 +10,51 @@ namespace pm {
 
 using IterKernel = void (*)(RobotConst, GridConst, IterArgs);
 
-// Tile shape: C steps per lane, L lanes per roll-out (H <= C * L).
-struct TileShape { int C, L; };
+// Tile shape: C steps per lane, L lanes per roll-out, P warps per roll-out
+// (H <= C * L * P).
+struct TileShape { int C, L, P; };
 
-// Shapes with an instantiated kernel, in order of preference for a horizon.
-constexpr TileShape kShapes[] = {{1, 16}, {1, 32}, {3, 16}, {2, 32}, {4, 32}, {8, 32}};
+// Every instantiated shape.
+constexpr TileShape kShapes[] = {{1, 16, 1}, {1, 32, 1}, {3, 16, 1}, {2, 32, 1}, {4, 32, 1},
+                                 {8, 32, 1}, {1, 32, 2}, {2, 32, 2}, {4, 32, 2}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-// Kernel for a tile shape and storage type, with its dynamic shared memory
-// limit raised to iteration_smem_bytes(C) (done once per kernel).
-IterKernel iteration_kernel_f32(int C, int L, bool trace);
-IterKernel iteration_kernel_f16(int C, int L, bool trace);
-IterKernel iteration_kernel_bf16(int C, int L, bool trace);
+// Default shape for a horizon: the smallest work unit that covers H.
+inline TileShape default_shape(int H)
+{
+    if (H <= 16) return {1, 16, 1};
+    if (H <= 32) return {1, 32, 1};
+    if (H <= 64) return {1, 32, 2};
+    if (H <= 128) return {2, 32, 2};
+    return {4, 32, 2};
+}
+
+// Kernel for a tile shape and storage type (nullptr if not instantiated;
+// trace kernels exist for the float field only).
+IterKernel iteration_kernel_f32(int C, int L, int P, bool trace);
+IterKernel iteration_kernel_f16(int C, int L, int P, bool trace);
+IterKernel iteration_kernel_bf16(int C, int L, int P, bool trace);
 
 } // namespace pm
 
-#define PM_INSTANTIATE_ITERATION_TABLE(NAME, GT)                                        \
+#define PM_KERNEL_CASE(C_, L_, P_, GT, WITH_TRACE)                                          \
+    if (C == C_ && L == L_ && P == P_)                                                   \
+        return trace ? (WITH_TRACE ? smpc_iteration_kernel<C_, L_, P_, GT, WITH_TRACE> : nullptr) \
+                     : smpc_iteration_kernel<C_, L_, P_, GT, false>;
+
+#define PM_INSTANTIATE_ITERATION_TABLE(NAME, GT, WITH_TRACE)                               \
     namespace pm {                                                                     \
-    IterKernel NAME(int C, int L, bool trace)                                          \
+    IterKernel NAME(int C, int L, int P, bool trace)                                   \
     {                                                                                  \
-        if (L == 16 && C == 1) return trace ? smpc_iteration_kernel<1, 16, GT, true>   \
-                                            : smpc_iteration_kernel<1, 16, GT, false>; \
-        if (L == 16 && C == 3) return trace ? smpc_iteration_kernel<3, 16, GT, true>   \
-                                            : smpc_iteration_kernel<3, 16, GT, false>; \
-        if (L == 32 && C == 1) return trace ? smpc_iteration_kernel<1, 32, GT, true>   \
-                                            : smpc_iteration_kernel<1, 32, GT, false>; \
-        if (L == 32 && C == 2) return trace ? smpc_iteration_kernel<2, 32, GT, true>   \
-                                            : smpc_iteration_kernel<2, 32, GT, false>; \
-        if (L == 32 && C == 4) return trace ? smpc_iteration_kernel<4, 32, GT, true>   \
-                                            : smpc_iteration_kernel<4, 32, GT, false>; \
-        if (L == 32 && C == 8) return trace ? smpc_iteration_kernel<8, 32, GT, true>   \
-                                            : smpc_iteration_kernel<8, 32, GT, false>; \
+        PM_KERNEL_CASE(1, 16, 1, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(1, 32, 1, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(3, 16, 1, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(2, 32, 1, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(4, 32, 1, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(8, 32, 1, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(1, 32, 2, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(2, 32, 2, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(4, 32, 2, GT, WITH_TRACE)                                       \
         return nullptr;                                                                \
     }                                                                                  \
     }

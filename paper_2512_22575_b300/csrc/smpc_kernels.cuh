@@ -12,8 +12,8 @@
 // (Eqs. 22, 23) and the state terms of q_{k+1}, qd_{k+1} (Eqs. 16, 19-20, 22,
 // 24) or, for k+1 = H, the terminal cost (Eq. 25).  The state terms of
 // k = 0 depend only on (q_0, qd_0) and are the same for every roll-out: one
-// warp computes them once and they are added to S at the end; they cancel
-// in the weights of Eq. 29.
+// warp of the last block computes them once and the merge adds them to S;
+// they cancel in the weights of Eq. 29.
 //
 // The sampled perturbations of a lane's steps are kept in shared memory
 // ([warp][step][joint][lane], conflict-free) from sampling to the weighted
@@ -22,12 +22,12 @@
 //
 // Soft-min (Eqs. 29-30).  Each warp keeps a running minimum m, sum
 // z = sum exp(-(S - m)/lambda) and accumulator sum exp(-(S - m)/lambda) eps,
-// rescaled when m drops.  Warps merge into a block partial.  Blocks form
-// groups of kGroup; the last block of a group to finish (atomic ticket after
-// a fence) merges the group's partials, and the last group to finish merges
-// the group partials and writes U* = Ubar + acc / z.  No block ever waits
-// for another, and the merge order is fixed, so results are deterministic
-// for a given launch shape.
+// rescaled when m drops.  Warps merge, in warp order, into one partial per
+// block (m_b, z_b, acc_b), written as [m][z][acc^T] over blocks.  A second,
+// wide kernel (softmin_merge_kernel in paramap.cu) merges the block partials
+// into U* = Ubar + sum_b f_b acc_b / sum_b f_b z_b, f_b = exp((min m - m_b)/
+// lambda), each sum in a fixed order, so results are deterministic for a
+// given launch shape.
 #pragma once
 
 #include "smpc_device.cuh"
@@ -36,9 +36,7 @@ namespace pm {
 
 constexpr int kBlock = 128;
 constexpr int kWarps = kBlock / 32;
-constexpr int kGroup = 32;                 // blocks per first-level merge
 constexpr int kMaxBlocks = 4096;
-constexpr int kMaxGroups = kMaxBlocks / kGroup;
 constexpr int kTraceCols = 8;   // pose, env, self, lim_q, lim_qd, lim_qdd, smooth, ns
 constexpr int kSphereBatch = 4;
 
@@ -52,13 +50,12 @@ constexpr size_t iteration_smem_bytes(int C)
 struct IterArgs {
     CallInputs in;              // q0, qd0, T_goal (device), sigma
     const float *Ubar;          // [H][7]
-    float *Uout;                // [H][7], may alias Ubar
-    float *costs;               // [K] or null
-    float *part;                // block partials [gridDim.x][2 + H*7]
-    float *gpart;               // group partials [groups][2 + H*7]
-    unsigned *counters;         // [0] = groups done, [1 + g] = blocks done in group g
-    float *c0;                  // [0] = k = 0 state terms, [1] = min S
+    float *costs;               // [K] or null (without the k = 0 terms)
+    float *part;                // block partials: m [nb], z [nb], acc [H*7][nb]; nb = gridDim.x
+    float *c0;                  // [0] = k = 0 state terms
     float *trace;               // [K][H+1][8] (trace kernels only)
+    unsigned long long *gathers;  // if not null: += number of 8-corner lookups performed
+    int noise_dtype;            // PM_F32 (0), PM_F16 (1) or PM_BF16 (2): rounding of eps
     int K, H;
     uint32_t seed_lo, seed_hi, iter;
     float dt, inv_lambda;
@@ -83,28 +80,35 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 }
 
 // sum over spheres s in [b, e) of frame F of max(0, d_act - (phi(p_s) - r_s))^2
-// (Eqs. 17, 19), four spheres per batch with all gathers issued together.
+// (Eqs. 17, 19).  The cell-corner minima of four spheres are loaded together;
+// a sphere whose minimum is above its skip threshold contributes exactly 0
+// and needs no gathers, the others are interpolated from their 8 corners.
 template <typename GT>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
-                                          const Frame &F, int b, int e)
+                                          const Frame &F, int b, int e, unsigned &ngath)
 {
     float env = 0.f;
     for (int s0 = b; s0 < e; s0 += kSphereBatch) {
         Cell c[kSphereBatch];
+        float mn[kSphereBatch];
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
             c[i] = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
         }
-        float v[kSphereBatch][8];
 #pragma unroll
-        for (int i = 0; i < kSphereBatch; ++i) corners<GT>(g, c[i].base, v[i]);
+        for (int i = 0; i < kSphereBatch; ++i) mn[i] = __ldg(g.cmin + c[i].base);
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
-            const int s = min(s0 + i, e - 1);
-            const float phi = interpolate(v[i], c[i].fx, c[i].fy, c[i].fz);
-            const float dl = fmaxf(rc.d_act - (phi - rc.sph_r[s]), 0.f);
-            env = (s0 + i < e) ? fmaf(dl, dl, env) : env;
+            const int s = s0 + i;
+            if (s < e && !(mn[i] > rc.sph_skip[s])) {
+                ++ngath;
+                float v[8];
+                corners<GT>(g, c[i].base, v);
+                const float phi = interpolate(v, c[i].fx, c[i].fy, c[i].fz);
+                const float dl = fmaxf(rc.d_act - (phi - rc.sph_r[s]), 0.f);
+                env = fmaf(dl, dl, env);
+            }
         }
     }
     return env;
@@ -116,14 +120,15 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
 template <typename GT, bool TRACE>
 __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
                                             const InstanceState &st, const float *q,
-                                            const float *qd, bool terminal, float *tr)
+                                            const float *qd, bool terminal, float *tr,
+                                            unsigned &ngath)
 {
     Frame F = base_frame();
     float env = 0.f;
 #pragma unroll
     for (int j = 0; j < kNJ; ++j) {
         dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
-        if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2]);
+        if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath);
     }
     const f3 tee = axpy(rc.flange_d, F.c3, F.t);
     float xi[6];
@@ -215,68 +220,42 @@ __device__ __forceinline__ float weight_factor(float m_from, float m_to, float i
     return (m_from == CUDART_INF_F) ? 0.f : expf((m_to - m_from) * inv_lambda);
 }
 
-// Merge n partials (m, z, acc[na]) at src + i*stride (i < n) into dst with a
-// common minimum; the whole block calls this.  Deterministic order over i.
-__device__ __noinline__ static void merge_partials(const float *src, int n, int stride, int na, float inv_lambda,
-                               float *s_f, float *s_red, float *dst_m, float *dst_z,
-                               float *dst_acc)
+// Barrier of the two warps (64 threads) of pair pr of this block.  Both
+// warps of a pair run the same sequence of roll-outs, so they always meet.
+__device__ __forceinline__ void pair_barrier(int pr)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float lm = CUDART_INF_F;
-    for (int i = tid; i < n; i += kBlock) lm = fminf(lm, __ldcg(src + static_cast<size_t>(i) * stride));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
-    if (lane == 0) s_red[warp] = lm;
-    __syncthreads();
-    float M = CUDART_INF_F;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) M = fminf(M, s_red[w]);
-    __syncthreads();
-    for (int i = tid; i < n; i += kBlock) {
-        const float *P = src + static_cast<size_t>(i) * stride;
-        s_f[i] = weight_factor(__ldcg(P), M, inv_lambda);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        float z = 0.f;
-        for (int i = 0; i < n; ++i) z = fmaf(s_f[i], __ldcg(src + static_cast<size_t>(i) * stride + 1), z);
-        *dst_m = M;
-        *dst_z = z;
-    }
-    for (int t = tid; t < na; t += kBlock) {
-        float acc = 0.f;
-        for (int i = 0; i < n; ++i) acc = fmaf(s_f[i], __ldcg(src + static_cast<size_t>(i) * stride + 2 + t), acc);
-        dst_acc[t] = acc;
-    }
-    __syncthreads();
+    asm volatile("bar.sync %0, 64;" ::"r"(pr + 1) : "memory");
 }
 
 // ------------------------------------------------------------------ kernel
-template <int C, int L, typename GT, bool TRACE>
+// P = 1: a warp tile holds R = 32/L roll-outs of up to C*L steps.
+// P = 2 (L = 32): two warps of a block share one roll-out, warp 2p taking
+// steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
+// totals of the first half and their partial costs through shared memory.
+template <int C, int L, int P, typename GT, bool TRACE>
 __global__ void __launch_bounds__(kBlock, 5)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
                       const __grid_constant__ IterArgs a)
 {
     static_assert(32 % L == 0 && C >= 1, "tile shape");
+    static_assert(P == 1 || (P == 2 && L == 32 && kWarps % 2 == 0), "pair tiles are whole warps");
     constexpr int R = 32 / L;
+    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
+    __shared__ float s_S[kWarps / 2 + 1][2][2];
     extern __shared__ float s_dyn[];
     typedef float PerWarp[C][kNJ][32];
     PerWarp *s_eps = reinterpret_cast<PerWarp *>(s_dyn);
     PerWarp *s_acc = reinterpret_cast<PerWarp *>(s_dyn + kWarps * C * kNJ * 32);
     __shared__ float s_state[kStateFloats];
-    __shared__ float s_blk[C * L * kNJ];
+    __shared__ float s_blk[C * L * P * kNJ];   // block accumulator [k][j], k < C*L*P (>= H, host-checked)
     __shared__ float s_wm[kWarps], s_wz[kWarps];
-    __shared__ float s_f[kGroup > kMaxGroups ? kGroup : kMaxGroups];
-    __shared__ float s_red[kWarps];
-    __shared__ float s_mz[2];
-    __shared__ unsigned s_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int seg = lane / L, sl = lane % L;
     const int H = a.H;
     static_assert(kBlock >= 44, "state loader needs 44 threads");
     load_state(a.in, s_state);
-    for (int i = tid; i < C * L * kNJ; i += kBlock) s_blk[i] = 0.f;
+    for (int i = tid; i < C * L * P * kNJ; i += kBlock) s_blk[i] = 0.f;
 #pragma unroll
     for (int s = 0; s < C; ++s)
 #pragma unroll
@@ -284,12 +263,21 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     __syncthreads();
     const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
 
-    if (!TRACE && blockIdx.x == 0 && warp == 0) initial_state_cost_warp<GT>(rc, g, st, a.c0);
+    // the last block holds the fewest roll-outs: its last warp computes the
+    // k = 0 terms before starting on its tiles
+    if (!TRACE && blockIdx.x == gridDim.x - 1 && warp == kWarps - 1)
+        initial_state_cost_warp<GT>(rc, g, st, a.c0);
 
     float run_m = CUDART_INF_F, run_z = 0.f;
     const float dt = a.dt, dt2 = a.dt * a.dt;
+    const int half = (P == 2) ? (warp & 1) : 0;
+    const int pr = warp >> 1;
+    const int kbase = half * 32 * C;
+    const int unit = (blockIdx.x * kWarps + warp) / P;
+    const int n_units = gridDim.x * kWarps / P;
+    unsigned ngath = 0;
     const int n_tiles = (a.K + R - 1) / R;
-    for (int tile = blockIdx.x * kWarps + warp; tile < n_tiles; tile += gridDim.x * kWarps) {
+    for (int tile = unit; tile < n_tiles; tile += n_units) {
         const int m = tile * R + seg;
         const bool active = m < a.K;
 
@@ -300,7 +288,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
         for (int j = 0; j < kNJ; ++j) { T[j] = 0.f; TB[j] = 0.f; }
 #pragma unroll 1
         for (int s = 0; s < C; ++s) {
-            const int k = sl * C + s;
+            const int k = kbase + sl * C + s;
             float z[8];
             const bool live = active && k < H;
             if (live) {
@@ -309,7 +297,10 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
             }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                const float e = live ? st.sigma[j] * z[j] : 0.f;
+                float e = live ? st.sigma[j] * z[j] : 0.f;
+                // precision variant: eps rounded as if stored in FP16 / BF16
+                if (a.noise_dtype == 1) e = __half2float(__float2half_rn(e));
+                else if (a.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
                 const float u = live ? __ldg(a.Ubar + k * kNJ + j) + e : 0.f;
                 s_eps[warp][s][j][lane] = e;
                 T[j] += u;
@@ -323,6 +314,25 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) TB[j] = fmaf(static_cast<float>(C), A0[j], TB[j]);
         seg_exclusive_scan<L>(TB, B0, sl);
+        if (P == 2) {
+            // A_{32C} and B_{32C} of the first half shift the second half's scans:
+            // A0 += A_{32C}, B0 += B_{32C} + (k0 - 32C) A_{32C}
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) {
+                const float At = __shfl_sync(0xffffffffu, A0[j] + T[j], 31);
+                const float Bt = __shfl_sync(0xffffffffu, B0[j] + TB[j], 31);
+                if (half == 0 && lane == 0) { s_tot[pr][j] = At; s_tot[pr][kNJ + j] = Bt; }
+            }
+            pair_barrier(pr);
+            if (half == 1) {
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) {
+                    const float a0 = s_tot[pr][j], b0 = s_tot[pr][kNJ + j];
+                    B0[j] += fmaf(static_cast<float>(sl * C), a0, b0);
+                    A0[j] += a0;
+                }
+            }
+        }
 
         // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25)
         float lsum = 0.f, lcomp = 0.f;
@@ -331,7 +341,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
         for (int j = 0; j < kNJ; ++j) { runU[j] = 0.f; runB[j] = B0[j]; }
 #pragma unroll 1
         for (int s = 0; s < C; ++s) {
-            const int k = sl * C + s;
+            const int k = kbase + sl * C + s;
             if (!(active && k < H)) break;
             float u[kNJ], q[kNJ], qd[kNJ];
             const float kp_dt = static_cast<float>(k + 1) * dt;
@@ -350,7 +360,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
                 tr_x = tr_u + kTraceCols;
             }
             float step = control_cost<TRACE>(rc, u, tr_u);
-            step += state_cost<GT, TRACE>(rc, g, st, q, qd, k + 1 == H, tr_x);
+            step += state_cost<GT, TRACE>(rc, g, st, q, qd, k + 1 == H, tr_x, ngath);
             kahan_add(lsum, lcomp, step);
         }
 
@@ -365,9 +375,16 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
             serr = serr + oe + e;
             ssum = ns;
         }
-        const float S = ssum + serr;
+        float S = ssum + serr;
+        if (P == 2) {
+            if (lane == 0) { s_S[pr][half][0] = ssum; s_S[pr][half][1] = serr; }
+            pair_barrier(pr);
+            float ns, e;
+            two_sum(s_S[pr][0][0], s_S[pr][1][0], ns, e);
+            S = ns + ((s_S[pr][0][1] + s_S[pr][1][1]) + e);
+        }
         if (TRACE) continue;
-        if (active && sl == 0 && a.costs) a.costs[m] = S;
+        if (active && sl == 0 && half == 0 && a.costs) a.costs[m] = S;
 
         // online soft-min accumulation (Eqs. 29-30)
         if (active) {
@@ -385,6 +402,12 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
         }
     }
     if (TRACE) return;
+    if (a.gathers) {
+        unsigned n = ngath;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(0xffffffffu, n, off);
+        if (lane == 0) atomicAdd(a.gathers, static_cast<unsigned long long>(n));
+    }
 
     // merge the R segments of the warp (they hold the same k slots)
 #pragma unroll
@@ -416,7 +439,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     for (int w = 0; w < kWarps; ++w) {
         if (warp == w && seg == 0) {
             for (int s = 0; s < C; ++s) {
-                const int k = sl * C + s;
+                const int k = kbase + sl * C + s;
                 if (k < H) {
 #pragma unroll
                     for (int j = 0; j < kNJ; ++j)
@@ -427,50 +450,16 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
         __syncthreads();
     }
     const int na = H * kNJ;
-    const int stride = 2 + na;
-    float *P = a.part + static_cast<size_t>(blockIdx.x) * stride;
+    const int nb = gridDim.x;
     if (tid == 0) {
         float zb = 0.f;
-        for (int w = 0; w < kWarps; ++w) zb += s_wz[w] * weight_factor(s_wm[w], Mb, a.inv_lambda);
-        P[0] = Mb;
-        P[1] = zb;
+        // a pair's two warps carry the same (m, z): count it once
+        for (int w = 0; w < kWarps; w += P) zb += s_wz[w] * weight_factor(s_wm[w], Mb, a.inv_lambda);
+        a.part[blockIdx.x] = Mb;
+        a.part[nb + blockIdx.x] = zb;
     }
-    for (int i = tid; i < na; i += kBlock) P[2 + i] = s_blk[i];
-
-    // first level: the last block of the group merges the group's partials
-    const int grp = blockIdx.x / kGroup;
-    const int g0 = grp * kGroup;
-    const int gn = min(kGroup, static_cast<int>(gridDim.x) - g0);
-    const int n_groups = (gridDim.x + kGroup - 1) / kGroup;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_flag = (atomicAdd(a.counters + 1 + grp, 1u) == static_cast<unsigned>(gn - 1)) ? 1u : 0u;
-    __syncthreads();
-    if (!s_flag) return;
-    __threadfence();
-    float *G = a.gpart + static_cast<size_t>(grp) * stride;
-    merge_partials(a.part + static_cast<size_t>(g0) * stride, gn, stride, na, a.inv_lambda, s_f,
-                   s_red, G, G + 1, G + 2);
-    if (tid == 0) a.counters[1 + grp] = 0u;
-
-    // second level: the last group merges the group partials into U*
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_flag = (atomicAdd(a.counters, 1u) == static_cast<unsigned>(n_groups - 1)) ? 1u : 0u;
-    __syncthreads();
-    if (!s_flag) return;
-    __threadfence();
-    merge_partials(a.gpart, n_groups, stride, na, a.inv_lambda, s_f, s_red, &s_mz[0], &s_mz[1],
-                   s_blk);
-    const float invZ = 1.0f / s_mz[1];
-    for (int i = tid; i < na; i += kBlock) a.Uout[i] = a.Ubar[i] + s_blk[i] * invZ;
-    const float c0 = __ldcg(a.c0);
-    if (tid == 0) {
-        a.c0[1] = s_mz[0] + c0;
-        a.counters[0] = 0u;
-    }
-    if (a.costs)
-        for (int i = tid; i < a.K; i += kBlock) a.costs[i] = __ldcg(a.costs + i) + c0;
+    float *acc_b = a.part + 2 * static_cast<size_t>(nb) + blockIdx.x;
+    for (int i = tid; i < na; i += kBlock) acc_b[static_cast<size_t>(i) * nb] = s_blk[i];
 }
 
 } // namespace pm

@@ -58,9 +58,12 @@ def test_noise_matches_oracle(K, H, it):
 
 
 # ------------------------------------------------------- one SMPC iteration
-def run_both(scene, K, H, seed, it, U=None, lam=0.05, sigma=SIGMA, dt=0.02, n_threads=0):
+def run_both(scene, K, H, seed, it, U=None, lam=0.05, sigma=SIGMA, dt=0.02, n_threads=0,
+             shape=None):
     U = np.zeros((H, 7), dtype=np.float32) if U is None else U.astype(np.float32)
     p = scene.planner()
+    if shape is not None:
+        p.set_tile_shape(*shape)
     Ug = U.copy()
     Sg = np.empty(K, dtype=np.float32)
     p.smpc_iterate(scene.q0, scene.qd0, scene.T, Ug, K, dt, lam, sigma, seed, it, costs_out=Sg)
@@ -95,6 +98,54 @@ def test_tiles_and_ragged_shapes(cfg1, K, H):
     Ug, Sg, Uo, So, wo = run_both(sc, K, H, 77, 1, U=U)
     assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL
     assert np.abs(Ug - Uo).max() <= U_ABS
+
+
+SHAPES = [(1, 16, 1), (1, 32, 1), (3, 16, 1), (2, 32, 1), (4, 32, 1), (8, 32, 1), (1, 32, 2),
+          (2, 32, 2), (4, 32, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_tile_shape(cfg1, shape):
+    """Each instantiated (C, L, P), forced, on a full and a ragged horizon."""
+    sc = cfg1[2]
+    C, L, P = shape
+    cap = C * L * P
+    for H in sorted({cap, max(1, cap - 5)}):
+        rng = np.random.default_rng(cap + H)
+        U = (rng.normal(size=(H, 7)) * 0.3).astype(np.float32)
+        Ug, Sg, Uo, So, _ = run_both(sc, 37, H, 13, 2, U=U, shape=shape)
+        assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL, (shape, H)
+        assert np.abs(Ug - Uo).max() <= U_ABS, (shape, H)
+
+
+def test_forced_shape_too_small_is_rejected(cfg1):
+    sc = cfg1[2]
+    p = sc.planner()
+    p.set_tile_shape(1, 16, 1)
+    with pytest.raises(pm.PmError) as e:
+        p.smpc_iterate(sc.q0, sc.qd0, sc.T, np.zeros((17, 7), np.float32), 8, 0.02, 0.05, SIGMA, 1, 0)
+    assert e.value.name == "PM_EINVAL"
+    with pytest.raises(pm.PmError):
+        p.set_tile_shape(5, 32, 1)
+    p.close()
+
+
+@pytest.mark.parametrize("value,expect_all", [(10.0, False), (0.0, True)])
+def test_gather_count_extremes(cfg1, value, expect_all):
+    """Far field: every sphere lookup is skipped (the cell minimum proves a
+    zero collision term); zero field: every lookup interpolates."""
+    sc = cfg1[0]
+    import paper_2512_22575_b300 as pmod
+    p = pmod.Planner(sc.robot, sc.grid_desc, sc.cp)
+    p.set_distance_field(np.full(sc.phi.shape, value, np.float32))
+    p.profile_enable(pmod.PM_PROFILE_GATHERS)
+    p.profile_gathers(reset=True)
+    K, H = 64, 32
+    p.smpc_iterate(sc.q0, sc.qd0, sc.T, np.zeros((H, 7), np.float32), K, 0.02, 0.05, SIGMA, 1, 0)
+    n = p.profile_gathers(reset=True)
+    p.close()
+    n_lookups = K * (H - 1) * len(sc.robot["sphere_radius"])
+    assert n == (n_lookups if expect_all else 0)
 
 
 def test_zero_sigma_returns_nominal(cfg1):
