@@ -208,6 +208,71 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------- ours
+def bench_batched(pm, torch, dev, stream, reps=20):
+    """Uneven-instance workload (64 arms, own K, H and field each): one
+    replan (8 iterations) of all instances as one batch (persistent kernel,
+    CUDA graph, autotuned plan) against the same replans issued one instance
+    at a time on one stream."""
+    import workloads
+    insts = workloads.load_scene("cfg3")["instances"]
+    sigma = np.full(7, 0.5, np.float32)
+    rb = workloads.panda_robot()
+    items, planners = [], []
+    units = 0
+    for i, sc in enumerate(insts):
+        p = pm.Planner(rb, sc["grid"], workloads.default_cost_params(sc["q0"]))
+        p.set_distance_field(workloads.build_scene_grid(sc))
+        planners.append(p)
+        K, H = int(sc["K"]), int(sc["H"])
+        units += K * H * 8
+        items.append(dict(ctx=p, q=torch.from_numpy(sc["q0"]).to(dev),
+                          qd=torch.from_numpy(sc["qd0"]).to(dev),
+                          T_goal=torch.from_numpy(sc["T_goal"].ravel().copy()).to(dev),
+                          U=torch.zeros((H, 7), dtype=torch.float32, device=dev),
+                          u0_out=torch.zeros(7, dtype=torch.float32, device=dev),
+                          best_cost=torch.zeros(1, dtype=torch.float32, device=dev),
+                          K=K, dt=0.02, lam=0.05, sigma=sigma, seed=300 + i, iter_index=0))
+    flags = pm.PM_BATCH_REPLAN | pm.PM_BATCH_GRAPH | pm.PM_BATCH_AUTOTUNE
+    b = pm.Batch(dev.index or 0)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            b.run(items, n_iters=8, flags=flags, stream=stream)
+        torch.cuda.synchronize()
+        t_batch = timed(lambda: b.run(items, n_iters=8, flags=flags, stream=stream))
+
+        def sequential():
+            for it in items:
+                it["ctx"].replan(it["q"], it["qd"], it["T_goal"], it["U"], it["K"], 8, 0.02, 0.05,
+                                 sigma, it["seed"], 0, u0_out=it["u0_out"], best_cost=it["best_cost"],
+                                 stream=stream)
+        sequential()
+        torch.cuda.synchronize()
+        t_seq = timed(sequential)
+    shapes, blocks, tuned_us = b.plan(items, n_iters=8, flags=flags)
+    b.close()
+    for p in planners:
+        p.close()
+    return {"workload": "64 uneven instances (K 256-4096, H 16-64, fields 64^3-128^3), one replan "
+                        "(8 iterations) each",
+            "value": units / (t_batch / 1e3), "unit": UNIT, "ms_per_batch_replan": t_batch,
+            "sequential_ms": t_seq, "sequential_value": units / (t_seq / 1e3),
+            "speedup_vs_sequential": t_seq / t_batch,
+            "plan": {"autotuned_us": tuned_us, "total_blocks": int(sum(blocks)),
+                     "shapes": sorted({f"{c}x{l}x{p_}" for c, l, p_ in shapes})}}
+
+
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
@@ -389,6 +454,8 @@ def run_ours(args, rank, world, local):
                              "ms_per_step": vms / n_v, "kernel_ms_per_launch": kms / max(kn, 1),
                              "replans": n_v}
     line["precision_variants"] = variants
+    if not args.no_batched:
+        line["batched"] = bench_batched(pm, torch, dev, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -414,6 +481,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -207,6 +207,65 @@ pm_status pm_smpc_iterate_noalloc(pm_ctx *ctx, const float *q0, const float *qd0
                                   uint32_t iter_index, float *costs_out, void *cuda_stream);
 
 /*
+ * Batched iterations: many arms, each with its own context (robot, costs,
+ * float32 distance field), K, H and inputs, advanced together in one
+ * persistent launch per SMPC iteration (Algorithm 1 for every item).  An
+ * item's roll-outs are cut into thread-block work items that a persistent
+ * grid pulls from a queue; the soft-min merge stays per item.  Every buffer
+ * of an item must be device memory of the batch's GPU (not checked).
+ *   q, qd        [7]    start state; with PM_BATCH_REPLAN replaced by the
+ *                       state after executing u0* (Sec. IV-C)
+ *   T_goal       [16]   target pose (row-major)
+ *   U            [H][7] nominal in, U* out (shifted one step with PM_BATCH_REPLAN)
+ *   costs_out    [K]    S^(m) of the last iteration, or NULL
+ *   u0_out       [7]    executed control (PM_BATCH_REPLAN), or NULL
+ *   best_cost    [1]    min_m S^(m) of the last iteration, or NULL
+ *   iteration it (0..n_iters-1) uses iter_index + it; H <= 256.
+ * pm_batch_run enqueues n_iters iterations (plus the replan step) on
+ * cuda_stream (NULL: the batch's own stream) and returns.  Flags:
+ *   PM_BATCH_REPLAN    execute u0*, advance q/qd and shift U after the iterations
+ *   PM_BATCH_GRAPH     capture the call's launches once per batch structure
+ *                      (the items' K, H and n_iters) as a CUDA graph and replay it
+ *   PM_BATCH_AUTOTUNE  the first time a structure is seen, time candidate plans
+ *                      (tile shape per item, thread blocks per item) and keep
+ *                      the fastest; otherwise a work-proportional default plan
+ * pm_batch_plan reports the plan used for a structure: shapes [n][3] as
+ * (C, L, P), blocks [n], and the autotuned time in microseconds (0 if the
+ * default plan was used).  Calls on one batch are serialised; they must not
+ * overlap on the GPU.  Errors: PM_EINVAL (item out of range, context without
+ * a float32 field or on another device), PM_ENOMEM, PM_ECUDA.
+ * The paper runs one arm; batching many is this library's addition.
+ */
+typedef struct pm_batch pm_batch;
+
+typedef struct {
+    pm_ctx *ctx;
+    float *q, *qd;
+    const float *T_goal;
+    float *U;
+    float *costs_out;
+    float *u0_out;
+    float *best_cost;
+    int K, H;
+    float dt, lambda;
+    float sigma[7];
+    uint64_t seed;
+    uint32_t iter_index;
+} pm_batch_item;
+
+#define PM_BATCH_REPLAN 1
+#define PM_BATCH_GRAPH 2
+#define PM_BATCH_AUTOTUNE 4
+
+pm_status pm_batch_create(int device, pm_batch **out);
+pm_status pm_batch_run(pm_batch *batch, const pm_batch_item *items, int n, int n_iters,
+                       int flags, void *cuda_stream);
+pm_status pm_batch_plan(pm_batch *batch, const pm_batch_item *items, int n, int n_iters,
+                        int flags, int *shapes, int *blocks, double *tuned_us);
+const char *pm_batch_last_error(pm_batch *batch);
+void pm_batch_destroy(pm_batch *batch);
+
+/*
  * Diagnostics used by the parity tests (same device code as the hot path).
  *
  * pm_philox4x32_10: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key) for

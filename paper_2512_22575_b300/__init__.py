@@ -15,8 +15,8 @@ import os
 
 import numpy as np
 
-from ._abi import (PM_BF16, PM_F16, PM_F32, PmCostParams, PmError, PmGridDesc, PmRobot,
-                   STATUS_NAMES, lib, lib_path)
+from ._abi import (PM_BF16, PM_F16, PM_F32, PmBatchItem, PmCostParams, PmError, PmGridDesc,
+                   PmRobot, STATUS_NAMES, lib, lib_path)
 
 __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
@@ -24,7 +24,7 @@ __all__ = [
     "philox4x32_10",
     "sample_noise", "rollout_trace", "profile_enable", "profile_read", "profile_gathers",
     "set_tile_shape", "set_noise_dtype", "PM_PROFILE_TIME", "PM_PROFILE_GATHERS", "destroy",
-    "last_error", "Planner",
+    "last_error", "Planner", "Batch", "PM_BATCH_REPLAN", "PM_BATCH_GRAPH", "PM_BATCH_AUTOTUNE",
 ]
 
 _DTYPES = {"f32": PM_F32, "f16": PM_F16, "bf16": PM_BF16,
@@ -245,6 +245,72 @@ def _stream(stream):
     if hasattr(stream, "cuda_stream"):
         return C.c_void_p(stream.cuda_stream)
     return C.c_void_p(int(stream))
+
+
+PM_BATCH_REPLAN, PM_BATCH_GRAPH, PM_BATCH_AUTOTUNE = 1, 2, 4
+
+
+class Batch:
+    """pm_batch_*: many contexts advanced together in one persistent launch.
+
+    Items are dicts with keys ctx (a Planner or a context handle), q, qd,
+    T_goal, U, and optionally costs_out, u0_out, best_cost (CUDA float32
+    tensors), K, dt, lam, sigma, seed, iter_index.  H is U's first dimension.
+    """
+
+    def __init__(self, device=0):
+        out = C.c_void_p()
+        _check(lib().pm_batch_create(int(device), C.byref(out)))
+        self.b = out
+
+    def _items(self, items):
+        arr = (PmBatchItem * len(items))()
+        for i, it in enumerate(items):
+            x = arr[i]
+            ctx = it["ctx"]
+            x.ctx = ctx.ctx if hasattr(ctx, "ctx") else ctx
+            H = int(it["U"].shape[0])
+            x.q = _ptr(it["q"], n=7); x.qd = _ptr(it["qd"], n=7)
+            x.T_goal = _ptr(it["T_goal"], n=16); x.U = _ptr(it["U"], n=7 * H)
+            x.costs_out = _ptr(it.get("costs_out"), n=int(it["K"]))
+            x.u0_out = _ptr(it.get("u0_out"), n=7)
+            x.best_cost = _ptr(it.get("best_cost"), n=1)
+            x.K = int(it["K"]); x.H = H
+            x.dt = float(it.get("dt", 0.02)); x.lambda_ = float(it.get("lam", 0.05))
+            sig = _f32(it.get("sigma", np.full(7, 0.5)), 7)
+            for j in range(7):
+                x.sigma[j] = float(sig[j])
+            x.seed = int(it.get("seed", 0)); x.iter_index = int(it.get("iter_index", 0))
+        return arr
+
+    def run(self, items, n_iters=1, flags=0, stream=None):
+        arr = self._items(items)
+        st = lib().pm_batch_run(self.b, arr, len(items), int(n_iters), int(flags), _stream(stream))
+        if st != 0:
+            raise PmError(st, STATUS_NAMES.get(st, str(st)), lib().pm_batch_last_error(self.b).decode())
+
+    def plan(self, items, n_iters=1, flags=0):
+        """(shapes [(C, L, P)], blocks per item, autotuned time in us or 0)."""
+        n = len(items)
+        arr = self._items(items)
+        shapes = (C.c_int * (3 * n))()
+        blocks = (C.c_int * n)()
+        us = C.c_double()
+        st = lib().pm_batch_plan(self.b, arr, n, int(n_iters), int(flags), shapes, blocks, C.byref(us))
+        if st != 0:
+            raise PmError(st, STATUS_NAMES.get(st, str(st)), lib().pm_batch_last_error(self.b).decode())
+        return ([tuple(shapes[3 * i:3 * i + 3]) for i in range(n)], list(blocks), us.value)
+
+    def close(self):
+        if self.b is not None:
+            lib().pm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Planner:

@@ -38,6 +38,13 @@ class PmCostParams(C.Structure):
                 ("w_s", C.c_float), ("w_ns", C.c_float), ("q_ref", _PF)]
 
 
+class PmBatchItem(C.Structure):
+    _fields_ = [("ctx", _V), ("q", _V), ("qd", _V), ("T_goal", _V), ("U", _V), ("costs_out", _V),
+                ("u0_out", _V), ("best_cost", _V), ("K", C.c_int), ("H", C.c_int),
+                ("dt", C.c_float), ("lambda_", C.c_float), ("sigma", C.c_float * 7),
+                ("seed", C.c_uint64), ("iter_index", C.c_uint32)]
+
+
 # Every exported entry point of include/paramap.h with its ctypes signature.
 SIGNATURES = {
     "pm_create": (C.c_int, [C.POINTER(PmRobot), C.POINTER(PmGridDesc), C.POINTER(PmCostParams),
@@ -58,6 +65,12 @@ SIGNATURES = {
     "pm_profile_gathers": (C.c_int, [_V, C.POINTER(C.c_uint64), C.c_int]),
     "pm_set_tile_shape": (C.c_int, [_V, C.c_int, C.c_int, C.c_int]),
     "pm_set_noise_dtype": (C.c_int, [_V, C.c_int]),
+    "pm_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "pm_batch_run": (C.c_int, [_V, C.POINTER(PmBatchItem), C.c_int, C.c_int, C.c_int, _V]),
+    "pm_batch_plan": (C.c_int, [_V, C.POINTER(PmBatchItem), C.c_int, C.c_int, C.c_int,
+                                C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "pm_batch_last_error": (C.c_char_p, [_V]),
+    "pm_batch_destroy": (None, [_V]),
     "pm_destroy": (None, [_V]),
     "pm_last_error": (C.c_char_p, [_V]),
     "pm_version": (C.c_char_p, []),

@@ -1,0 +1,75 @@
+// Internal definition of the context (shared by paramap.cu and batch.cu).
+#pragma once
+
+#include "paramap.h"
+#include "smpc_dispatch.h"
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+struct pm_ctx {
+    int device = 0;
+    int n_sm = 0;
+    pm::RobotConst rc{};
+    pm::RobotConst *d_rc = nullptr;     // device copy (read by the batched kernels)
+    pm_grid_desc gd{};
+    size_t grid_elems = 0;
+    void *d_grid = nullptr;
+    float *d_cmin = nullptr;            // per-cell corner minimum of the stored field
+    bool has_grid = false;
+    cudaStream_t stream = nullptr;
+    // Ring of staging slots for host inputs: slot i holds q0 [0..7], qd0
+    // [8..15] and T_goal [16..31]; its event marks the copy as done so the
+    // pinned slot can be reused.
+    float *d_stage = nullptr;
+    float *h_stage = nullptr;           // pinned
+    cudaEvent_t slot_ev[16] = {};
+    bool slot_pending[16] = {};
+    int slot = 0;
+    float *d_U = nullptr;
+    size_t cap_U = 0;
+    float *h_U = nullptr;               // pinned [PM_MAX_HORIZON * 8]
+    float *d_costs = nullptr;
+    size_t cap_costs = 0;
+    float *h_out = nullptr;             // pinned: costs / small outputs
+    size_t cap_h_out = 0;
+    float *d_part = nullptr;            // block partials
+    size_t cap_part = 0;
+
+    float *d_c0 = nullptr;              // [c0, best, q(8), qd(8), u0(8)]
+    pm::TileShape forced{0, 0, 0};          // tile shape set by pm_set_tile_shape (0 = default)
+    unsigned long long *d_gathers = nullptr;  // 8-corner lookups, counted while enabled
+    bool count_gathers = false;
+    int noise_dtype = PM_F32;           // rounding of the sampled perturbations
+    bool prof = false;                  // bracket iteration kernels with events
+    std::vector<cudaEvent_t> prof_ev;   // pairs (start, end)
+    size_t prof_used = 0;               // events recorded since the last reset
+    cudaStream_t prof_stream = nullptr;
+    std::string err;
+    std::mutex mu;
+};
+
+
+namespace pm {
+
+// Kernel view of a context's distance field.
+inline GridConst grid_const(const pm_ctx *c)
+{
+    GridConst g;
+    g.phi = c->d_grid;
+    g.cmin = c->d_cmin;
+    g.nx = c->gd.nx; g.ny = c->gd.ny; g.nz = c->gd.nz;
+    g.inv_res = 1.0f / c->gd.res;
+    g.ox = c->gd.origin[0]; g.oy = c->gd.origin[1]; g.oz = c->gd.origin[2];
+    g.mx = static_cast<float>(c->gd.nx - 1);
+    g.my = static_cast<float>(c->gd.ny - 1);
+    g.mz = static_cast<float>(c->gd.nz - 1);
+    return g;
+}
+
+// Resident blocks per SM of an iteration kernel (raises its dynamic shared
+// memory limit on first use); -1 if the limit cannot be set.
+int resident_blocks_per_sm(const void *fn, int block, size_t smem);
+
+} // namespace pm

@@ -1,8 +1,7 @@
 // C ABI of the SMPC hot path (include/paramap.h): contexts, argument checks,
 // host<->device staging and kernel dispatch.  The arithmetic lives in
 // smpc_device.cuh / smpc_kernels.cuh.
-#include "paramap.h"
-#include "smpc_dispatch.h"
+#include "ctx_internal.h"
 
 #include <algorithm>
 #include <cmath>
@@ -17,46 +16,7 @@
 
 using namespace pm;
 
-struct pm_ctx {
-    int device = 0;
-    int n_sm = 0;
-    RobotConst rc{};
-    pm_grid_desc gd{};
-    size_t grid_elems = 0;
-    void *d_grid = nullptr;
-    float *d_cmin = nullptr;            // per-cell corner minimum of the stored field
-    bool has_grid = false;
-    cudaStream_t stream = nullptr;
-    // Ring of staging slots for host inputs: slot i holds q0 [0..7], qd0
-    // [8..15] and T_goal [16..31]; its event marks the copy as done so the
-    // pinned slot can be reused.
-    float *d_stage = nullptr;
-    float *h_stage = nullptr;           // pinned
-    cudaEvent_t slot_ev[16] = {};
-    bool slot_pending[16] = {};
-    int slot = 0;
-    float *d_U = nullptr;
-    size_t cap_U = 0;
-    float *h_U = nullptr;               // pinned [PM_MAX_HORIZON * 8]
-    float *d_costs = nullptr;
-    size_t cap_costs = 0;
-    float *h_out = nullptr;             // pinned: costs / small outputs
-    size_t cap_h_out = 0;
-    float *d_part = nullptr;            // block partials
-    size_t cap_part = 0;
 
-    float *d_c0 = nullptr;              // [c0, best, q(8), qd(8), u0(8)]
-    TileShape forced{0, 0, 0};          // tile shape set by pm_set_tile_shape (0 = default)
-    unsigned long long *d_gathers = nullptr;  // 8-corner lookups, counted while enabled
-    bool count_gathers = false;
-    int noise_dtype = PM_F32;           // rounding of the sampled perturbations
-    bool prof = false;                  // bracket iteration kernels with events
-    std::vector<cudaEvent_t> prof_ev;   // pairs (start, end)
-    size_t prof_used = 0;               // events recorded since the last reset
-    cudaStream_t prof_stream = nullptr;
-    std::string err;
-    std::mutex mu;
-};
 
 namespace {
 
@@ -152,31 +112,6 @@ long long launch_blocks(long long K, TileShape sh, long long resident)
     const long long tiles = (K + R - 1) / R;
     const long long need = (tiles * sh.P + kWarps - 1) / kWarps;
     return std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)}));
-}
-
-// Resident blocks per SM of an iteration kernel; on first use also raises
-// its dynamic shared memory limit to what its tile shape needs.
-int resident_blocks_per_sm(IterKernel fn, size_t smem)
-{
-    static std::mutex mu;
-    static std::unordered_map<const void *, int> cache;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(reinterpret_cast<const void *>(fn));
-    if (it != cache.end()) return it->second;
-    if (cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess) {
-        cudaGetLastError();
-        return -1;
-    }
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, smem) != cudaSuccess) {
-        cudaGetLastError();
-        n = 1;
-    }
-    n = std::max(n, 1);
-    cache[reinterpret_cast<const void *>(fn)] = n;
-    return n;
 }
 
 size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : 2; }
@@ -350,19 +285,6 @@ pm_status ensure_capacity(pm_ctx *c, int K, int H, int nb)
     return PM_OK;
 }
 
-GridConst grid_const(const pm_ctx *c)
-{
-    GridConst g;
-    g.phi = c->d_grid;
-    g.cmin = c->d_cmin;
-    g.nx = c->gd.nx; g.ny = c->gd.ny; g.nz = c->gd.nz;
-    g.inv_res = 1.0f / c->gd.res;
-    g.ox = c->gd.origin[0]; g.oy = c->gd.origin[1]; g.oz = c->gd.origin[2];
-    g.mx = static_cast<float>(c->gd.nx - 1);
-    g.my = static_cast<float>(c->gd.ny - 1);
-    g.mz = static_cast<float>(c->gd.nz - 1);
-    return g;
-}
 
 // Validate the per-call arguments shared by iterate / replan / trace.
 pm_status check_call(pm_ctx *c, const float *q0, const float *qd0, const float *T_goal,
@@ -481,7 +403,7 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
     if (!fn) return set_err(c, trace ? PM_EINVAL : PM_EINTERNAL, "no %s kernel for C=%d L=%d P=%d",
                             trace ? "trace" : "iteration", sh.C, sh.L, sh.P);
     const size_t smem = iteration_smem_bytes(sh.C);
-    const int per_sm = resident_blocks_per_sm(fn, smem);
+    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
     if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
     const long long resident = static_cast<long long>(c->n_sm) * per_sm;
     const int nb = static_cast<int>(launch_blocks(K, sh, resident));
@@ -495,6 +417,27 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
 cudaStream_t pick_stream(pm_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
 
 } // namespace
+
+int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(fn);
+    if (it != cache.end()) return it->second;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    n = std::max(n, 1);
+    cache[fn] = n;
+    return n;
+}
 
 // ===================================================================== ABI
 extern "C" {
@@ -623,6 +566,8 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     if (!ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device), "SM count") ||
         !ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream") ||
         !ck(cudaMalloc(&c->d_grid, elems * dtype_size(gd->dtype)), "grid alloc") ||
+        !ck(cudaMalloc(&c->d_rc, sizeof(RobotConst)), "robot constants alloc") ||
+        !ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy") ||
         !ck(cudaMalloc(&c->d_cmin, elems * sizeof(float)), "cell-minimum alloc") ||
         !ck(cudaMalloc(&c->d_stage, sizeof(float) * kSlots * kSlotFloats), "staging alloc") ||
         !ck(cudaMallocHost(&c->h_stage, sizeof(float) * kSlots * kSlotFloats), "pinned staging alloc") ||
@@ -903,6 +848,7 @@ void pm_destroy(pm_ctx *c)
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         cudaFree(c->d_grid);
+        cudaFree(c->d_rc);
         cudaFree(c->d_cmin);
         cudaFree(c->d_stage);
         cudaFreeHost(c->h_stage);
@@ -985,7 +931,7 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
     IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
     if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
     const size_t smem = iteration_smem_bytes(sh.C);
-    const int per_sm = resident_blocks_per_sm(fn, smem);
+    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
     if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
     const long long resident = static_cast<long long>(c->n_sm) * per_sm;
     long long nb = launch_blocks(K, sh, resident);

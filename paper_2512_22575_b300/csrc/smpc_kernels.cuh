@@ -199,13 +199,11 @@ __device__ __noinline__ static void initial_state_cost_warp(const RobotConst &rc
 
 // ---------------------------------------------------------- warp scans
 // Exclusive prefix sum over the L lanes of each segment, for 7 values.
-template <int L>
-__device__ __forceinline__ void seg_exclusive_scan(const float *x, float *ex, int sl)
+__device__ __forceinline__ void seg_exclusive_scan(const float *x, float *ex, int sl, int L)
 {
 #pragma unroll
     for (int j = 0; j < kNJ; ++j) {
         float v = x[j];
-#pragma unroll
         for (int d = 1; d < L; d <<= 1) {
             const float t = __shfl_up_sync(0xffffffffu, v, d, L);
             if (sl >= d) v += t;
@@ -227,59 +225,59 @@ __device__ __forceinline__ void pair_barrier(int pr)
     asm volatile("bar.sync %0, 64;" ::"r"(pr + 1) : "memory");
 }
 
-// ------------------------------------------------------------------ kernel
-// P = 1: a warp tile holds R = 32/L roll-outs of up to C*L steps.
-// P = 2 (L = 32): two warps of a block share one roll-out, warp 2p taking
-// steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
-// totals of the first half and their partial costs through shared memory.
-template <int C, int L, int P, typename GT, bool TRACE>
-__global__ void __launch_bounds__(kBlock, 5)
-smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
-                      const __grid_constant__ IterArgs a)
-{
-    static_assert(32 % L == 0 && C >= 1, "tile shape");
-    static_assert(P == 1 || (P == 2 && L == 32 && kWarps % 2 == 0), "pair tiles are whole warps");
-    constexpr int R = 32 / L;
-    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
-    __shared__ float s_S[kWarps / 2 + 1][2][2];
-    extern __shared__ float s_dyn[];
-    typedef float PerWarp[C][kNJ][32];
-    PerWarp *s_eps = reinterpret_cast<PerWarp *>(s_dyn);
-    PerWarp *s_acc = reinterpret_cast<PerWarp *>(s_dyn + kWarps * C * kNJ * 32);
-    __shared__ float s_state[kStateFloats];
-    __shared__ float s_blk[C * L * P * kNJ];   // block accumulator [k][j], k < C*L*P (>= H, host-checked)
-    __shared__ float s_wm[kWarps], s_wz[kWarps];
+// The inputs of one instance's iteration as a block sees them (filled from
+// IterArgs by the single-instance kernel, from a descriptor by the batched one).
+struct TileJob {
+    const float *Ubar;          // [H][7]
+    float *costs;               // [K] or null
+    float *part;                // this instance's block partials: m [nb], z [nb], acc [H*7][nb]
+    int K, H, nb;
+    uint32_t seed_lo, seed_hi, iter;
+    float dt, inv_lambda;
+    int noise_dtype;
+};
 
+// Shared-memory arrays a block needs for run_block.
+struct BlockSmem {
+    float *eps, *acc;           // [kWarps][C][7][32] each
+    float (*tot)[2 * kNJ];      // [kWarps/2 + 1] pair scan totals
+    float (*S)[2][2];           // [kWarps/2 + 1] pair partial costs
+    float *blk;                 // [C*L*P*7] block accumulator
+    float *wm, *wz;             // [kWarps]
+};
+
+// Local block lb (of job.nb) of an instance: its roll-out tiles, then its
+// block partial (m_b, z_b, acc_b) into job.part.  Tile shape (C, L, P) as
+// described at the top of this file; called by every thread of the block.
+// With constant arguments (the single-instance kernel) the shape folds away.
+template <typename GT, bool TRACE>
+__device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst &g,
+                                          const InstanceState &st, const TileJob &job,
+                                          float *trace, const int C, const int L, const int P,
+                                          const int lb, const BlockSmem &sm, unsigned &ngath)
+{
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = 32 / L;
     const int seg = lane / L, sl = lane % L;
-    const int H = a.H;
-    static_assert(kBlock >= 44, "state loader needs 44 threads");
-    load_state(a.in, s_state);
-    for (int i = tid; i < C * L * P * kNJ; i += kBlock) s_blk[i] = 0.f;
-#pragma unroll
+    const int H = job.H;
+    auto E = [&](int w, int s, int j) { return ((w * C + s) * kNJ + j) * 32; };
+    for (int i = tid; i < C * L * P * kNJ; i += kBlock) sm.blk[i] = 0.f;
     for (int s = 0; s < C; ++s)
 #pragma unroll
-        for (int j = 0; j < kNJ; ++j) s_acc[warp][s][j][lane] = 0.f;
+        for (int j = 0; j < kNJ; ++j) sm.acc[E(warp, s, j) + lane] = 0.f;
     __syncthreads();
-    const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
-
-    // the last block holds the fewest roll-outs: its last warp computes the
-    // k = 0 terms before starting on its tiles
-    if (!TRACE && blockIdx.x == gridDim.x - 1 && warp == kWarps - 1)
-        initial_state_cost_warp<GT>(rc, g, st, a.c0);
 
     float run_m = CUDART_INF_F, run_z = 0.f;
-    const float dt = a.dt, dt2 = a.dt * a.dt;
+    const float dt = job.dt, dt2 = job.dt * job.dt;
     const int half = (P == 2) ? (warp & 1) : 0;
     const int pr = warp >> 1;
     const int kbase = half * 32 * C;
-    const int unit = (blockIdx.x * kWarps + warp) / P;
-    const int n_units = gridDim.x * kWarps / P;
-    unsigned ngath = 0;
-    const int n_tiles = (a.K + R - 1) / R;
+    const int unit = (lb * kWarps + warp) / P;
+    const int n_units = job.nb * kWarps / P;
+    const int n_tiles = (job.K + R - 1) / R;
     for (int tile = unit; tile < n_tiles; tile += n_units) {
         const int m = tile * R + seg;
-        const bool active = m < a.K;
+        const bool active = m < job.K;
 
         // sample and perturb (Algorithm 1, Eq. 27): eps ~ D, u = ubar + eps;
         // chunk sums T = sum_s u_s and TB = sum_s sum_{s'<=s} u_s' for the scans
@@ -292,17 +290,17 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
             float z[8];
             const bool live = active && k < H;
             if (live) {
-                step_normals(a.seed_lo, a.seed_hi, a.iter, static_cast<uint32_t>(m),
+                step_normals(job.seed_lo, job.seed_hi, job.iter, static_cast<uint32_t>(m),
                              static_cast<uint32_t>(k), z);
             }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
                 float e = live ? st.sigma[j] * z[j] : 0.f;
                 // precision variant: eps rounded as if stored in FP16 / BF16
-                if (a.noise_dtype == 1) e = __half2float(__float2half_rn(e));
-                else if (a.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
-                const float u = live ? __ldg(a.Ubar + k * kNJ + j) + e : 0.f;
-                s_eps[warp][s][j][lane] = e;
+                if (job.noise_dtype == 1) e = __half2float(__float2half_rn(e));
+                else if (job.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
+                const float u = live ? __ldg(job.Ubar + k * kNJ + j) + e : 0.f;
+                sm.eps[E(warp, s, j) + lane] = e;
                 T[j] += u;
                 TB[j] += T[j];
             }
@@ -310,10 +308,10 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
 
         // roll-out (Eq. 7) by two segmented prefix scans
         float A0[kNJ], B0[kNJ];
-        seg_exclusive_scan<L>(T, A0, sl);
+        seg_exclusive_scan(T, A0, sl, L);
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) TB[j] = fmaf(static_cast<float>(C), A0[j], TB[j]);
-        seg_exclusive_scan<L>(TB, B0, sl);
+        seg_exclusive_scan(TB, B0, sl, L);
         if (P == 2) {
             // A_{32C} and B_{32C} of the first half shift the second half's scans:
             // A0 += A_{32C}, B0 += B_{32C} + (k0 - 32C) A_{32C}
@@ -321,13 +319,13 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
             for (int j = 0; j < kNJ; ++j) {
                 const float At = __shfl_sync(0xffffffffu, A0[j] + T[j], 31);
                 const float Bt = __shfl_sync(0xffffffffu, B0[j] + TB[j], 31);
-                if (half == 0 && lane == 0) { s_tot[pr][j] = At; s_tot[pr][kNJ + j] = Bt; }
+                if (half == 0 && lane == 0) { sm.tot[pr][j] = At; sm.tot[pr][kNJ + j] = Bt; }
             }
             pair_barrier(pr);
             if (half == 1) {
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
-                    const float a0 = s_tot[pr][j], b0 = s_tot[pr][kNJ + j];
+                    const float a0 = sm.tot[pr][j], b0 = sm.tot[pr][kNJ + j];
                     B0[j] += fmaf(static_cast<float>(sl * C), a0, b0);
                     A0[j] += a0;
                 }
@@ -347,7 +345,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
             const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                u[j] = __ldg(a.Ubar + k * kNJ + j) + s_eps[warp][s][j][lane];
+                u[j] = __ldg(job.Ubar + k * kNJ + j) + sm.eps[E(warp, s, j) + lane];
                 runU[j] += u[j];
                 const float A = A0[j] + runU[j];           // A_{k+1}
                 runB[j] += A;                               // B_{k+1}
@@ -356,7 +354,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
             }
             float *tr_u = nullptr, *tr_x = nullptr;
             if (TRACE) {
-                tr_u = a.trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
+                tr_u = trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
                 tr_x = tr_u + kTraceCols;
             }
             float step = control_cost<TRACE>(rc, u, tr_u);
@@ -366,7 +364,6 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
 
         // S'^(m): compensated sum over the segment's lanes
         float ssum = lsum, serr = -lcomp;
-#pragma unroll
         for (int off = L / 2; off > 0; off >>= 1) {
             const float os = __shfl_xor_sync(0xffffffffu, ssum, off);
             const float oe = __shfl_xor_sync(0xffffffffu, serr, off);
@@ -377,65 +374,59 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
         }
         float S = ssum + serr;
         if (P == 2) {
-            if (lane == 0) { s_S[pr][half][0] = ssum; s_S[pr][half][1] = serr; }
+            if (lane == 0) { sm.S[pr][half][0] = ssum; sm.S[pr][half][1] = serr; }
             pair_barrier(pr);
             float ns, e;
-            two_sum(s_S[pr][0][0], s_S[pr][1][0], ns, e);
-            S = ns + ((s_S[pr][0][1] + s_S[pr][1][1]) + e);
+            two_sum(sm.S[pr][0][0], sm.S[pr][1][0], ns, e);
+            S = ns + ((sm.S[pr][0][1] + sm.S[pr][1][1]) + e);
         }
         if (TRACE) continue;
-        if (active && sl == 0 && half == 0 && a.costs) a.costs[m] = S;
+        if (active && sl == 0 && half == 0 && job.costs) job.costs[m] = S;
 
         // online soft-min accumulation (Eqs. 29-30)
         if (active) {
             const float nm = fminf(run_m, S);
-            const float f_old = weight_factor(run_m, nm, a.inv_lambda);
-            const float f_new = expf((nm - S) * a.inv_lambda);
+            const float f_old = weight_factor(run_m, nm, job.inv_lambda);
+            const float f_new = expf((nm - S) * job.inv_lambda);
             run_z = fmaf(run_z, f_old, f_new);
 #pragma unroll 1
             for (int s = 0; s < C; ++s)
 #pragma unroll
-                for (int j = 0; j < kNJ; ++j)
-                    s_acc[warp][s][j][lane] = fmaf(s_acc[warp][s][j][lane], f_old,
-                                                   f_new * s_eps[warp][s][j][lane]);
+                for (int j = 0; j < kNJ; ++j) {
+                    float &acc = sm.acc[E(warp, s, j) + lane];
+                    acc = fmaf(acc, f_old, f_new * sm.eps[E(warp, s, j) + lane]);
+                }
             run_m = nm;
         }
     }
     if (TRACE) return;
-    if (a.gathers) {
-        unsigned n = ngath;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(0xffffffffu, n, off);
-        if (lane == 0) atomicAdd(a.gathers, static_cast<unsigned long long>(n));
-    }
 
     // merge the R segments of the warp (they hold the same k slots)
-#pragma unroll
     for (int off = L; off < 32; off <<= 1) {
         const float om = __shfl_xor_sync(0xffffffffu, run_m, off);
         const float oz = __shfl_xor_sync(0xffffffffu, run_z, off);
         const float nm = fminf(run_m, om);
-        const float fa = weight_factor(run_m, nm, a.inv_lambda);
-        const float fb = weight_factor(om, nm, a.inv_lambda);
+        const float fa = weight_factor(run_m, nm, job.inv_lambda);
+        const float fb = weight_factor(om, nm, job.inv_lambda);
         run_z = run_z * fa + oz * fb;
 #pragma unroll 1
         for (int s = 0; s < C; ++s)
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                const float mine = s_acc[warp][s][j][lane];
+                float &mine = sm.acc[E(warp, s, j) + lane];
                 const float o = __shfl_xor_sync(0xffffffffu, mine, off);
-                s_acc[warp][s][j][lane] = mine * fa + o * fb;
+                mine = mine * fa + o * fb;
             }
         run_m = nm;
     }
 
     // block partial, warps merged in warp order
-    if (lane == 0) { s_wm[warp] = run_m; s_wz[warp] = run_z; }
+    if (lane == 0) { sm.wm[warp] = run_m; sm.wz[warp] = run_z; }
     __syncthreads();
     float Mb = CUDART_INF_F;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) Mb = fminf(Mb, s_wm[w]);
-    const float fw = weight_factor(run_m, Mb, a.inv_lambda);
+    for (int w = 0; w < kWarps; ++w) Mb = fminf(Mb, sm.wm[w]);
+    const float fw = weight_factor(run_m, Mb, job.inv_lambda);
     for (int w = 0; w < kWarps; ++w) {
         if (warp == w && seg == 0) {
             for (int s = 0; s < C; ++s) {
@@ -443,23 +434,78 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
                 if (k < H) {
 #pragma unroll
                     for (int j = 0; j < kNJ; ++j)
-                        s_blk[k * kNJ + j] = fmaf(fw, s_acc[warp][s][j][lane], s_blk[k * kNJ + j]);
+                        sm.blk[k * kNJ + j] = fmaf(fw, sm.acc[E(warp, s, j) + lane], sm.blk[k * kNJ + j]);
                 }
             }
         }
         __syncthreads();
     }
     const int na = H * kNJ;
-    const int nb = gridDim.x;
+    const int nb = job.nb;
     if (tid == 0) {
         float zb = 0.f;
         // a pair's two warps carry the same (m, z): count it once
-        for (int w = 0; w < kWarps; w += P) zb += s_wz[w] * weight_factor(s_wm[w], Mb, a.inv_lambda);
-        a.part[blockIdx.x] = Mb;
-        a.part[nb + blockIdx.x] = zb;
+        for (int w = 0; w < kWarps; w += P) zb += sm.wz[w] * weight_factor(sm.wm[w], Mb, job.inv_lambda);
+        job.part[lb] = Mb;
+        job.part[nb + lb] = zb;
     }
-    float *acc_b = a.part + 2 * static_cast<size_t>(nb) + blockIdx.x;
-    for (int i = tid; i < na; i += kBlock) acc_b[static_cast<size_t>(i) * nb] = s_blk[i];
+    float *acc_b = job.part + 2 * static_cast<size_t>(nb) + lb;
+    for (int i = tid; i < na; i += kBlock) acc_b[static_cast<size_t>(i) * nb] = sm.blk[i];
+}
+
+// ------------------------------------------------------------------ kernel
+// P = 1: a warp tile holds R = 32/L roll-outs of up to C*L steps.
+// P = 2 (L = 32): two warps of a block share one roll-out, warp 2p taking
+// steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
+// totals of the first half and their partial costs through shared memory.
+template <int C, int L, int P, typename GT, bool TRACE>
+__global__ void __launch_bounds__(kBlock, 5)
+smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
+                      const __grid_constant__ IterArgs a)
+{
+    static_assert(32 % L == 0 && C >= 1, "tile shape");
+    static_assert(P == 1 || (P == 2 && L == 32 && kWarps % 2 == 0), "pair tiles are whole warps");
+    static_assert(kBlock >= 44, "state loader needs 44 threads");
+    extern __shared__ float s_dyn[];
+    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
+    __shared__ float s_S[kWarps / 2 + 1][2][2];
+    __shared__ float s_state[kStateFloats];
+    __shared__ float s_blk[C * L * P * kNJ];   // block accumulator [k][j], k < C*L*P (>= H, host-checked)
+    __shared__ float s_wm[kWarps], s_wz[kWarps];
+
+    load_state(a.in, s_state);
+    __syncthreads();
+    const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
+    const int warp = threadIdx.x >> 5;
+
+    // the last block holds the fewest roll-outs: its last warp computes the
+    // k = 0 terms before starting on its tiles
+    if (!TRACE && blockIdx.x == gridDim.x - 1 && warp == kWarps - 1)
+        initial_state_cost_warp<GT>(rc, g, st, a.c0);
+
+    TileJob job;
+    job.Ubar = a.Ubar;
+    job.costs = a.costs;
+    job.part = a.part;
+    job.K = a.K;
+    job.H = a.H;
+    job.nb = gridDim.x;
+    job.seed_lo = a.seed_lo;
+    job.seed_hi = a.seed_hi;
+    job.iter = a.iter;
+    job.dt = a.dt;
+    job.inv_lambda = a.inv_lambda;
+    job.noise_dtype = a.noise_dtype;
+    BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz};
+    unsigned ngath = 0;
+    run_block<GT, TRACE>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
+    if (!TRACE && a.gathers) {
+        const int lane = threadIdx.x & 31;
+        unsigned n = ngath;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(0xffffffffu, n, off);
+        if (lane == 0) atomicAdd(a.gathers, static_cast<unsigned long long>(n));
+    }
 }
 
 } // namespace pm
