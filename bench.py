@@ -273,6 +273,139 @@ def bench_batched(pm, torch, dev, stream, reps=20):
                      "shapes": sorted({f"{c}x{l}x{p_}" for c, l, p_ in shapes})}}
 
 
+SERVE_RATES = (500, 1000, 2000, 3000, 4000, 6000)
+
+
+def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, deadline_ms=10.0,
+                  seed=7, spin_us=5000):
+    """Serving workload: Poisson replan requests from 256 arms (own field of
+    96^3-128^3 at 1 cm each; per request K in {512, 1024, 2048, 4096}, H in
+    {16, 32, 48, 64}, 8 iterations, warm start from the arm's resident
+    sequence, 10 ms admission deadline) at each offered rate, once through
+    the server (continuous batching) and once as per-request plain
+    pm_replan calls in arrival order on one stream.  Latency runs from the
+    request's scheduled arrival to its result on the host."""
+    import workloads
+    from concurrent.futures import ThreadPoolExecutor
+    scenes = workloads.load_scene("cfg5")["instances"]
+    rb = workloads.panda_robot()
+    with ThreadPoolExecutor(max(1, min(32, os.cpu_count() or 1))) as ex:
+        fields = list(ex.map(workloads.build_scene_grid, scenes))
+    dev_i = dev.index or 0
+    planners = []
+    for sc, phi in zip(scenes, fields):
+        p = pm.Planner(rb, sc["grid"], workloads.default_cost_params(sc["q0"]), device=dev_i)
+        p.set_distance_field(phi)
+        planners.append(p)
+    del fields
+    n_arms = len(planners)
+    q0 = [sc["q0"].astype(np.float32) for sc in scenes]
+    qd0 = [sc["qd0"].astype(np.float32) for sc in scenes]
+    Tg = [sc["T_goal"].astype(np.float32).ravel().copy() for sc in scenes]
+    sigma = np.full(7, 0.5, np.float32)
+    rng = np.random.default_rng(seed)
+    deadline_s = deadline_ms / 1e3
+
+    def arrivals(rate):
+        n = max(1, int(rate * duration_s))
+        return (np.cumsum(rng.exponential(1.0 / rate, n)), rng.integers(0, n_arms, n),
+                rng.choice([512, 1024, 2048, 4096], n), rng.choice([16, 32, 48, 64], n))
+
+    def spin_until(t):
+        while time.perf_counter() < t:
+            pass
+
+    def summary(lat_s, n, span_s):
+        lat = np.asarray(lat_s) * 1e3
+        ok = len(lat)
+        return {"p50_ms": float(np.percentile(lat, 50)) if ok else None,
+                "p99_ms": float(np.percentile(lat, 99)) if ok else None,
+                "plans_s": ok / span_s if span_s > 0 else 0.0,
+                "completed": ok, "missed_deadline": n - ok}
+
+    srv = pm.Server(dev_i, max_batch=64, max_inflight=2, spin_us=spin_us)
+    arm_ids = [srv.add_arm(p) for p in planners]
+    stream = torch.cuda.Stream(device=dev)
+    U_plain = [torch.zeros((256, 7), dtype=torch.float32, device=dev) for _ in range(n_arms)]
+    H_plain = [0] * n_arms
+    rounds = [0] * n_arms
+
+    def served(t_arr, arm, K, H):
+        tickets, late = [], []
+        st0 = srv.stats()
+        t0 = time.perf_counter() + 0.01
+        for i in range(len(t_arr)):
+            spin_until(t0 + t_arr[i])
+            a = int(arm[i])
+            late.append(time.perf_counter() - (t0 + t_arr[i]))
+            tickets.append(srv.submit(arm_ids[a], q0[a], qd0[a], Tg[a], int(K[i]), int(H[i]), n_iters,
+                                      seed=1000 + a, iter_index=rounds[a] * n_iters,
+                                      deadline_us=int(deadline_ms * 1e3)))
+            rounds[a] += 1
+        lat, sizes, queue, t_end = [], [], [], t0
+        for i, tk in enumerate(tickets):
+            r = srv.wait(tk, timeout_us=60_000_000)
+            if r["status"] == "PM_OK":
+                lat.append(late[i] + r["latency_us"] * 1e-6)
+                sizes.append(r["batch_size"])
+                queue.append(r["queue_us"])
+                t_end = max(t_end, t0 + t_arr[i] + lat[-1])
+        st1 = srv.stats()
+        out = summary(lat, len(t_arr), t_end - t0)
+        out["mean_batch"] = float(np.mean(sizes)) if sizes else 0.0
+        out["queue_ms_p50"] = float(np.percentile(queue, 50)) * 1e-3 if queue else None
+        nb = st1["batches"] - st0["batches"]
+        out["launch_host_ms_mean"] = (st1["launch_host_us"] - st0["launch_host_us"]) * 1e-3 / max(nb, 1)
+        out["batch_run_ms_mean"] = (st1["batch_run_us"] - st0["batch_run_us"]) * 1e-3 / max(nb, 1)
+        return out
+
+    def plain(t_arr, arm, K, H):
+        lat = []
+        u0h, besth = np.empty(7, np.float32), np.empty(1, np.float32)
+        t0 = time.perf_counter() + 0.01
+        t_end = t0
+        with torch.cuda.stream(stream):
+            for i in range(len(t_arr)):
+                arrive = t0 + t_arr[i]
+                spin_until(arrive)
+                if time.perf_counter() - arrive > deadline_s:
+                    continue                      # not started within the deadline
+                a, h = int(arm[i]), int(H[i])
+                U = U_plain[a]
+                if 0 < H_plain[a] < h:            # warm start: extend with the last row
+                    U[H_plain[a]:h] = U[H_plain[a] - 1]
+                elif H_plain[a] == 0:
+                    U[:h].zero_()
+                planners[a].replan(q0[a].copy(), qd0[a].copy(), Tg[a], U[:h], int(K[i]), n_iters, 0.02,
+                                   0.05, sigma, 1000 + a, rounds[a], u0_out=u0h, best_cost=besth,
+                                   stream=stream)
+                rounds[a] += 1
+                H_plain[a] = h
+                t_end = time.perf_counter()
+                lat.append(t_end - arrive)
+        return summary(lat, len(t_arr), t_end - t0)
+
+    # warm up both paths (kernel loading, plan caches, pinned staging)
+    w = arrivals(2000)
+    served(*[x[:200] for x in w])
+    plain(*[x[:50] for x in w])
+    torch.cuda.synchronize()
+    results = []
+    for rate in rates:
+        a = arrivals(rate)
+        results.append({"offered_per_s": rate, "requests": len(a[0]),
+                        "served": served(*a), "plain": plain(*a)})
+    stats = srv.stats()
+    srv.close()
+    for p in planners:
+        p.close()
+    return {"workload": f"{n_arms} arms, fields 96^3-128^3 at 1 cm, Poisson requests with K in "
+                        "{512,1024,2048,4096}, H in {16,32,48,64}, 8 iterations, warm start, "
+                        f"{deadline_ms:g} ms admission deadline, {duration_s:g} s per rate",
+            "latency": "scheduled arrival to result on the host", "rates": results,
+            "server_stats": stats}
+
+
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
@@ -456,6 +589,8 @@ def run_ours(args, rank, world, local):
     line["precision_variants"] = variants
     if not args.no_batched:
         line["batched"] = bench_batched(pm, torch, dev, stream)
+    if not args.no_serving:
+        line["serving"] = bench_serving(pm, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -482,6 +617,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -225,7 +225,9 @@ pm_status pm_smpc_iterate_noalloc(pm_ctx *ctx, const float *q0, const float *qd0
  * cuda_stream (NULL: the batch's own stream) and returns.  Flags:
  *   PM_BATCH_REPLAN    execute u0*, advance q/qd and shift U after the iterations
  *   PM_BATCH_GRAPH     capture the call's launches once per batch structure
- *                      (the items' K, H and n_iters) as a CUDA graph and replay it
+ *                      (the items' K, H and n_iters) as a CUDA graph and replay it;
+ *                      up to 64 graphs and 1024 plans are cached per batch, the
+ *                      cache starts over when full
  *   PM_BATCH_AUTOTUNE  the first time a structure is seen, time candidate plans
  *                      (tile shape per item, thread blocks per item) and keep
  *                      the fastest; otherwise a work-proportional default plan
@@ -264,6 +266,86 @@ pm_status pm_batch_plan(pm_batch *batch, const pm_batch_item *items, int n, int 
                         int flags, int *shapes, int *blocks, double *tuned_us);
 const char *pm_batch_last_error(pm_batch *batch);
 void pm_batch_destroy(pm_batch *batch);
+
+/*
+ * Replanning server (continuous batching; the paper runs one arm at 50 Hz,
+ * Sec. V -- serving many arms is this library's addition).
+ * pm_server_create starts a scheduler thread on `device`.  Arms are
+ * registered with pm_server_add_arm (a context with a float32 field; the
+ * server keeps the arm's nominal sequence resident on the device, 2 x 7 KiB).
+ * pm_submit copies a request and returns a ticket at once; the scheduler
+ * batches pending requests -- at most one per arm and one n_iters per
+ * batch, oldest first, admitted while free device memory covers the batch's
+ * workspace plus cfg.hbm_headroom -- and runs each batch as one replan of
+ * every request (n_iters iterations of Algorithm 1, then u0* executed and the
+ * sequence shifted, Sec. IV-C), with up to cfg.max_inflight batches on the
+ * GPU at once.  A request with warm_start starts from its arm's resident
+ * sequence (truncated or extended with the last row to its H), otherwise
+ * from zeros; on success the arm keeps the shifted result.  pm_poll returns
+ * PM_ENOTREADY while the ticket is pending and the result (then forgets it);
+ * pm_wait blocks up to timeout_us.  A request not admitted within
+ * deadline_us (0 = none) completes with status PM_EBUSY; a failed batch
+ * completes its requests with the error and leaves their arms' sequences
+ * unchanged.  A batch of one request runs on the single-instance kernels.
+ * All device and pinned workspace is reserved by pm_server_create (about
+ * 8.5 MiB per in-flight slot on 148 SMs plus the batch engine's), so
+ * serving allocates nothing.  A registered context may still be used
+ * directly, but its distance field must not change while requests of its
+ * arm are pending.  Errors of the calls themselves: PM_EINVAL (unknown arm
+ * or ticket, argument out of range or not finite), PM_ENOMEM, PM_EBUSY
+ * (server stopping).
+ */
+typedef struct pm_server pm_server;
+
+typedef struct {
+    int max_batch;          /* requests per batch (default 64)             */
+    int max_inflight;       /* batches on the GPU at once (default 2)      */
+    size_t hbm_headroom;    /* bytes kept free on the device (256 MiB)     */
+    int batch_flags;        /* PM_BATCH_GRAPH / PM_BATCH_AUTOTUNE (0)      */
+    uint32_t spin_us;       /* the scheduler busy-polls (one host core) for
+                               this long after its last activity before it
+                               sleeps; 0 = always sleep (default 5000)     */
+} pm_server_config;
+
+typedef struct {
+    uint32_t arm;
+    float q[7], qd[7];      /* current state                               */
+    float T_goal[16];       /* target pose, row-major                      */
+    int K, H, n_iters;
+    float dt, lambda;
+    float sigma[7];
+    uint64_t seed;
+    uint32_t iter_index;    /* first iteration index of the replan         */
+    uint32_t deadline_us;   /* admission deadline after submit; 0 = none   */
+    int warm_start;
+} pm_request;
+
+typedef struct {
+    pm_status status;
+    float u0[7];            /* executed control u0*                        */
+    float q_next[7], qd_next[7];
+    float best_cost;        /* min S of the last iteration                 */
+    double latency_us;      /* submit to completion                        */
+    double queue_us;        /* submit to the launch of its batch           */
+    int batch_size;
+} pm_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, rejected, deferred, batches, batched_requests;
+    double launch_host_us;  /* host time spent forming and enqueuing batches */
+    double batch_run_us;    /* sum over batches of launch to completion seen */
+} pm_server_stats;
+
+pm_status pm_server_create(int device, const pm_server_config *cfg, pm_server **out);
+pm_status pm_server_add_arm(pm_server *server, pm_ctx *ctx, uint32_t *arm_id);
+pm_status pm_submit(pm_server *server, const pm_request *req, uint64_t *ticket);
+/* n requests at once (all validated first: PM_EINVAL submits none), queued
+ * together so that the scheduler sees all of them in its next batch. */
+pm_status pm_submit_many(pm_server *server, const pm_request *reqs, int n, uint64_t *tickets);
+pm_status pm_poll(pm_server *server, uint64_t ticket, pm_result *out);
+pm_status pm_wait(pm_server *server, uint64_t ticket, uint32_t timeout_us, pm_result *out);
+pm_status pm_server_get_stats(pm_server *server, pm_server_stats *out);
+void pm_server_destroy(pm_server *server);
 
 /*
  * Diagnostics used by the parity tests (same device code as the hot path).

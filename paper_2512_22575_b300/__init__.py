@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 from ._abi import (PM_BF16, PM_F16, PM_F32, PmBatchItem, PmCostParams, PmError, PmGridDesc,
-                   PmRobot, STATUS_NAMES, lib, lib_path)
+                   PmRequest, PmResult, PmRobot, PmServerConfig, PmServerStats, STATUS_NAMES, lib,
+                   lib_path)
 
 __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
@@ -24,7 +25,7 @@ __all__ = [
     "philox4x32_10",
     "sample_noise", "rollout_trace", "profile_enable", "profile_read", "profile_gathers",
     "set_tile_shape", "set_noise_dtype", "PM_PROFILE_TIME", "PM_PROFILE_GATHERS", "destroy",
-    "last_error", "Planner", "Batch", "PM_BATCH_REPLAN", "PM_BATCH_GRAPH", "PM_BATCH_AUTOTUNE",
+    "last_error", "Planner", "Batch", "Server", "PM_BATCH_REPLAN", "PM_BATCH_GRAPH", "PM_BATCH_AUTOTUNE",
 ]
 
 _DTYPES = {"f32": PM_F32, "f16": PM_F16, "bf16": PM_BF16,
@@ -305,6 +306,101 @@ class Batch:
         if self.b is not None:
             lib().pm_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """pm_server_*: continuously batched replanning for many arms.
+
+    submit() copies a request and returns a ticket; poll() returns None while
+    it is pending, else a dict with status (a STATUS_NAMES string), u0,
+    q_next, qd_next, best_cost, latency_us, queue_us and batch_size."""
+
+    def __init__(self, device=0, max_batch=64, max_inflight=2, hbm_headroom=256 << 20,
+                 batch_flags=0, spin_us=5000):
+        cfg = PmServerConfig(int(max_batch), int(max_inflight), int(hbm_headroom), int(batch_flags),
+                             int(spin_us))
+        out = C.c_void_p()
+        _check(lib().pm_server_create(int(device), C.byref(cfg), C.byref(out)))
+        self.s = out
+
+    def add_arm(self, planner):
+        aid = C.c_uint32()
+        _check(lib().pm_server_add_arm(self.s, planner.ctx if hasattr(planner, "ctx") else planner,
+                                       C.byref(aid)))
+        return aid.value
+
+    @staticmethod
+    def _request(arm, q, qd, T_goal, K, H, n_iters=8, dt=0.02, lam=0.05, sigma=None, seed=0,
+                 iter_index=0, deadline_us=0, warm_start=True, r=None):
+        r = PmRequest() if r is None else r
+        r.arm = int(arm)
+        q = _f32(q, 7); qd = _f32(qd, 7); T = _f32(T_goal, 16)
+        sig = _f32(np.full(7, 0.5) if sigma is None else sigma, 7)
+        for j in range(7):
+            r.q[j] = float(q[j]); r.qd[j] = float(qd[j]); r.sigma[j] = float(sig[j])
+        for j in range(16):
+            r.T_goal[j] = float(T[j])
+        r.K, r.H, r.n_iters = int(K), int(H), int(n_iters)
+        r.dt, r.lambda_ = float(dt), float(lam)
+        r.seed, r.iter_index = int(seed), int(iter_index)
+        r.deadline_us, r.warm_start = int(deadline_us), int(bool(warm_start))
+        return r
+
+    def submit(self, arm, q, qd, T_goal, K, H, n_iters=8, **kw):
+        """pm_submit; further keyword arguments dt, lam, sigma, seed,
+        iter_index, deadline_us, warm_start."""
+        r = self._request(arm, q, qd, T_goal, K, H, n_iters, **kw)
+        t = C.c_uint64()
+        _check(lib().pm_submit(self.s, C.byref(r), C.byref(t)))
+        return t.value
+
+    def submit_many(self, requests):
+        """pm_submit_many: requests is a list of dicts with submit()'s
+        arguments; returns the tickets in order."""
+        n = len(requests)
+        arr = (PmRequest * n)()
+        for i, kw in enumerate(requests):
+            self._request(r=arr[i], **kw)
+        t = (C.c_uint64 * n)()
+        _check(lib().pm_submit_many(self.s, arr, n, t))
+        return list(t)
+
+    @staticmethod
+    def _result(res):
+        return {"status": STATUS_NAMES.get(res.status, str(res.status)),
+                "u0": np.array(res.u0[:], np.float32), "q_next": np.array(res.q_next[:], np.float32),
+                "qd_next": np.array(res.qd_next[:], np.float32), "best_cost": res.best_cost,
+                "latency_us": res.latency_us, "queue_us": res.queue_us, "batch_size": res.batch_size}
+
+    def poll(self, ticket):
+        res = PmResult()
+        st = lib().pm_poll(self.s, C.c_uint64(int(ticket)), C.byref(res))
+        if st == 6:  # PM_ENOTREADY
+            return None
+        _check(st)
+        return self._result(res)
+
+    def wait(self, ticket, timeout_us=10_000_000):
+        res = PmResult()
+        st = lib().pm_wait(self.s, C.c_uint64(int(ticket)), int(timeout_us), C.byref(res))
+        _check(st)
+        return self._result(res)
+
+    def stats(self):
+        st = PmServerStats()
+        _check(lib().pm_server_get_stats(self.s, C.byref(st)))
+        return {n: getattr(st, n) for n, _ in PmServerStats._fields_}
+
+    def close(self):
+        if self.s is not None:
+            lib().pm_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

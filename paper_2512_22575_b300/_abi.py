@@ -45,6 +45,31 @@ class PmBatchItem(C.Structure):
                 ("seed", C.c_uint64), ("iter_index", C.c_uint32)]
 
 
+class PmServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int), ("max_inflight", C.c_int), ("hbm_headroom", C.c_size_t),
+                ("batch_flags", C.c_int), ("spin_us", C.c_uint32)]
+
+
+class PmRequest(C.Structure):
+    _fields_ = [("arm", C.c_uint32), ("q", C.c_float * 7), ("qd", C.c_float * 7),
+                ("T_goal", C.c_float * 16), ("K", C.c_int), ("H", C.c_int), ("n_iters", C.c_int),
+                ("dt", C.c_float), ("lambda_", C.c_float), ("sigma", C.c_float * 7),
+                ("seed", C.c_uint64), ("iter_index", C.c_uint32), ("deadline_us", C.c_uint32),
+                ("warm_start", C.c_int)]
+
+
+class PmResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("u0", C.c_float * 7), ("q_next", C.c_float * 7),
+                ("qd_next", C.c_float * 7), ("best_cost", C.c_float), ("latency_us", C.c_double),
+                ("queue_us", C.c_double), ("batch_size", C.c_int)]
+
+
+class PmServerStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "deferred",
+                                          "batches", "batched_requests")] + \
+               [("launch_host_us", C.c_double), ("batch_run_us", C.c_double)]
+
+
 # Every exported entry point of include/paramap.h with its ctypes signature.
 SIGNATURES = {
     "pm_create": (C.c_int, [C.POINTER(PmRobot), C.POINTER(PmGridDesc), C.POINTER(PmCostParams),
@@ -71,6 +96,14 @@ SIGNATURES = {
                                 C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "pm_batch_last_error": (C.c_char_p, [_V]),
     "pm_batch_destroy": (None, [_V]),
+    "pm_server_create": (C.c_int, [C.c_int, C.POINTER(PmServerConfig), C.POINTER(C.c_void_p)]),
+    "pm_server_add_arm": (C.c_int, [_V, _V, C.POINTER(C.c_uint32)]),
+    "pm_submit": (C.c_int, [_V, C.POINTER(PmRequest), C.POINTER(C.c_uint64)]),
+    "pm_submit_many": (C.c_int, [_V, C.POINTER(PmRequest), C.c_int, C.POINTER(C.c_uint64)]),
+    "pm_poll": (C.c_int, [_V, C.c_uint64, C.POINTER(PmResult)]),
+    "pm_wait": (C.c_int, [_V, C.c_uint64, C.c_uint32, C.POINTER(PmResult)]),
+    "pm_server_get_stats": (C.c_int, [_V, C.POINTER(PmServerStats)]),
+    "pm_server_destroy": (None, [_V]),
     "pm_destroy": (None, [_V]),
     "pm_last_error": (C.c_char_p, [_V]),
     "pm_version": (C.c_char_p, []),

@@ -171,6 +171,9 @@ struct Plan {
     std::string how;
 };
 
+constexpr size_t kMaxPlans = 1024;   // cached plans per engine
+constexpr size_t kMaxGraphs = 64;    // cached executable graphs per engine
+
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int n_inst = 0;
@@ -452,6 +455,37 @@ pm_status time_candidate(pm_batch *b, const pm_batch_item *it, int n, int n_iter
 
 } // namespace
 
+pm_status pm::batch_reserve(pm_batch *b, int max_items, int flags)
+{
+    if (!b || max_items < 1) return PM_EINVAL;
+    std::lock_guard<std::mutex> lk(b->mu);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    struct Restore { int p, d; ~Restore() { if (p >= 0 && p != d) cudaSetDevice(p); } } restore{prev, b->device};
+    if (b->pending) {
+        PM_BCUDA(b, cudaEventSynchronize(b->done));
+        b->pending = false;
+    }
+    // make_plan gives each item max(1, min(need, share)) blocks with shares
+    // rounding to at most scale * resident + n/2 in all
+    const size_t n = static_cast<size_t>(max_items);
+    const double scale = (flags & PM_BATCH_AUTOTUNE) ? 4.0 : 1.0;
+    const size_t work = static_cast<size_t>(scale * b->n_sm * b->blocks_per_sm) + 2 * n;
+    const size_t rows = n * ((kBatchMaxSteps * kNJ + kBatchMergeWarps - 1) / kBatchMergeWarps);
+    pm_status st;
+    if ((st = grow_dev(b, &b->d_inst, &b->cap_inst, n)) != PM_OK) return st;
+    if ((st = grow_host(b, &b->h_inst, &b->cap_hinst, n)) != PM_OK) return st;
+    if ((st = grow_dev(b, &b->d_work, &b->cap_work, work)) != PM_OK) return st;
+    if ((st = grow_host(b, &b->h_work, &b->cap_hwork, work)) != PM_OK) return st;
+    if ((st = grow_dev(b, &b->d_rows, &b->cap_rows, rows)) != PM_OK) return st;
+    if ((st = grow_host(b, &b->h_rows, &b->cap_hrows, rows)) != PM_OK) return st;
+    if ((st = grow_dev(b, &b->d_part, &b->cap_part, work * (2 + static_cast<size_t>(kBatchMaxSteps) * kNJ))) != PM_OK)
+        return st;
+    if ((st = grow_dev(b, &b->d_c0, &b->cap_c0, 2 * n)) != PM_OK) return st;
+    return grow_dev(b, &b->d_queue, &b->cap_queue, static_cast<size_t>(1024));
+}
+
 // ========================================================================= ABI
 extern "C" {
 
@@ -502,6 +536,7 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
     const std::string key = structure_key(items, n, n_iters, flags);
     auto pit = b->plans.find(key);
     if (pit == b->plans.end()) {
+        if (b->plans.size() >= kMaxPlans) b->plans.clear();   // bounded cache: start over
         Plan best = make_plan(b, items, n, 1.0, false);
         if (flags & PM_BATCH_AUTOTUNE) {
             double best_us = 1e30;
@@ -525,6 +560,12 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
     if ((st = grow_dev(b, &b->d_queue, &b->cap_queue, static_cast<size_t>(n_iters))) != PM_OK) return st;
 
     if (flags & PM_BATCH_GRAPH) {
+        if (b->graphs.size() >= kMaxGraphs && !b->graphs.count(key)) {
+            // bounded cache; an executable graph still running is freed when it completes
+            for (auto &kv : b->graphs)
+                if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            b->graphs.clear();
+        }
         GraphEntry &g = b->graphs[key];
         if (!g.exec || g.gen != b->gen || g.n_inst != n) {
             if (g.exec) cudaGraphExecDestroy(g.exec);

@@ -72,4 +72,20 @@ inline GridConst grid_const(const pm_ctx *c)
 // memory limit on first use); -1 if the limit cannot be set.
 int resident_blocks_per_sm(const void *fn, int block, size_t smem);
 
+// One replan (n_iters iterations with the shape-specialised kernels, then u0*
+// executed and U shifted) on stream s, with the block partials and the
+// [c0, best] pair in caller-owned device scratch instead of the context's,
+// so that nothing is allocated.  Inputs, U and outputs are device pointers;
+// q_out / qd_out may alias in.q0 / in.qd0.  Uses fewer blocks when the
+// partials would not fit part_floats.
+pm_status replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &in, float *U, int K, int H,
+                              int n_iters, float dt, float lambda, uint64_t seed, uint32_t iter0,
+                              float *part, size_t part_floats, float *c0, float *q_out, float *qd_out,
+                              float *u0_out, float *best_out);
+
+// Grow a batch's workspace (device and pinned) to what any call with up to
+// max_items items of up to kMaxHorizon steps needs under the given flags, so
+// that later calls allocate nothing.
+pm_status batch_reserve(pm_batch *b, int max_items, int flags);
+
 } // namespace pm

@@ -439,6 +439,35 @@ int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
     return n;
 }
 
+pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &in, float *U, int K, int H,
+                                  int n_iters, float dt, float lambda, uint64_t seed, uint32_t iter0,
+                                  float *part, size_t part_floats, float *c0, float *q_out, float *qd_out,
+                                  float *u0_out, float *best_out)
+{
+    std::lock_guard<std::mutex> lk(c->mu);
+    TileShape sh;
+    pm_status st = pick_shape(c, H, sh);
+    if (st != PM_OK) return st;
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
+    if (!fn) return set_err(c, PM_EINTERNAL, "no iteration kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
+    const size_t smem = iteration_smem_bytes(sh.C);
+    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
+    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
+    long long nb = launch_blocks(K, sh, static_cast<long long>(c->n_sm) * per_sm);
+    const size_t per_block = 2 + static_cast<size_t>(H) * kNJ;
+    while (nb > 1 && static_cast<size_t>(nb) * per_block > part_floats) --nb;   // fewer, longer blocks
+    if (static_cast<size_t>(nb) * per_block > part_floats)
+        return set_err(c, PM_EINVAL, "H=%d needs more than %zu floats of partials", H, part_floats);
+    for (int it = 0; it < n_iters; ++it) {
+        st = enqueue_iteration(c, s, fn, static_cast<int>(nb), smem, in, U, U, nullptr, part, c0, K, H, dt,
+                               lambda, seed, iter0 + static_cast<uint32_t>(it), false, nullptr, nullptr);
+        if (st != PM_OK) return st;
+    }
+    replan_advance_kernel<<<1, 256, 0, s>>>(in.q0, in.qd0, U, H, dt, q_out, qd_out, u0_out, c0, best_out);
+    PM_CUDA(c, cudaGetLastError());
+    return PM_OK;
+}
+
 // ===================================================================== ABI
 extern "C" {
 
