@@ -17,6 +17,11 @@ struct pm_ctx {
     size_t grid_elems = 0;
     void *d_grid = nullptr;
     float *d_cmin = nullptr;            // per-cell corner minimum of the stored field
+    // The same minimum, widened to the 3x3x3 neighbouring cells, in a 3-D
+    // array of (nx-1) x (ny-1) x (nz-1) cells read through a point-sampled
+    // texture (see GridConst::cmin_tex).
+    cudaArray_t cmin_arr = nullptr;
+    cudaTextureObject_t cmin_tex = 0;
     bool has_grid = false;
     cudaStream_t stream = nullptr;
     // Ring of staging slots for host inputs: slot i holds q0 [0..7], qd0
@@ -59,9 +64,12 @@ inline GridConst grid_const(const pm_ctx *c)
     GridConst g;
     g.phi = c->d_grid;
     g.cmin = c->d_cmin;
+    g.cmin_tex = c->cmin_tex;
     g.nx = c->gd.nx; g.ny = c->gd.ny; g.nz = c->gd.nz;
     g.inv_res = 1.0f / c->gd.res;
-    g.ox = c->gd.origin[0]; g.oy = c->gd.origin[1]; g.oz = c->gd.origin[2];
+    g.bx = static_cast<float>(-static_cast<double>(c->gd.origin[0]) / c->gd.res - 0.5);
+    g.by = static_cast<float>(-static_cast<double>(c->gd.origin[1]) / c->gd.res - 0.5);
+    g.bz = static_cast<float>(-static_cast<double>(c->gd.origin[2]) / c->gd.res - 0.5);
     g.mx = static_cast<float>(c->gd.nx - 1);
     g.my = static_cast<float>(c->gd.ny - 1);
     g.mz = static_cast<float>(c->gd.nz - 1);

@@ -50,9 +50,16 @@ struct GridConst {
     const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16
     const float *cmin;            // [nz][ny][nx]: min of the 8 corners of the cell
                                   // with base voxel (i, j, l), as the lookup reads them
+    // cmin widened to the 3x3x3 neighbourhood of cells, as a point-sampled
+    // texture over the (nx-1) x (ny-1) x (nz-1) cells (clamped addressing,
+    // unnormalised coordinates): fetched at a grid coordinate g it returns
+    // the cell floor(g) clamped into range -- the cell the lookup uses, or,
+    // where the texture unit's fixed-point coordinates round across a cell
+    // face, its neighbour, whose widened minimum also covers the cell.
+    cudaTextureObject_t cmin_tex;
     int nx, ny, nz;
     float inv_res;
-    float ox, oy, oz;             // origin
+    float bx, by, bz;             // -origin / res - 1/2: grid coordinate g = p / res + b
     float mx, my, mz;             // n - 1 (clamp bound)
 };
 
@@ -212,11 +219,26 @@ struct Cell { int base; float fx, fy, fz; };
 __device__ __forceinline__ Cell locate(const GridConst &g, f3 p)
 {
     Cell c;
-    const int ix = cell((p.x - g.ox) * g.inv_res - 0.5f, g.mx, g.nx, c.fx);
-    const int iy = cell((p.y - g.oy) * g.inv_res - 0.5f, g.my, g.ny, c.fy);
-    const int iz = cell((p.z - g.oz) * g.inv_res - 0.5f, g.mz, g.nz, c.fz);
+    const int ix = cell(fmaf(p.x, g.inv_res, g.bx), g.mx, g.nx, c.fx);
+    const int iy = cell(fmaf(p.y, g.inv_res, g.by), g.my, g.ny, c.fy);
+    const int iz = cell(fmaf(p.z, g.inv_res, g.bz), g.mz, g.nz, c.fz);
     c.base = (iz * g.ny + iy) * g.nx + ix;
     return c;
+}
+
+// Index of a coordinate's cell only (no fraction): same clamp and floor as cell().
+__device__ __forceinline__ int cell_index(float g, float gmax, int n)
+{
+    return min(static_cast<int>(fminf(fmaxf(g, 0.0f), gmax)), n - 2);
+}
+
+// Base voxel offset of a point's cell, as locate() finds it.
+__device__ __forceinline__ int cell_base(const GridConst &g, f3 p)
+{
+    const int ix = cell_index(fmaf(p.x, g.inv_res, g.bx), g.mx, g.nx);
+    const int iy = cell_index(fmaf(p.y, g.inv_res, g.by), g.my, g.ny);
+    const int iz = cell_index(fmaf(p.z, g.inv_res, g.bz), g.mz, g.nz);
+    return (iz * g.ny + iy) * g.nx + ix;
 }
 
 // The 8 corner samples of a cell, in the order (x, y, z) = 000, 100, 010,
@@ -307,10 +329,14 @@ __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 
         }
         w = scale(sgn * th, ax);
     }
-    // v = V(th)^{-1} t_delta
+    // v = V(th)^{-1} t_delta, c(th) = (1 - (th/2) cot(th/2)) / th^2 with
+    // (th/2) cot(th/2) = th (1 + cos th) / (2 sin th) = th (1 + cth) / nv
+    // away from 0 and pi (nv = |vee| = 2 sin th)
     float cc;
     if (th < 1e-2f) {
         cc = (1.0f / 12.0f) + th * th * (1.0f / 720.0f);
+    } else if (th < CUDART_PI_F - 0.05f) {
+        cc = (1.0f - th * (1.0f + cth) / nv) / (th * th);
     } else {
         const float h = 0.5f * th;
         float sh, ch;

@@ -80,32 +80,34 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 }
 
 // sum over spheres s in [b, e) of frame F of max(0, d_act - (phi(p_s) - r_s))^2
-// (Eqs. 17, 19).  The cell-corner minima of four spheres are loaded together;
-// a sphere whose minimum is above its skip threshold contributes exactly 0
-// and needs no gathers, the others are interpolated from their 8 corners.
+// (Eqs. 17, 19).  The widened cell-corner minima of four spheres are fetched
+// together through the texture unit; a sphere whose minimum is above its
+// skip threshold contributes exactly 0 and needs no gathers, the others are
+// located exactly and interpolated from their 8 corners.
 template <typename GT>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
                                           const Frame &F, int b, int e, unsigned &ngath)
 {
     float env = 0.f;
     for (int s0 = b; s0 < e; s0 += kSphereBatch) {
-        Cell c[kSphereBatch];
         float mn[kSphereBatch];
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
-            c[i] = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
+            const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+            mn[i] = tex3D<float>(g.cmin_tex, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by),
+                                 fmaf(p.z, g.inv_res, g.bz));
         }
-#pragma unroll
-        for (int i = 0; i < kSphereBatch; ++i) mn[i] = __ldg(g.cmin + c[i].base);
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = s0 + i;
             if (s < e && !(mn[i] > rc.sph_skip[s])) {
+                // the few spheres near an obstacle: locate again with fractions
                 ++ngath;
+                const Cell c = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
                 float v[8];
-                corners<GT>(g, c[i].base, v);
-                const float phi = interpolate(v, c[i].fx, c[i].fy, c[i].fz);
+                corners<GT>(g, c.base, v);
+                const float phi = interpolate(v, c.fx, c.fy, c.fz);
                 const float dl = fmaxf(rc.d_act - (phi - rc.sph_r[s]), 0.f);
                 env = fmaf(dl, dl, env);
             }
@@ -123,11 +125,31 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
                                             const float *qd, bool terminal, float *tr,
                                             unsigned &ngath)
 {
+    float lq = 0.f, lqd = 0.f, ns = 0.f;
+    if (!terminal) {
+#pragma unroll
+        for (int j = 0; j < kNJ; ++j) {
+            const float a = limit_violation(q[j], rc.q_lo[j], rc.q_hi[j]);
+            const float b = limit_violation(qd[j], rc.qd_lo[j], rc.qd_hi[j]);
+            const float e = q[j] - rc.q_ref[j];
+            lq = fmaf(a, a, lq);
+            lqd = fmaf(b, b, lqd);
+            ns = fmaf(e, e, ns);
+        }
+    }
     Frame F = base_frame();
     float env = 0.f;
+    // Not unrolled: the kernel's code then fits the instruction cache, which
+    // outweighs the indexed constant loads this costs.  The joint angles
+    // rotate through qr so that the loop indexes no register array.
+    float qr[kNJ];
 #pragma unroll
+    for (int j = 0; j < kNJ; ++j) qr[j] = q[j];
+#pragma unroll 1
     for (int j = 0; j < kNJ; ++j) {
-        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
+        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], qr[0] + rc.th0[j]);
+#pragma unroll
+        for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
         if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath);
     }
     const f3 tee = axpy(rc.flange_d, F.c3, F.t);
@@ -139,16 +161,6 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         return c;
     }
     const float pose = quad_cost(xi, rc.Q);
-    float lq = 0.f, lqd = 0.f, ns = 0.f;
-#pragma unroll
-    for (int j = 0; j < kNJ; ++j) {
-        const float a = limit_violation(q[j], rc.q_lo[j], rc.q_hi[j]);
-        const float b = limit_violation(qd[j], rc.qd_lo[j], rc.qd_hi[j]);
-        const float e = q[j] - rc.q_ref[j];
-        lq = fmaf(a, a, lq);
-        lqd = fmaf(b, b, lqd);
-        ns = fmaf(e, e, ns);
-    }
     env *= rc.w_env;
     lq *= rc.w_q;
     lqd *= rc.w_qd;
@@ -222,7 +234,11 @@ __device__ __forceinline__ float weight_factor(float m_from, float m_to, float i
 // warps of a pair run the same sequence of roll-outs, so they always meet.
 __device__ __forceinline__ void pair_barrier(int pr)
 {
-    asm volatile("bar.sync %0, 64;" ::"r"(pr + 1) : "memory");
+    // immediate barrier ids: with a register id the compiler must reserve
+    // every hardware barrier for the block, which caps blocks per SM
+    static_assert(kWarps / 2 <= 2, "pair barriers 1 and 2 cover at most two pairs");
+    if (pr == 0) asm volatile("bar.sync 1, 64;" ::: "memory");
+    else asm volatile("bar.sync 2, 64;" ::: "memory");
 }
 
 // The inputs of one instance's iteration as a block sees them (filled from
