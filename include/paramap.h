@@ -21,6 +21,12 @@
  *    stream before returning; if all inputs and outputs are device memory
  *    the call only enqueues work on the stream (outputs are valid once the
  *    stream reaches that point).
+ *  - Streams: device inputs must be ready when the stream reaches the call.
+ *    A NULL cuda_stream selects the context's (or batch's) own stream,
+ *    which is a blocking stream: it waits for earlier work on the legacy
+ *    default stream and that stream waits for it, so callers that produce
+ *    inputs on the default stream need no synchronisation.  Inputs made on
+ *    any other stream need that stream passed (or synchronised).
  *  - The caller owns every buffer it passes.  The library copies the robot
  *    description, cost parameters and distance field into memory it owns.
  *  - A context may be used from one host thread at a time (calls on one

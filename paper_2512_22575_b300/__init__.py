@@ -11,6 +11,7 @@ message.  Importing this package loads the library and raises if it is
 missing: there is no fallback implementation.
 """
 import ctypes as C
+import sys
 import os
 
 import numpy as np
@@ -241,7 +242,13 @@ def destroy(ctx):
 
 
 def _stream(stream):
+    """cudaStream_t of `stream`: a torch.cuda.Stream, a raw handle, or None
+    for PyTorch's current stream when torch has initialised CUDA (so a call
+    is ordered after the torch work that produced its inputs), else NULL."""
     if stream is None:
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
         return None
     if hasattr(stream, "cuda_stream"):
         return C.c_void_p(stream.cuda_stream)

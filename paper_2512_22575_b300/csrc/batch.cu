@@ -201,7 +201,8 @@ struct pm_batch {
     size_t gen = 1;             // bumped whenever a workspace buffer moves
     cudaEvent_t done = nullptr; // the last call's staging reads are complete
     bool pending = false;
-    cudaStream_t own = nullptr;
+    cudaStream_t own = nullptr;         // blocking: ordered with the legacy default stream
+    cudaStream_t cap = nullptr;         // non-blocking, for graph capture only
     std::map<std::string, Plan> plans;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -504,7 +505,8 @@ pm_status pm_batch_create(int device, pm_batch **out)
     };
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->own, cudaStreamDefault) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return fail(PM_ECUDA);
@@ -570,7 +572,7 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
         if (!g.exec || g.gen != b->gen || g.n_inst != n) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
-            cudaStream_t cap = b->own;
+            cudaStream_t cap = b->cap;
             cudaGraph_t graph;
             PM_BCUDA(b, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
             pm_status cst = enqueue_batch(b, n, nw, nr, n_iters, flags, false, cap);
@@ -634,6 +636,7 @@ void pm_batch_destroy(pm_batch *b)
     cudaFree(b->d_tune);
     if (b->done) cudaEventDestroy(b->done);
     if (b->own) cudaStreamDestroy(b->own);
+    if (b->cap) cudaStreamDestroy(b->cap);
     if (prev >= 0) cudaSetDevice(prev);
     delete b;
 }

@@ -617,7 +617,7 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         return false;
     };
     if (!ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device), "SM count") ||
-        !ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream") ||
+        !ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault), "stream") ||
         !ck(cudaMalloc(&c->d_grid, elems * dtype_size(gd->dtype)), "grid alloc") ||
         !ck(cudaMalloc(&c->d_rc, sizeof(RobotConst)), "robot constants alloc") ||
         !ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy") ||

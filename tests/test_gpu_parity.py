@@ -223,6 +223,36 @@ def test_repeat_calls_are_deterministic(cfg1):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
 
 
+@pytest.mark.parametrize("stream_arg", ["null", "torch_current"])
+def test_device_inputs_made_just_before_the_call_are_seen(cfg1, stream_arg):
+    """Inputs written by torch on the default stream right before the call
+    (behind a long matmul, so the writes are still pending when the call is
+    enqueued) are read by the iteration: the context's own stream (NULL) is
+    a blocking stream, and the binding's default is torch's current stream."""
+    sc = cfg1[8]
+    p = sc.planner()
+    K, H = 1024, 32
+    U0 = (np.random.default_rng(5).normal(size=(H, 7)) * 0.2).astype(np.float32)
+    ref = U0.copy()
+    p.smpc_iterate(sc.q0, sc.qd0, sc.T, ref, K, 0.02, 0.05, SIGMA, 9, 4)
+    q0 = torch.from_numpy(sc.q0).to(DEV)
+    qd0 = torch.from_numpy(sc.qd0).to(DEV)
+    Td = torch.from_numpy(sc.T.ravel().copy()).to(DEV)
+    U0d = torch.from_numpy(U0).to(DEV)
+    big = torch.randn(4096, 4096, device=DEV)
+    torch.cuda.synchronize()
+    for rep in range(5):
+        U = torch.full((H, 7), 7.0, device=DEV)    # stale values if read too early
+        torch.cuda.synchronize()
+        for _ in range(4):
+            big = big @ big * 1e-3                  # keeps the default stream busy
+        U.copy_(U0d)
+        p.smpc_iterate(q0, qd0, Td, U, K, 0.02, 0.05, SIGMA, 9, 4,
+                       stream=0 if stream_arg == "null" else None)
+        assert np.array_equal(U.cpu().numpy(), ref), rep
+    p.close()
+
+
 def test_invalid_arguments_leave_U_untouched(cfg1):
     sc = cfg1[8]
     p = sc.planner()
