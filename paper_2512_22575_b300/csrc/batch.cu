@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     __shared__ float s_blk[kBatchMaxSteps * kNJ];
     __shared__ float s_wm[kWarps], s_wz[kWarps];
     __shared__ int s_item;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x;
 
     for (;;) {
         __syncthreads();   // the previous item is done with shared memory
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
         const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
         TileJob job = s_inst.job;
         job.iter += ba.it;
-        if (w.y == job.nb - 1 && warp == kWarps - 1) initial_state_cost_warp<GT>(s_rc, s_inst.g, st, s_inst.c0);
+        job.c0 = s_inst.c0;
         const int C = s_inst.C;
         BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz};
         unsigned ngath = 0;

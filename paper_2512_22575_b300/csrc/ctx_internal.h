@@ -17,9 +17,8 @@ struct pm_ctx {
     size_t grid_elems = 0;
     void *d_grid = nullptr;
     float *d_cmin = nullptr;            // per-cell corner minimum of the stored field
-    // The same minimum, widened to the 3x3x3 neighbouring cells, in a 3-D
-    // array of (nx-1) x (ny-1) x (nz-1) cells read through a point-sampled
-    // texture (see GridConst::cmin_tex).
+    // The same minima in a 3-D array of (nx-1) x (ny-1) x (nz-1) cells read
+    // through a point-sampled texture (see GridConst::cmin_tex).
     cudaArray_t cmin_arr = nullptr;
     cudaTextureObject_t cmin_tex = 0;
     bool has_grid = false;

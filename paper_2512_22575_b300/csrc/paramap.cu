@@ -155,30 +155,6 @@ __global__ void cell_min_kernel(const T *phi, float *cmin, int nx, int ny, int n
     }
 }
 
-// Widen the cell minima to the 3x3x3 neighbourhood of cells (clamped at the
-// faces): out[(l (ny-1) + j) (nx-1) + i] over the (nx-1)(ny-1)(nz-1) cells.
-__global__ void cell_min_widen_kernel(const float *cmin, float *out, int nx, int ny, int nz)
-{
-    const int cx = nx - 1, cy = ny - 1, cz = nz - 1;
-    const size_t n = static_cast<size_t>(cx) * cy * cz;
-    for (size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; id < n;
-         id += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(id % cx);
-        const int j = static_cast<int>((id / cx) % cy);
-        const int l = static_cast<int>(id / (static_cast<size_t>(cx) * cy));
-        float m = CUDART_INF_F;
-        for (int dl = -1; dl <= 1; ++dl)
-            for (int dj = -1; dj <= 1; ++dj)
-                for (int di = -1; di <= 1; ++di) {
-                    const int ii = min(max(i + di, 0), cx - 1);
-                    const int jj = min(max(j + dj, 0), cy - 1);
-                    const int ll = min(max(l + dl, 0), cz - 1);
-                    m = fminf(m, cmin[(static_cast<size_t>(ll) * ny + jj) * nx + ii]);
-                }
-        out[id] = m;
-    }
-}
-
 __global__ void philox_words_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                     size_t n)
 {
@@ -632,7 +608,7 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         !ck(cudaMemset(c->d_c0, 0, 32 * sizeof(float)), "c0 zero"))
         return fail(c->err.find("alloc") != std::string::npos ? PM_ENOMEM : PM_ECUDA);
     {
-        // widened cell minima: 3-D array + point-sampled, clamped texture
+        // cell minima: 3-D array + point-sampled, clamped texture
         const cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
         if (!ck(cudaMalloc3DArray(&c->cmin_arr, &fd, make_cudaExtent(gd->nx - 1, gd->ny - 1, gd->nz - 1)),
                 "cell-minimum array alloc"))
@@ -691,24 +667,14 @@ pm_status pm_set_distance_field(pm_ctx *c, const float *grid, int grid_is_device
         cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const __nv_bfloat16 *>(c->d_grid),
                                                       c->d_cmin, c->gd.nx, c->gd.ny, c->gd.nz);
     PM_CUDA(c, cudaGetLastError());
-    // widened minima into the texture's array
-    const int cx = c->gd.nx - 1, cy = c->gd.ny - 1, cz = c->gd.nz - 1;
-    const size_t ncell = static_cast<size_t>(cx) * cy * cz;
-    float *wide = nullptr;
-    PM_CUDA(c, cudaMalloc(&wide, ncell * sizeof(float)));
-    cell_min_widen_kernel<<<static_cast<unsigned>(std::min<size_t>((ncell + 255) / 256, 8u * c->n_sm)), 256, 0,
-                            c->stream>>>(c->d_cmin, wide, c->gd.nx, c->gd.ny, c->gd.nz);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) {
-        cudaMemcpy3DParms cp{};
-        cp.srcPtr = make_cudaPitchedPtr(wide, cx * sizeof(float), cx, cy);
-        cp.dstArray = c->cmin_arr;
-        cp.extent = make_cudaExtent(cx, cy, cz);
-        cp.kind = cudaMemcpyDeviceToDevice;
-        e = cudaMemcpy3DAsync(&cp, c->stream);
-    }
+    // cell minima into the texture's array
+    cudaMemcpy3DParms cp{};
+    cp.srcPtr = make_cudaPitchedPtr(c->d_cmin, c->gd.nx * sizeof(float), c->gd.nx - 1, c->gd.ny);
+    cp.dstArray = c->cmin_arr;
+    cp.extent = make_cudaExtent(c->gd.nx - 1, c->gd.ny - 1, c->gd.nz - 1);
+    cp.kind = cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpy3DAsync(&cp, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(wide);
     PM_CUDA(c, e);
     c->has_grid = true;
     return PM_OK;

@@ -50,12 +50,10 @@ struct GridConst {
     const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16
     const float *cmin;            // [nz][ny][nx]: min of the 8 corners of the cell
                                   // with base voxel (i, j, l), as the lookup reads them
-    // cmin widened to the 3x3x3 neighbourhood of cells, as a point-sampled
-    // texture over the (nx-1) x (ny-1) x (nz-1) cells (clamped addressing,
-    // unnormalised coordinates): fetched at a grid coordinate g it returns
-    // the cell floor(g) clamped into range -- the cell the lookup uses, or,
-    // where the texture unit's fixed-point coordinates round across a cell
-    // face, its neighbour, whose widened minimum also covers the cell.
+    // cmin of the (nx-1) x (ny-1) x (nz-1) cells as a point-sampled texture
+    // (clamped addressing, unnormalised coordinates), fetched at the centre
+    // of the cell (see cell_centre), so the texture unit's fixed-point
+    // coordinates cannot round into a neighbouring cell.
     cudaTextureObject_t cmin_tex;
     int nx, ny, nz;
     float inv_res;
@@ -224,6 +222,15 @@ __device__ __forceinline__ Cell locate(const GridConst &g, f3 p)
     const int iz = cell(fmaf(p.z, g.inv_res, g.bz), g.mz, g.nz, c.fz);
     c.base = (iz * g.ny + iy) * g.nx + ix;
     return c;
+}
+
+// floor(g) + 1/2 for g in [0, 2^23): adding 2^23 rounded down leaves
+// 2^23 + floor(g), and the subtraction is exact.  Below 0 the result is at
+// most 1/2 and above 2^23 it is huge, so the texture's clamp to the first or
+// last cell matches the clamp of cell().
+__device__ __forceinline__ float cell_centre(float g)
+{
+    return __fadd_rd(g, 8388608.0f) - 8388607.5f;
 }
 
 // Index of a coordinate's cell only (no fraction): same clamp and floor as cell().

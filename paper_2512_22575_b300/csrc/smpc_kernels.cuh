@@ -12,8 +12,8 @@
 // (Eqs. 22, 23) and the state terms of q_{k+1}, qd_{k+1} (Eqs. 16, 19-20, 22,
 // 24) or, for k+1 = H, the terminal cost (Eq. 25).  The state terms of
 // k = 0 depend only on (q_0, qd_0) and are the same for every roll-out: one
-// warp of the last block computes them once and the merge adds them to S;
-// they cancel in the weights of Eq. 29.
+// lane evaluates them once, in an extra pass through the step code, and the
+// merge adds them to S; they cancel in the weights of Eq. 29.
 //
 // The sampled perturbations of a lane's steps are kept in shared memory
 // ([warp][step][joint][lane], conflict-free) from sampling to the weighted
@@ -80,7 +80,7 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 }
 
 // sum over spheres s in [b, e) of frame F of max(0, d_act - (phi(p_s) - r_s))^2
-// (Eqs. 17, 19).  The widened cell-corner minima of four spheres are fetched
+// (Eqs. 17, 19).  The cell-corner minima of four spheres are fetched
 // together through the texture unit; a sphere whose minimum is above its
 // skip threshold contributes exactly 0 and needs no gathers, the others are
 // located exactly and interpolated from their 8 corners.
@@ -95,8 +95,8 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
             const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-            mn[i] = tex3D<float>(g.cmin_tex, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by),
-                                 fmaf(p.z, g.inv_res, g.bz));
+            mn[i] = tex3D<float>(g.cmin_tex, cell_centre(fmaf(p.x, g.inv_res, g.bx)),
+                                 cell_centre(fmaf(p.y, g.inv_res, g.by)), cell_centre(fmaf(p.z, g.inv_res, g.bz)));
         }
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
@@ -169,46 +169,6 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     return pose + env + lq + lqd + ns;
 }
 
-// k = 0 state terms, computed by one warp: lane p takes spheres p, p+32;
-// lane 0 adds the pose, joint-limit and null-space terms.
-template <typename GT>
-__device__ __noinline__ static void initial_state_cost_warp(const RobotConst &rc, const GridConst &g,
-                                        const InstanceState &st, float *out)
-{
-    const int lane = threadIdx.x & 31;
-    Frame F = base_frame();
-    float env = 0.f;
-#pragma unroll
-    for (int j = 0; j < kNJ; ++j) {
-        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], st.q0[j] + rc.th0[j]);
-        for (int s = rc.link_begin[j + 1]; s < rc.link_begin[j + 2]; ++s) {
-            if ((s & 31) != lane) continue;
-            const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-            const float dl = fmaxf(rc.d_act - (phi_trilinear<GT>(g, p) - rc.sph_r[s]), 0.f);
-            env = fmaf(dl, dl, env);
-        }
-    }
-    float v = rc.w_env * env;
-    if (lane == 0) {
-        const f3 tee = axpy(rc.flange_d, F.c3, F.t);
-        float xi[6];
-        pose_error(st.Rg, st.tg, F.c1, F.c2, F.c3, tee, xi);
-        float lq = 0.f, lqd = 0.f, ns = 0.f;
-        for (int j = 0; j < kNJ; ++j) {
-            const float a = limit_violation(st.q0[j], rc.q_lo[j], rc.q_hi[j]);
-            const float b = limit_violation(st.qd0[j], rc.qd_lo[j], rc.qd_hi[j]);
-            const float e = st.q0[j] - rc.q_ref[j];
-            lq = fmaf(a, a, lq);
-            lqd = fmaf(b, b, lqd);
-            ns = fmaf(e, e, ns);
-        }
-        v += quad_cost(xi, rc.Q) + rc.w_q * lq + rc.w_qd * lqd + rc.w_ns * ns;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) *out = v;
-}
-
 // ---------------------------------------------------------- warp scans
 // Exclusive prefix sum over the L lanes of each segment, for 7 values.
 __device__ __forceinline__ void seg_exclusive_scan(const float *x, float *ex, int sl, int L)
@@ -247,6 +207,7 @@ struct TileJob {
     const float *Ubar;          // [H][7]
     float *costs;               // [K] or null
     float *part;                // this instance's block partials: m [nb], z [nb], acc [H*7][nb]
+    float *c0;                  // [0] <- state terms of k = 0 (null: not computed)
     int K, H, nb;
     uint32_t seed_lo, seed_hi, iter;
     float dt, inv_lambda;
@@ -348,34 +309,56 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             }
         }
 
-        // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25)
+        // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25).
+        // The state terms of k = 0 are the same for every roll-out: the lane
+        // holding step 0 of the last tile evaluates them once, in an extra
+        // pass through the same code (so they add no code to the kernel),
+        // into job.c0; the merge adds them to S.
+        const bool c0_lane = !TRACE && job.c0 && tile == n_tiles - 1 && seg == 0 && sl == 0 && half == 0;
         float lsum = 0.f, lcomp = 0.f;
         float runU[kNJ], runB[kNJ];
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) { runU[j] = 0.f; runB[j] = B0[j]; }
 #pragma unroll 1
-        for (int s = 0; s < C; ++s) {
+        for (int s = 0; s <= C; ++s) {
+            const bool extra = (s == C);
             const int k = kbase + sl * C + s;
-            if (!(active && k < H)) break;
+            if (extra) {
+                if (!c0_lane) break;
+            } else if (!(active && k < H)) {
+                if (!c0_lane) break;
+                s = C - 1;          // no more steps: on to the extra pass
+                continue;
+            }
             float u[kNJ], q[kNJ], qd[kNJ];
-            const float kp_dt = static_cast<float>(k + 1) * dt;
+            if (!extra) {
+                const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
-            for (int j = 0; j < kNJ; ++j) {
-                u[j] = __ldg(job.Ubar + k * kNJ + j) + sm.eps[E(warp, s, j) + lane];
-                runU[j] += u[j];
-                const float A = A0[j] + runU[j];           // A_{k+1}
-                runB[j] += A;                               // B_{k+1}
-                qd[j] = fmaf(dt, A, st.qd0[j]);
-                q[j] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
+                for (int j = 0; j < kNJ; ++j) {
+                    u[j] = __ldg(job.Ubar + k * kNJ + j) + sm.eps[E(warp, s, j) + lane];
+                    runU[j] += u[j];
+                    const float A = A0[j] + runU[j];           // A_{k+1}
+                    runB[j] += A;                               // B_{k+1}
+                    qd[j] = fmaf(dt, A, st.qd0[j]);
+                    q[j] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) { u[j] = 0.f; q[j] = st.q0[j]; qd[j] = st.qd0[j]; }
             }
             float *tr_u = nullptr, *tr_x = nullptr;
             if (TRACE) {
                 tr_u = trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
                 tr_x = tr_u + kTraceCols;
             }
-            float step = control_cost<TRACE>(rc, u, tr_u);
-            step += state_cost<GT, TRACE>(rc, g, st, q, qd, k + 1 == H, tr_x, ngath);
-            kahan_add(lsum, lcomp, step);
+            const unsigned ng0 = ngath;
+            const float sc = state_cost<GT, TRACE>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath);
+            if (extra) {
+                ngath = ng0;        // lookups of the roll-outs only
+                *job.c0 = sc;
+            } else {
+                kahan_add(lsum, lcomp, control_cost<TRACE>(rc, u, tr_u) + sc);
+            }
         }
 
         // S'^(m): compensated sum over the segment's lanes
@@ -492,17 +475,11 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     load_state(a.in, s_state);
     __syncthreads();
     const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
-    const int warp = threadIdx.x >> 5;
-
-    // the last block holds the fewest roll-outs: its last warp computes the
-    // k = 0 terms before starting on its tiles
-    if (!TRACE && blockIdx.x == gridDim.x - 1 && warp == kWarps - 1)
-        initial_state_cost_warp<GT>(rc, g, st, a.c0);
-
     TileJob job;
     job.Ubar = a.Ubar;
     job.costs = a.costs;
     job.part = a.part;
+    job.c0 = TRACE ? nullptr : a.c0;
     job.K = a.K;
     job.H = a.H;
     job.nb = gridDim.x;
