@@ -276,6 +276,69 @@ def bench_batched(pm, torch, dev, stream, reps=20):
 SERVE_RATES = (500, 1000, 2000, 3000, 4000, 6000)
 
 
+def kernel_traffic_bytes():
+    """DRAM bytes (read + write) per launch of the iteration kernel from the
+    committed ncu counters, or None when the kernel sources changed since
+    they were captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "smpc_iteration_kernel_cfg2_counters.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def bench_latency_cfg1(pm, torch, dev, stream, reps=200):
+    """Single SMPC iteration of the plain workload (K=256, H=32, 64^3 field
+    at 2 cm): device time of the iteration (CUDA events around each call on
+    the launching stream, the GPU kept busy so the host does not starve it),
+    and the host-observed latency of a call with host buffers."""
+    import workloads
+    sc = workloads.load_scene("cfg1_seed0")
+    p = pm.Planner(workloads.panda_robot(), sc["grid"], workloads.default_cost_params(sc["q0"]),
+                   device=dev.index or 0)
+    p.set_distance_field(workloads.build_scene_grid(sc))
+    K, H = int(sc["K"]), int(sc["H"])
+    sigma = np.full(7, 0.5, np.float32)
+    q0 = torch.from_numpy(sc["q0"].astype(np.float32)).to(dev)
+    qd0 = torch.from_numpy(sc["qd0"].astype(np.float32)).to(dev)
+    T = torch.from_numpy(sc["T_goal"].astype(np.float32).ravel().copy()).to(dev)
+    U = torch.zeros((H, 7), dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        for i in range(5):
+            p.smpc_iterate(q0, qd0, T, U, K, 0.02, 0.05, sigma, 1, i, stream=stream)
+        torch.cuda.synchronize()
+        torch.cuda._sleep(50_000_000)            # queue the calls behind a busy GPU
+        for i in range(reps):
+            ev[i][0].record(stream)
+            p.smpc_iterate(q0, qd0, T, U, K, 0.02, 0.05, sigma, 1, i, stream=stream)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    dev_us = np.array([a.elapsed_time(b) * 1e3 for a, b in ev])
+    qh, qdh = sc["q0"].astype(np.float32), sc["qd0"].astype(np.float32)
+    Th = sc["T_goal"].astype(np.float32).ravel().copy()
+    Uh = np.zeros((H, 7), np.float32)
+    host_us = []
+    for i in range(reps):
+        t0 = time.perf_counter()
+        p.smpc_iterate(qh, qdh, Th, Uh, K, 0.02, 0.05, sigma, 1, i)
+        host_us.append((time.perf_counter() - t0) * 1e6)
+    p.close()
+    return {"workload": "one SMPC iteration, K=256, H=32, 64^3 field at 2 cm (plain single iteration)",
+            "device_us_p50": float(np.percentile(dev_us, 50)), "device_us_p99": float(np.percentile(dev_us, 99)),
+            "host_call_us_p50": float(np.percentile(host_us, 50)),
+            "host_call_us_p99": float(np.percentile(host_us, 99)),
+            "host_call": "pm_smpc_iterate with host buffers (copies in and out, synchronous)",
+            "rollout_steps_per_s_device": K * H / (np.percentile(dev_us, 50) * 1e-6)}
+
+
 def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, deadline_ms=10.0,
                   seed=7, spin_us=5000):
     """Serving workload: Poisson replan requests from 256 arms (own field of
@@ -530,8 +593,11 @@ def run_ours(args, rank, world, local):
     achieved = flops_launch / avg_kernel_s / 1e12
     props = torch.cuda.get_device_properties(dev)
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    fma_peak = pm.fp32_fma_peak(local)
+    traffic = kernel_traffic_bytes()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_measured_fma": fma_peak, "frac_of_measured_fma": achieved / fma_peak,
                 "kernel": "smpc_iteration_kernel<C=1,L=32,P=2,float>",
                 "gathered_fraction": gathers_per_launch / (K * (H - 1) * 28),
                 "kernel_ms_per_launch": avg_kernel_s * 1e3, "launches_timed": launches,
@@ -587,6 +653,7 @@ def run_ours(args, rank, world, local):
                              "ms_per_step": vms / n_v, "kernel_ms_per_launch": kms / max(kn, 1),
                              "replans": n_v}
     line["precision_variants"] = variants
+    line["latency_cfg1"] = bench_latency_cfg1(pm, torch, dev, stream)
     if not args.no_batched:
         line["batched"] = bench_batched(pm, torch, dev, stream)
     if not args.no_serving:

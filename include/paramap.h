@@ -370,6 +370,15 @@ void pm_server_destroy(pm_server *server);
  */
 pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, size_t n,
                            void *cuda_stream);
+/*
+ * pm_fp32_fma_peak: measured FP32 rate of `device` (a yardstick for the
+ * iteration kernel, which is bound by FP32 and integer arithmetic; the paper
+ * has no counterpart).  Every thread of 8 resident blocks per SM runs 8
+ * independent chains of dependent FMAs; *tflops = 2 x FMAs / best of 5
+ * event-timed launches, in 1e12 FLOP/s.  Synchronous.  Errors: PM_EINVAL
+ * (NULL output), PM_ECUDA.
+ */
+pm_status pm_fp32_fma_peak(int device, double *tflops);
 pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed,
                           uint32_t iter_index, float *eps, void *cuda_stream);
 pm_status pm_rollout_trace(pm_ctx *ctx, const float *q0, const float *qd0,

@@ -189,6 +189,13 @@ def rollout_trace(ctx, q0, qd0, T_goal, U, K, dt, sigma, seed, iter_index, trace
                                   _ptr(trace, n=int(K) * (H + 1) * 8, writable=True)), ctx)
 
 
+def fp32_fma_peak(device=0):
+    """pm_fp32_fma_peak: measured FP32 FMA rate of the device in TFLOP/s."""
+    t = C.c_double()
+    _check(lib().pm_fp32_fma_peak(int(device), C.byref(t)))
+    return t.value
+
+
 def philox4x32_10(ctr, key, out, stream=None):
     """pm_philox4x32_10 on CUDA uint32 tensors ctr, out of shape [n][4]."""
     n = ctr.numel() // 4

@@ -155,6 +155,22 @@ __global__ void cell_min_kernel(const T *phi, float *cmin, int nx, int ny, int n
     }
 }
 
+// FP32 yardstick: 8 independent chains of dependent FMAs per thread.
+__global__ void __launch_bounds__(256) fma_peak_kernel(float *sink, int iters, float a, float b)
+{
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = static_cast<float>(threadIdx.x + i);
+#pragma unroll 4
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == 1.2345e-30f) sink[0] = s;   // never true; keeps the chains live
+}
+
 __global__ void philox_words_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                     size_t n)
 {
@@ -797,6 +813,48 @@ pm_status pm_rollout_trace(pm_ctx *c, const float *q0, const float *qd0, const f
     st = launch_iteration(c, s, in, Ud, nullptr, nullptr, K, H, dt, 1.0f, seed, iter_index, true, trace);
     if (st != PM_OK) return st;
     PM_CUDA(c, cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+pm_status pm_fp32_fma_peak(int device, double *tflops)
+{
+    if (!tflops) return PM_EINVAL;
+    DeviceGuard dg(device);
+    if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return PM_ECUDA; }
+    int n_sm = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ECUDA;
+    }
+    float *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    const int blocks = 8 * n_sm, threads = 256, iters = 8192;
+    double best_ms = 1e30;
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        fma_peak_kernel<<<blocks, threads, 0, s>>>(sink, iters, 0.999999f, 1e-7f);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best_ms = std::min(best_ms, static_cast<double>(ms));   // first launch warms up
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ECUDA;
+    }
+    const double flops = 2.0 * 8.0 * iters * static_cast<double>(blocks) * threads;
+    *tflops = flops / (best_ms * 1e-3) / 1e12;
     return PM_OK;
 }
 

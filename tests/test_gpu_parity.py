@@ -253,6 +253,14 @@ def test_device_inputs_made_just_before_the_call_are_seen(cfg1, stream_arg):
     p.close()
 
 
+def test_fp32_fma_peak_is_plausible():
+    props = torch.cuda.get_device_properties(0)
+    t = pm.fp32_fma_peak(0)
+    # at most the SMs' 128 FP32 lanes at 2.1 GHz; far below would mean a broken timer
+    assert 0.2 * props.multi_processor_count * 128 * 2 * 2.1e9 / 1e12 < t
+    assert t < props.multi_processor_count * 128 * 2 * 2.1e9 / 1e12
+
+
 def test_invalid_arguments_leave_U_untouched(cfg1):
     sc = cfg1[8]
     p = sc.planner()
