@@ -516,8 +516,6 @@ def run_ours(args, rank, world, local):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    planner.profile_enable(pm.PM_PROFILE_TIME)
-    planner.profile_read(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -535,10 +533,13 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    kernel_ms, launches = planner.profile_read(reset=True)
-    # gathers per launch, counted on an untimed re-run of the first replans
-    n_count = min(args.steps, 25)
-    planner.profile_enable(pm.PM_PROFILE_GATHERS)
+    # iteration-kernel time (CUDA events around each launch, on its stream)
+    # and gathers per launch, over a second timed pass of the same replans:
+    # events between the kernels would break the programmatic launch overlap
+    # that the first pass measures
+    n_count = min(args.steps, 200)
+    planner.profile_enable(pm.PM_PROFILE_TIME | pm.PM_PROFILE_GATHERS)
+    planner.profile_read(reset=True)
     planner.profile_gathers(reset=True)
     with torch.cuda.stream(stream):
         for i in range(n_count):
@@ -547,6 +548,7 @@ def run_ours(args, rank, world, local):
             planner.replan(q, qd, Ts[r], U, K, iters, dt, lam, sigma, seed, r % EPISODE,
                            u0_out=u0, best_cost=best, stream=stream)
     torch.cuda.synchronize()
+    kernel_ms, launches = planner.profile_read(reset=True)
     gathers_per_launch = planner.profile_gathers(reset=True) / (n_count * iters)
     planner.profile_enable(0)
     step_ms = np.array([s.elapsed_time(e) for s, e in ev])
@@ -601,6 +603,8 @@ def run_ours(args, rank, world, local):
                 "kernel": "smpc_iteration_kernel<C=1,L=32,P=2,float>",
                 "gathered_fraction": gathers_per_launch / (K * (H - 1) * 28),
                 "kernel_ms_per_launch": avg_kernel_s * 1e3, "launches_timed": launches,
+                "kernel_timing": f"CUDA events around each iteration kernel on its stream, second timed "
+                                 f"pass of {n_count} replans",
                 "flops_per_launch": flops_launch,
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
                               f"x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (unit counts and max clock)"}

@@ -116,6 +116,27 @@ long long launch_blocks(long long K, TileShape sh, long long resident)
 
 size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : 2; }
 
+// Launch a kernel that may start while its predecessor in the stream is
+// still running (programmatic dependent launch): the kernel's
+// grid_dependency_prologue() waits for the predecessor's completion and
+// memory before anything else, so only the launch latency overlaps.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ------------------------------------------------------------ small kernels
 __global__ void convert_grid_kernel(const float *src, void *dst, size_t n, int dtype)
 {
@@ -216,6 +237,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
 softmin_merge_kernel(const float *part, int nb, int na, const float *Ubar, float *Uout,
                      float inv_lambda, float *c0, float *costs, int K)
 {
+    grid_dependency_prologue();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float *pm_ = part, *pz = part + nb, *pacc = part + 2 * static_cast<size_t>(nb);
     float lm = CUDART_INF_F;
@@ -223,17 +245,19 @@ softmin_merge_kernel(const float *part, int nb, int na, const float *Ubar, float
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
     const float M = lm;
-    float lz = 0.f;
-    for (int b = lane; b < nb; b += 32) lz = fmaf(weight_factor(__ldg(pm_ + b), M, inv_lambda), __ldg(pz + b), lz);
-    const float Z = warp_sum_lane0(lz);
+    // Z = sum_b f_b z_b and this warp's row sum_b f_b acc_b in one pass,
+    // f_b = exp((M - m_b) / lambda), each sum in lane-strided then fixed tree order
     const int t = blockIdx.x * kMergeWarps + warp;
-    if (t < na) {
-        const float *row = pacc + static_cast<size_t>(t) * nb;
-        float la = 0.f;
-        for (int b = lane; b < nb; b += 32) la = fmaf(weight_factor(__ldg(pm_ + b), M, inv_lambda), __ldg(row + b), la);
-        const float acc = warp_sum_lane0(la);
-        if (lane == 0) Uout[t] = Ubar[t] + acc / Z;
+    const float *row = pacc + static_cast<size_t>(t < na ? t : 0) * nb;
+    float lz = 0.f, la = 0.f;
+    for (int b = lane; b < nb; b += 32) {
+        const float f = weight_factor(__ldg(pm_ + b), M, inv_lambda);
+        lz = fmaf(f, __ldg(pz + b), lz);
+        if (t < na) la = fmaf(f, __ldg(row + b), la);
     }
+    const float Z = warp_sum_lane0(lz);
+    const float acc = warp_sum_lane0(la);
+    if (t < na && lane == 0) Uout[t] = Ubar[t] + acc / Z;
     const float k0 = __ldg(c0);
     if (blockIdx.x == 0 && threadIdx.x == 0) c0[1] = M + k0;
     if (costs)
@@ -247,6 +271,7 @@ __global__ void replan_advance_kernel(const float *q0, const float *qd0, float *
                                       float *q_out, float *qd_out, float *u0_out, const float *c0,
                                       float *best_out)
 {
+    grid_dependency_prologue();
     __shared__ float sU[kMaxHorizon * kNJ];
     const int n = H * kNJ;
     for (int i = threadIdx.x; i < n; i += blockDim.x) sU[i] = U[i];
@@ -392,7 +417,7 @@ pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, si
         }
         PM_CUDA(c, cudaEventRecord(c->prof_ev[c->prof_used], s));
     }
-    fn<<<nb, kBlock, smem, s>>>(c->rc, grid_const(c), a);
+    PM_CUDA(c, launch_dependent(fn, dim3(nb), dim3(kBlock), smem, s, c->rc, grid_const(c), a));
     PM_CUDA(c, cudaGetLastError());
     if (prof) {
         PM_CUDA(c, cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
@@ -401,8 +426,9 @@ pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, si
     }
     if (!trace) {
         const int na = H * kNJ;
-        softmin_merge_kernel<<<(na + kMergeWarps - 1) / kMergeWarps, 32 * kMergeWarps, 0, s>>>(
-            part, nb, na, Ubar, Uout, a.inv_lambda, c0, costs, K);
+        PM_CUDA(c, launch_dependent(softmin_merge_kernel, dim3((na + kMergeWarps - 1) / kMergeWarps),
+                                    dim3(32 * kMergeWarps), 0, s, static_cast<const float *>(part), nb, na,
+                                    Ubar, Uout, a.inv_lambda, c0, costs, K));
         PM_CUDA(c, cudaGetLastError());
     }
     return PM_OK;
@@ -479,7 +505,8 @@ pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &i
                                lambda, seed, iter0 + static_cast<uint32_t>(it), false, nullptr, nullptr);
         if (st != PM_OK) return st;
     }
-    replan_advance_kernel<<<1, 256, 0, s>>>(in.q0, in.qd0, U, H, dt, q_out, qd_out, u0_out, c0, best_out);
+    PM_CUDA(c, launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, U, H, dt, q_out,
+                                qd_out, u0_out, static_cast<const float *>(c0), best_out));
     PM_CUDA(c, cudaGetLastError());
     return PM_OK;
 }
@@ -767,9 +794,11 @@ pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *
         if (st != PM_OK) return st;
     }
     float *small = c->d_c0 + 8;  // [q 8][qd 8][u0 8] device scratch
-    replan_advance_kernel<<<1, 256, 0, s>>>(in.q0, in.qd0, Ud, H, dt, dq ? q : small, dqd ? qd : small + 8,
-                                            u0_out ? (du0 ? u0_out : small + 16) : nullptr, c->d_c0,
-                                            best_cost ? (dbest ? best_cost : c->d_c0 + 2) : nullptr);
+    PM_CUDA(c, launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, Ud, H, dt,
+                                dq ? q : small, dqd ? qd : small + 8,
+                                u0_out ? (du0 ? u0_out : small + 16) : static_cast<float *>(nullptr),
+                                static_cast<const float *>(c->d_c0),
+                                best_cost ? (dbest ? best_cost : c->d_c0 + 2) : static_cast<float *>(nullptr)));
     PM_CUDA(c, cudaGetLastError());
     const bool host_out = !dU || !dq || !dqd || (u0_out && !du0) || (best_cost && !dbest);
     if (host_out) {

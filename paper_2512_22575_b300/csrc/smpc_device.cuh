@@ -93,6 +93,16 @@ __device__ __forceinline__ void load_state(const CallInputs &in, float *s_state)
 }
 constexpr int kStateFloats = sizeof(InstanceState) / sizeof(float);
 
+// Programmatic dependent launch (sm_90 and later): let the next kernel in
+// the stream be scheduled now, then wait until every predecessor this grid
+// depends on has completed and its writes are visible.  Both are no-ops for
+// a kernel launched without the programmatic-serialisation attribute.
+__device__ __forceinline__ void grid_dependency_prologue()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32: per round two 32x32 -> 64 bit products, words permuted and
 // xored with the key; the key is bumped by the Weyl constants each round.

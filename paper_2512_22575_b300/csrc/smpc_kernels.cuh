@@ -472,6 +472,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     __shared__ float s_blk[C * L * P * kNJ];   // block accumulator [k][j], k < C*L*P (>= H, host-checked)
     __shared__ float s_wm[kWarps], s_wz[kWarps];
 
+    grid_dependency_prologue();
     load_state(a.in, s_state);
     __syncthreads();
     const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
