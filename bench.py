@@ -276,6 +276,49 @@ def bench_batched(pm, torch, dev, stream, reps=20):
 SERVE_RATES = (500, 1000, 2000, 3000, 4000, 6000)
 
 
+def bench_self_collision(pm, torch, dev, stream, w, Ts, n_replans=100, min_link_gap=2):
+    """The replanning workload with the self-collision term on (Eqs. 18-20):
+    sphere pairs on frames at least two apart (240 pairs), w_self = 1.
+    Replans timed with events per replan, then the iteration kernel alone."""
+    import workloads
+    sc = w["scene"]
+    rb = dict(w["robot"])
+    rb["self_pairs"] = workloads.self_collision_pairs(rb, min_link_gap=min_link_gap)
+    cp = dict(w["cp"])
+    cp["w_self"] = np.float32(1.0)
+    K, H, iters, dt, lam, sigma = w["K"], w["H"], w["iters"], w["dt"], w["lam"], w["sigma"]
+    p = pm.Planner(rb, sc["grid"], cp, device=dev.index or 0)
+    p.set_distance_field(w["phi"])
+    q0 = torch.from_numpy(sc["q0"].astype(np.float32)).to(dev)
+    qd0 = torch.from_numpy(sc["qd0"].astype(np.float32)).to(dev)
+    q, qd = q0.clone(), qd0.clone()
+    U = torch.zeros((H, 7), dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_replans)]
+    with torch.cuda.stream(stream):
+        for r in range(3):
+            p.replan(q, qd, Ts[r % len(Ts)], U, K, iters, dt, lam, sigma, 100, r, stream=stream)
+        q.copy_(q0); qd.copy_(qd0); U.zero_()
+        torch.cuda.synchronize()
+        for r in range(n_replans):
+            ev[r][0].record(stream)
+            p.replan(q, qd, Ts[r % len(Ts)], U, K, iters, dt, lam, sigma, 100, r % EPISODE, stream=stream)
+            ev[r][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        p.profile_enable(pm.PM_PROFILE_TIME)
+        p.profile_read(reset=True)
+        q.copy_(q0); qd.copy_(qd0); U.zero_()
+        for r in range(min(n_replans, 50)):
+            p.replan(q, qd, Ts[r % len(Ts)], U, K, iters, dt, lam, sigma, 100, r, stream=stream)
+        torch.cuda.synchronize()
+        kms, kn = p.profile_read(reset=True)
+    p.close()
+    return {"workload": f"replanning workload (K={K}, H={H}) with the self-collision term: "
+                        f"{len(rb['self_pairs'])} sphere pairs on frames >= {min_link_gap} apart, w_self = 1",
+            "value": K * H * iters / (ms * 1e-3), "unit": UNIT, "ms_per_replan": ms,
+            "kernel_ms_per_launch": kms / max(kn, 1), "replans": n_replans}
+
+
 def kernel_traffic_bytes():
     """DRAM bytes (read + write) per launch of the iteration kernel from the
     committed ncu counters, or None when the kernel sources changed since
@@ -658,6 +701,7 @@ def run_ours(args, rank, world, local):
                              "replans": n_v}
     line["precision_variants"] = variants
     line["latency_cfg1"] = bench_latency_cfg1(pm, torch, dev, stream)
+    line["self_collision"] = bench_self_collision(pm, torch, dev, stream, w, Ts)
     if not args.no_batched:
         line["batched"] = bench_batched(pm, torch, dev, stream)
     if not args.no_serving:

@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
         job.iter += ba.it;
         job.c0 = s_inst.c0;
         const int C = s_inst.C;
-        BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz};
+        BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
+                     s_rc.n_self_groups > 0 ? s_dyn + 2 * kWarps * kBatchCMax * kNJ * 32 : nullptr};
         unsigned ngath = 0;
         run_block<GT, false>(s_rc, s_inst.g, st, job, nullptr, C, s_inst.L, s_inst.P, w.y, sm, ngath);
     }
@@ -185,7 +186,9 @@ struct GraphEntry {
 struct pm_batch {
     int device = 0;
     int n_sm = 0;
-    int blocks_per_sm = 1;
+    int blocks_per_sm = 1;      // resident batch blocks per SM without the self-collision region
+    int bps_call = 1;           // ... for the current call's shared memory
+    size_t smem_call = 0;       // dynamic shared memory of the current call
     std::mutex mu;
     std::string err;
     // workspace
@@ -275,7 +278,7 @@ Plan make_plan(pm_batch *b, const pm_batch_item *it, int n, double scale, bool w
     Plan p;
     double total = 0.0;
     for (int i = 0; i < n; ++i) total += static_cast<double>(it[i].K) * it[i].H;
-    const double B = scale * b->n_sm * b->blocks_per_sm;
+    const double B = scale * b->n_sm * b->bps_call;
     for (int i = 0; i < n; ++i) {
         TileShape s = default_shape(it[i].H);
         if (wide && it[i].H > 32 && it[i].H <= 64) s = TileShape{2, 32, 1};
@@ -291,10 +294,20 @@ Plan make_plan(pm_batch *b, const pm_batch_item *it, int n, double scale, bool w
     return p;
 }
 
+// Dynamic shared memory of a batch: the tile arrays plus, if any item has
+// the self-collision term on, the largest item's self slots.
+size_t call_smem(const pm_batch_item *it, int n)
+{
+    size_t extra = 0;
+    for (int i = 0; i < n; ++i)
+        if (it[i].ctx) extra = std::max(extra, self_smem_bytes(it[i].ctx->rc));
+    return batch_smem() + extra;
+}
+
 std::string structure_key(const pm_batch_item *it, int n, int n_iters, int flags)
 {
     std::ostringstream os;
-    os << n_iters << ':' << (flags & PM_BATCH_REPLAN) << ':';
+    os << n_iters << ':' << (flags & PM_BATCH_REPLAN) << ':' << call_smem(it, n) << ':';
     for (int i = 0; i < n; ++i) os << it[i].K << ',' << it[i].H << ';';
     return os.str();
 }
@@ -391,10 +404,10 @@ pm_status enqueue_batch(pm_batch *b, int n, int n_work, int n_rows, int n_iters,
     PM_BCUDA(b, cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int2) * n_work, cudaMemcpyHostToDevice, s));
     PM_BCUDA(b, cudaMemcpyAsync(b->d_rows, b->h_rows, sizeof(int2) * n_rows, cudaMemcpyHostToDevice, s));
     PM_BCUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned) * n_iters, s));
-    const int grid = std::max(1, std::min(n_work, b->n_sm * b->blocks_per_sm));
+    const int grid = std::max(1, std::min(n_work, b->n_sm * b->bps_call));
     for (int itn = 0; itn < n_iters; ++itn) {
         BatchArgs a{b->d_inst, b->d_work, n_work, b->d_queue + itn, static_cast<uint32_t>(itn)};
-        smpc_batch_kernel<float><<<grid, kBlock, batch_smem(), s>>>(a);
+        smpc_batch_kernel<float><<<grid, kBlock, b->smem_call, s>>>(a);
         PM_BCUDA(b, cudaGetLastError());
         batch_merge_kernel<<<n_rows, 32 * kBatchMergeWarps, 0, s>>>(b->d_inst, b->d_rows);
         PM_BCUDA(b, cudaGetLastError());
@@ -514,6 +527,8 @@ pm_status pm_batch_create(int device, pm_batch **out)
     b->blocks_per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float>), kBlock,
                                               batch_smem());
     if (b->blocks_per_sm < 1) return fail(PM_ECUDA);
+    b->bps_call = b->blocks_per_sm;
+    b->smem_call = batch_smem();
     if (prev >= 0) cudaSetDevice(prev);
     *out = b;
     return PM_OK;
@@ -535,6 +550,10 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
         PM_BCUDA(b, cudaEventSynchronize(b->done));   // pinned staging is about to be rewritten
         b->pending = false;
     }
+    b->smem_call = call_smem(items, n);
+    b->bps_call = resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float>), kBlock,
+                                         b->smem_call);
+    if (b->bps_call < 1) return berr(b, PM_ECUDA, "cannot give the batch kernel %zu bytes of shared memory", b->smem_call);
     const std::string key = structure_key(items, n, n_iters, flags);
     auto pit = b->plans.find(key);
     if (pit == b->plans.end()) {

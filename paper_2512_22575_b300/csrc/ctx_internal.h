@@ -13,6 +13,8 @@ struct pm_ctx {
     int n_sm = 0;
     pm::RobotConst rc{};
     pm::RobotConst *d_rc = nullptr;     // device copy (read by the batched kernels)
+    unsigned *d_self_pairs = nullptr;   // self-collision pairs, grouped (rc.self_pairs)
+    float *d_self_rsum = nullptr;       // their radius sums (rc.self_rsum)
     pm_grid_desc gd{};
     size_t grid_elems = 0;
     void *d_grid = nullptr;

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -444,7 +445,7 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
     IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace);
     if (!fn) return set_err(c, trace ? PM_EINVAL : PM_EINTERNAL, "no %s kernel for C=%d L=%d P=%d",
                             trace ? "trace" : "iteration", sh.C, sh.L, sh.P);
-    const size_t smem = iteration_smem_bytes(sh.C);
+    const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
     const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
     if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
     const long long resident = static_cast<long long>(c->n_sm) * per_sm;
@@ -463,13 +464,19 @@ cudaStream_t pick_stream(pm_ctx *c, void *s) { return s ? static_cast<cudaStream
 int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
 {
     static std::mutex mu;
-    static std::unordered_map<const void *, int> cache;
+    static std::map<std::pair<const void *, size_t>, int> cache;
+    static std::unordered_map<const void *, size_t> attr_set;   // dynamic shared memory limit set so far
     std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(fn);
+    const auto key = std::make_pair(fn, smem);
+    auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess) {
-        cudaGetLastError();
-        return -1;
+    if (smem > attr_set[fn]) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        attr_set[fn] = smem;
     }
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
@@ -477,7 +484,7 @@ int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
         n = 1;
     }
     n = std::max(n, 1);
-    cache[fn] = n;
+    cache[key] = n;
     return n;
 }
 
@@ -492,7 +499,7 @@ pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &i
     if (st != PM_OK) return st;
     IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
     if (!fn) return set_err(c, PM_EINTERNAL, "no iteration kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
-    const size_t smem = iteration_smem_bytes(sh.C);
+    const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
     const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
     if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
     long long nb = launch_blocks(K, sh, static_cast<long long>(c->n_sm) * per_sm);
@@ -551,9 +558,14 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
             rb->sphere_radius[s] < 0.f)
             return set_err(nullptr, PM_EINVAL, "bad sphere %d", s);
     }
-    if (rb->n_self_pairs < 0) return set_err(nullptr, PM_EINVAL, "n_self_pairs < 0");
-    if (rb->n_self_pairs > 0 && cp->w_self != 0.f)
-        return set_err(nullptr, PM_EINVAL, "the self-collision term (w_self > 0 with pairs) is not built yet");
+    if (rb->n_self_pairs < 0 || rb->n_self_pairs > kMaxSelfPairs)
+        return set_err(nullptr, PM_EINVAL, "n_self_pairs=%d out of [0, %d]", rb->n_self_pairs, kMaxSelfPairs);
+    if (rb->n_self_pairs > 0 && !rb->self_pairs) return set_err(nullptr, PM_EINVAL, "self_pairs is NULL");
+    for (int i = 0; i < rb->n_self_pairs; ++i)
+        for (int k = 0; k < 2; ++k)
+            if (rb->self_pairs[2 * i + k] < 0 || rb->self_pairs[2 * i + k] >= rb->n_spheres)
+                return set_err(nullptr, PM_EINVAL, "self_pairs[%d][%d]=%d is not a sphere", i, k,
+                               rb->self_pairs[2 * i + k]);
     if (gd->nx < 2 || gd->ny < 2 || gd->nz < 2)
         return set_err(nullptr, PM_EINVAL, "grid needs >= 2 voxels per axis");
     const size_t elems = static_cast<size_t>(gd->nx) * gd->ny * gd->nz;
@@ -614,6 +626,54 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         r.q_ref[j] = cp->q_ref[j];
     }
     r.flange_d = rb->flange_d;
+    // self-collision set: pairs in internal sphere order, grouped by their
+    // frames (fa <= fb); each frame's bounding sphere around its spheres
+    std::vector<unsigned> self_pairs;
+    std::vector<float> self_rsum;
+    if (cp->w_self > 0.f && rb->n_self_pairs > 0) {
+        std::vector<int> inv(rb->n_spheres);
+        for (int i = 0; i < rb->n_spheres; ++i) inv[order[i]] = i;
+        double lc[kNJ][3] = {}, lr[kNJ] = {};
+        for (int j = 0; j < n; ++j) {
+            const int b = r.link_begin[j + 1], e = r.link_begin[j + 2];
+            if (e == b) continue;
+            for (int i = b; i < e; ++i)
+                for (int k = 0; k < 3; ++k) lc[j][k] += r.sph_off[i][k] / static_cast<double>(e - b);
+            for (int i = b; i < e; ++i) {
+                double d2 = 0.0;
+                for (int k = 0; k < 3; ++k) d2 += (r.sph_off[i][k] - lc[j][k]) * (r.sph_off[i][k] - lc[j][k]);
+                lr[j] = std::max(lr[j], std::sqrt(d2) + r.sph_r[i]);
+            }
+            for (int k = 0; k < 3; ++k) r.link_c[j][k] = static_cast<float>(lc[j][k]);
+        }
+        struct P { int fa, fb, a, b; };
+        std::vector<P> ps;
+        for (int i = 0; i < rb->n_self_pairs; ++i) {
+            int a = inv[rb->self_pairs[2 * i]], b = inv[rb->self_pairs[2 * i + 1]];
+            int fa = rb->sphere_link[order[a]] - 1, fb = rb->sphere_link[order[b]] - 1;
+            if (fa > fb) { std::swap(a, b); std::swap(fa, fb); }
+            ps.push_back(P{fa, fb, a, b});
+        }
+        std::stable_sort(ps.begin(), ps.end(),
+                         [](const P &x, const P &y) { return x.fa != y.fa ? x.fa < y.fa : x.fb < y.fb; });
+        int g = -1;
+        for (size_t i = 0; i < ps.size(); ++i) {
+            if (g < 0 || ps[i].fa != r.grp_fa[g] || ps[i].fb != r.grp_fb[g]) {
+                ++g;
+                r.grp_fa[g] = static_cast<unsigned char>(ps[i].fa);
+                r.grp_fb[g] = static_cast<unsigned char>(ps[i].fb);
+                r.grp_begin[g] = static_cast<unsigned short>(i);
+                // exact skip with a 0.1 mm + 1e-5 relative margin for FP32 rounding
+                const double R = lr[ps[i].fa] + lr[ps[i].fb];
+                const double thr = R + 1e-4 + 1e-5 * R;
+                r.grp_thr2[g] = std::nextafter(static_cast<float>(thr * thr), INFINITY);
+            }
+            self_pairs.push_back(static_cast<unsigned>(ps[i].a) | (static_cast<unsigned>(ps[i].b) << 8));
+            self_rsum.push_back(r.sph_r[ps[i].a] + r.sph_r[ps[i].b]);
+        }
+        r.n_self_groups = g + 1;
+        r.grp_begin[g + 1] = static_cast<unsigned short>(ps.size());
+    }
     for (int i = 0; i < 6; ++i) { r.Q[i] = cp->Q[i]; r.QH[i] = cp->QH[i]; }
     r.w_env = cp->w_env; r.d_act = cp->d_act; r.w_self = cp->w_self;
     r.w_q = cp->w_q; r.w_qd = cp->w_qd; r.w_qdd = cp->w_qdd;
@@ -639,7 +699,6 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         !ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault), "stream") ||
         !ck(cudaMalloc(&c->d_grid, elems * dtype_size(gd->dtype)), "grid alloc") ||
         !ck(cudaMalloc(&c->d_rc, sizeof(RobotConst)), "robot constants alloc") ||
-        !ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy") ||
         !ck(cudaMalloc(&c->d_cmin, elems * sizeof(float)), "cell-minimum alloc") ||
         !ck(cudaMalloc(&c->d_stage, sizeof(float) * kSlots * kSlotFloats), "staging alloc") ||
         !ck(cudaMallocHost(&c->h_stage, sizeof(float) * kSlots * kSlotFloats), "pinned staging alloc") ||
@@ -670,6 +729,20 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     for (int k = 0; k < kSlots; ++k)
         if (!ck(cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming), "event"))
             return fail(PM_ECUDA);
+    if (!self_pairs.empty()) {
+        if (!ck(cudaMalloc(&c->d_self_pairs, self_pairs.size() * sizeof(unsigned)), "self pairs alloc") ||
+            !ck(cudaMalloc(&c->d_self_rsum, self_rsum.size() * sizeof(float)), "self radii alloc"))
+            return fail(PM_ENOMEM);
+        if (!ck(cudaMemcpy(c->d_self_pairs, self_pairs.data(), self_pairs.size() * sizeof(unsigned),
+                           cudaMemcpyHostToDevice), "self pairs copy") ||
+            !ck(cudaMemcpy(c->d_self_rsum, self_rsum.data(), self_rsum.size() * sizeof(float),
+                           cudaMemcpyHostToDevice), "self radii copy"))
+            return fail(PM_ECUDA);
+        c->rc.self_pairs = c->d_self_pairs;
+        c->rc.self_rsum = c->d_self_rsum;
+    }
+    if (!ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy"))
+        return fail(PM_ECUDA);
     *out = c;
     return PM_OK;
 }
@@ -990,6 +1063,8 @@ void pm_destroy(pm_ctx *c)
         if (c->stream) cudaStreamSynchronize(c->stream);
         cudaFree(c->d_grid);
         cudaFree(c->d_rc);
+        cudaFree(c->d_self_pairs);
+        cudaFree(c->d_self_rsum);
         cudaFree(c->d_cmin);
         if (c->cmin_tex) cudaDestroyTextureObject(c->cmin_tex);
         if (c->cmin_arr) cudaFreeArray(c->cmin_arr);
@@ -1073,7 +1148,7 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
     if (st != PM_OK) return st;
     IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
     if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
-    const size_t smem = iteration_smem_bytes(sh.C);
+    const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
     const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
     if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
     const long long resident = static_cast<long long>(c->n_sm) * per_sm;

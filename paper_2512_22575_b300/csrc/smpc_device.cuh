@@ -22,6 +22,8 @@ namespace pm {
 constexpr int kNJ = 7;            // joints of the compiled kinematic chain
 constexpr int kMaxSpheres = 64;
 constexpr int kMaxHorizon = 256;
+constexpr int kMaxSelfGroups = (kNJ * (kNJ + 1)) / 2;   // frame pairs (a <= b) of the self-collision set
+constexpr int kMaxSelfPairs = 4096;
 
 // Arm + cost constants, passed by value as a kernel parameter (constant bank).
 struct RobotConst {
@@ -44,7 +46,23 @@ struct RobotConst {
     float w_env, d_act, w_self;
     float w_q, w_qd, w_qdd, w_s, w_ns;
     float q_ref[kNJ];
+    // Self-collision set S (Eq. 18), grouped by the frames (a <= b) of its
+    // two spheres; n_self_groups = 0 switches the term off.  A group whose
+    // frames' bounding-sphere centres are farther apart than
+    // sqrt(grp_thr2) holds no pair closer than the sum of its radii, so
+    // its violations are exactly 0 and it is skipped.
+    int n_self_groups;
+    unsigned char grp_fa[kMaxSelfGroups], grp_fb[kMaxSelfGroups];   // frame index - 1
+    unsigned short grp_begin[kMaxSelfGroups + 1];                    // pairs of group g
+    float grp_thr2[kMaxSelfGroups];
+    float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
+    const unsigned *self_pairs;   // device [n]: internal sphere a | b << 8, grouped
+    const float *self_rsum;       // device [n]: r_a + r_b
 };
+
+// Per-lane shared-memory slots of the self-collision term: the world
+// centres of the step's spheres, then of the frames' bounding spheres.
+__host__ __device__ constexpr int self_slots(int n_spheres) { return 3 * n_spheres + 3 * kNJ; }
 
 struct GridConst {
     const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16

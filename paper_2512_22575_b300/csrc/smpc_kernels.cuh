@@ -47,6 +47,12 @@ constexpr size_t iteration_smem_bytes(int C)
     return 2u * kWarps * C * kNJ * 32 * sizeof(float);
 }
 
+// Extra dynamic shared memory of the self-collision term (0 when off).
+inline size_t self_smem_bytes(const RobotConst &rc)
+{
+    return rc.n_self_groups > 0 ? static_cast<size_t>(kWarps) * 32 * self_slots(rc.n_spheres) * sizeof(float) : 0;
+}
+
 struct IterArgs {
     CallInputs in;              // q0, qd0, T_goal (device), sigma
     const float *Ubar;          // [H][7]
@@ -86,7 +92,7 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 // located exactly and interpolated from their 8 corners.
 template <typename GT>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
-                                          const Frame &F, int b, int e, unsigned &ngath)
+                                          const Frame &F, int b, int e, unsigned &ngath, float *sp)
 {
     float env = 0.f;
     for (int s0 = b; s0 < e; s0 += kSphereBatch) {
@@ -95,6 +101,11 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
             const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+            if (sp) {                           // kept for the self-collision term
+                sp[(3 * s) * 32] = p.x;
+                sp[(3 * s + 1) * 32] = p.y;
+                sp[(3 * s + 2) * 32] = p.z;
+            }
             mn[i] = tex3D<float>(g.cmin_tex, cell_centre(fmaf(p.x, g.inv_res, g.bx)),
                                  cell_centre(fmaf(p.y, g.inv_res, g.by)), cell_centre(fmaf(p.z, g.inv_res, g.bz)));
         }
@@ -116,6 +127,33 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
     return env;
 }
 
+// Self-collision term (Eqs. 18-20): w_self sum over S of max(0, -d_self)^2,
+// d_self = |c_a - c_b| - (r_a + r_b), from the sphere and bounding-sphere
+// centres the step stored in its lane's slots sp (stride 32 floats).
+__device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp)
+{
+    const int lb0 = 3 * rc.n_spheres;
+    float acc = 0.f;
+    for (int gi = 0; gi < rc.n_self_groups; ++gi) {
+        const int fa = lb0 + 3 * rc.grp_fa[gi], fb = lb0 + 3 * rc.grp_fb[gi];
+        const float gx = sp[fa * 32] - sp[fb * 32];
+        const float gy = sp[(fa + 1) * 32] - sp[(fb + 1) * 32];
+        const float gz = sp[(fa + 2) * 32] - sp[(fb + 2) * 32];
+        if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > rc.grp_thr2[gi]) continue;   // exact zero
+        for (int p = rc.grp_begin[gi]; p < rc.grp_begin[gi + 1]; ++p) {
+            const unsigned ab = __ldg(rc.self_pairs + p);
+            const int a = 3 * static_cast<int>(ab & 0xffu), b = 3 * static_cast<int>(ab >> 8);
+            const float ex = sp[a * 32] - sp[b * 32];
+            const float ey = sp[(a + 1) * 32] - sp[(b + 1) * 32];
+            const float ez = sp[(a + 2) * 32] - sp[(b + 2) * 32];
+            const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) - __ldg(rc.self_rsum + p);
+            const float del = fmaxf(-d, 0.f);
+            acc = fmaf(del, del, acc);
+        }
+    }
+    return rc.w_self * acc;
+}
+
 // State terms at a step (Eqs. 16, 19-20, 22, 24), or the terminal cost (Eq. 25).
 // Forward kinematics runs frame by frame; the spheres of each frame are
 // looked up as soon as it is known.
@@ -123,8 +161,9 @@ template <typename GT, bool TRACE>
 __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
                                             const InstanceState &st, const float *q,
                                             const float *qd, bool terminal, float *tr,
-                                            unsigned &ngath)
+                                            unsigned &ngath, float *sp)
 {
+    if (terminal) sp = nullptr;
     float lq = 0.f, lqd = 0.f, ns = 0.f;
     if (!terminal) {
 #pragma unroll
@@ -150,7 +189,14 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], qr[0] + rc.th0[j]);
 #pragma unroll
         for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
-        if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath);
+        if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
+        if (sp) {
+            const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
+            const int t = 3 * rc.n_spheres + 3 * j;
+            sp[t * 32] = c.x;
+            sp[(t + 1) * 32] = c.y;
+            sp[(t + 2) * 32] = c.z;
+        }
     }
     const f3 tee = axpy(rc.flange_d, F.c3, F.t);
     float xi[6];
@@ -165,8 +211,9 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     lq *= rc.w_q;
     lqd *= rc.w_qd;
     ns *= rc.w_ns;
-    if (TRACE) { tr[0] = pose; tr[1] = env; tr[3] = lq; tr[4] = lqd; tr[7] = ns; }
-    return pose + env + lq + lqd + ns;
+    const float self = sp ? self_cost(rc, sp) : 0.f;
+    if (TRACE) { tr[0] = pose; tr[1] = env; tr[2] = self; tr[3] = lq; tr[4] = lqd; tr[7] = ns; }
+    return pose + env + self + lq + lqd + ns;
 }
 
 // ---------------------------------------------------------- warp scans
@@ -221,6 +268,7 @@ struct BlockSmem {
     float (*S)[2][2];           // [kWarps/2 + 1] pair partial costs
     float *blk;                 // [C*L*P*7] block accumulator
     float *wm, *wz;             // [kWarps]
+    float *self;                // [kWarps][self_slots][32] when the self term is on, else null
 };
 
 // Local block lb (of job.nb) of an instance: its roll-out tiles, then its
@@ -246,6 +294,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 
     float run_m = CUDART_INF_F, run_z = 0.f;
     const float dt = job.dt, dt2 = job.dt * job.dt;
+    float *sp = (rc.n_self_groups > 0 && sm.self) ? sm.self + warp * self_slots(rc.n_spheres) * 32 + lane
+                                                  : nullptr;
     const int half = (P == 2) ? (warp & 1) : 0;
     const int pr = warp >> 1;
     const int kbase = half * 32 * C;
@@ -352,7 +402,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 tr_x = tr_u + kTraceCols;
             }
             const unsigned ng0 = ngath;
-            const float sc = state_cost<GT, TRACE>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath);
+            const float sc = state_cost<GT, TRACE>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp);
             if (extra) {
                 ngath = ng0;        // lookups of the roll-outs only
                 *job.c0 = sc;
@@ -490,7 +540,8 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     job.dt = a.dt;
     job.inv_lambda = a.inv_lambda;
     job.noise_dtype = a.noise_dtype;
-    BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz};
+    BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
+                 rc.n_self_groups > 0 ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr};
     unsigned ngath = 0;
     run_block<GT, TRACE>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
     if (!TRACE && a.gathers) {

@@ -12,7 +12,7 @@ configurations, target poses) are written by ``oracle/make_scenes.py``, which
 uses the oracle's forward kinematics for the collision-free and reachability
 rejection tests; this package only reads them.
 """
-from .robot import panda_robot, default_cost_params, READY_POSE
+from .robot import panda_robot, default_cost_params, self_collision_pairs, READY_POSE
 from .scenes import (
     GridDesc,
     occupancy_grid,
@@ -26,6 +26,7 @@ from .scenes import (
 __all__ = [
     "panda_robot",
     "default_cost_params",
+    "self_collision_pairs",
     "READY_POSE",
     "GridDesc",
     "occupancy_grid",
