@@ -354,6 +354,42 @@ pm_status pm_server_get_stats(pm_server *server, pm_server_stats *out);
 void pm_server_destroy(pm_server *server);
 
 /*
+ * Mapping (Sec. III-B; Sec. IV-B-2, Remark 2).
+ *
+ * pm_edt_squared: exact squared Euclidean distance transform of an
+ *   occupancy grid, in voxel units: d2[v] = min over occupied voxels o of
+ *   |v - o|^2, or INT32_MAX when no voxel is occupied.  The separable
+ *   three-pass transform (1-D Felzenszwalb-Huttenlocher lower envelope along
+ *   y, x, then z), each line gathered by one thread into its own
+ *   shared-memory column on the native layout (Sec. III-B).  occ: device
+ *   uint8 [nz][ny][nx] (non-zero = occupied); d2: device int32 [nz][ny][nx].
+ *   Each extent 1..16384.  Enqueued on cuda_stream (NULL:
+ *   the legacy default stream); allocates its scratch on that stream.
+ *   Errors: PM_EINVAL, PM_ENOMEM, PM_ECUDA.
+ * pm_robot_mask: clears (sets to 0) every voxel of occ whose centre lies in
+ *   a sphere of the context's model at configuration q (radius + inflate,
+ *   closed ball), so that the robot's own body is not fused into the map
+ *   (Remark 2).  occ: device uint8 on the context's grid; q: host or device
+ *   [7]; inflate >= 0 m.  Enqueued on cuda_stream (NULL: the context's);
+ *   waits for it when q is host memory.
+ * pm_map_update: the context's distance field from an occupancy grid:
+ *   occ (host or device as occ_is_device says, uint8 on the context's grid)
+ *   is copied, masked at q_mask if it is not NULL (pm_robot_mask with
+ *   inflate), transformed on the GPU (pm_edt_squared), converted to metres
+ *   phi = res sqrt(d2) (rounded once from FP64 to the field's storage type;
+ *   1e10 m if nothing is occupied) and installed with its cell minima, as
+ *   pm_set_distance_field does.  Enqueued on cuda_stream (NULL: the
+ *   context's); the scratch (1 + 8 bytes per voxel) is allocated on first
+ *   use.  Iterations reading the field on other streams must not overlap it.
+ *   The paper has no separate entry for this; it is the mapping step that
+ *   precedes planning.
+ */
+pm_status pm_edt_squared(const uint8_t *occ, int nx, int ny, int nz, int32_t *d2, void *cuda_stream);
+pm_status pm_robot_mask(pm_ctx *ctx, uint8_t *occ, const float *q, float inflate, void *cuda_stream);
+pm_status pm_map_update(pm_ctx *ctx, const uint8_t *occ, int occ_is_device, const float *q_mask,
+                        float inflate, void *cuda_stream);
+
+/*
  * Diagnostics used by the parity tests (same device code as the hot path).
  *
  * pm_philox4x32_10: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key) for

@@ -78,6 +78,8 @@ def lib():
         L.or_replan.restype = C.c_int
         L.or_edt_bruteforce.argtypes = [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int,
                                         C.POINTER(C.c_int64)]
+        L.or_robot_mask.argtypes = [C.POINTER(OrRobot), _PD, C.c_int, C.c_int, C.c_int, C.c_double,
+                                    _PD, C.c_double, C.POINTER(C.c_uint8)]
         _lib = L
     return _lib
 
@@ -279,3 +281,15 @@ def edt_bruteforce(occ):
 
 def cores_available():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def robot_mask(robot, grid_desc, q, occ, inflate=0.0):
+    """Copy of occ (nz, ny, nx) with the voxels covered by the sphere model at
+    q cleared (Sec. IV-B-2, Remark 2)."""
+    out = np.ascontiguousarray(np.array(occ, dtype=np.uint8, copy=True))
+    nz, ny, nx = out.shape
+    origin = _f64(grid_desc.origin)
+    lib().or_robot_mask(C.byref(robot), _dp(_f64(q)), nx, ny, nz, float(grid_desc.res), _dp(origin),
+                        float(inflate), out.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return out
+

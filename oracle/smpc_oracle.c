@@ -523,3 +523,31 @@ void or_edt_bruteforce(const uint8_t *occ, int nx, int ny, int nz, int64_t *D)
             }
     free(sx); free(sy); free(sz);
 }
+
+/* Robot-masked occupancy reset (Sec. IV-B-2, Remark 2): every voxel whose
+ * centre origin + (i + 1/2, j + 1/2, l + 1/2) res lies within a sphere of the
+ * model at configuration q (radius + inflate, closed ball) is set to 0 in
+ * occ [nz][ny][nx]; other voxels are left as they are. */
+void or_robot_mask(const or_robot *rb, const double *q, int nx, int ny, int nz, double res,
+                   const double *origin, double inflate, uint8_t *occ)
+{
+    double T[OR_MAX_J + 2][4][4];
+    double p[OR_MAX_S][3];
+    or_fk(rb, q, T);
+    or_sphere_centres(rb, T, p);
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double c[3] = { origin[0] + (i + 0.5) * res, origin[1] + (j + 0.5) * res,
+                                      origin[2] + (l + 0.5) * res };
+                for (int s = 0; s < rb->n_spheres; ++s) {
+                    const double dx = c[0] - p[s][0], dy = c[1] - p[s][1], dz = c[2] - p[s][2];
+                    const double r = rb->sphere_radius[s] + inflate;
+                    if (dx * dx + dy * dy + dz * dz <= r * r) {
+                        occ[((size_t)l * ny + j) * nx + i] = 0;
+                        break;
+                    }
+                }
+            }
+}
+

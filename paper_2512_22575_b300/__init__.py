@@ -53,7 +53,8 @@ def _ptr(x, dtype=np.float32, n=None, writable=False):
     if hasattr(x, "data_ptr"):  # torch tensor
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
-        want = {np.float32: "torch.float32", np.uint32: "torch.uint32"}[dtype]
+        want = {np.float32: "torch.float32", np.uint32: "torch.uint32", np.uint8: "torch.uint8",
+                np.int32: "torch.int32"}[dtype]
         if str(x.dtype) != want:
             raise ValueError(f"tensor dtype {x.dtype} != {want}")
         if n is not None and x.numel() < n:
@@ -187,6 +188,35 @@ def rollout_trace(ctx, q0, qd0, T_goal, U, K, dt, sigma, seed, iter_index, trace
                                   _ptr(U, n=7 * H), int(K), H, float(dt), _ptr(sigma),
                                   C.c_uint64(int(seed)), C.c_uint32(int(iter_index)),
                                   _ptr(trace, n=int(K) * (H + 1) * 8, writable=True)), ctx)
+
+
+def edt_squared(occ, d2, stream=None):
+    """pm_edt_squared: occ CUDA uint8 [nz][ny][nx] -> d2 CUDA int32 (squared
+    distances in voxels; 2^31 - 1 when nothing is occupied)."""
+    nz, ny, nx = (int(x) for x in occ.shape)
+    _check(lib().pm_edt_squared(_ptr(occ, np.uint8, nx * ny * nz), nx, ny, nz,
+                                _ptr(d2, np.int32, nx * ny * nz, writable=True), _stream(stream)))
+
+
+def robot_mask(ctx, occ, q, inflate=0.0, stream=None):
+    """pm_robot_mask: clear the voxels of occ (CUDA uint8, the context's grid)
+    covered by the sphere model at q."""
+    q = q if hasattr(q, "data_ptr") else _f32(q, 7)
+    _check(lib().pm_robot_mask(ctx, _ptr(occ, np.uint8, writable=True), _ptr(q, n=7), float(inflate),
+                               _stream(stream)), ctx)
+
+
+def map_update(ctx, occ, q_mask=None, inflate=0.0, stream=None):
+    """pm_map_update: the context's field from an occupancy grid (numpy or
+    CUDA uint8 [nz][ny][nx]), masked at q_mask if given."""
+    dev = hasattr(occ, "data_ptr")
+    if not dev:
+        occ = np.ascontiguousarray(np.asarray(occ, dtype=np.uint8))
+    if q_mask is not None and not hasattr(q_mask, "data_ptr"):
+        q_mask = _f32(q_mask, 7)
+    _check(lib().pm_map_update(ctx, _ptr(occ, np.uint8), int(dev),
+                               _ptr(q_mask, n=7) if q_mask is not None else None, float(inflate),
+                               _stream(stream)), ctx)
 
 
 def fp32_fma_peak(device=0):
@@ -432,6 +462,12 @@ class Planner:
 
     def set_distance_field(self, grid):
         set_distance_field(self.ctx, grid)
+
+    def map_update(self, occ, q_mask=None, inflate=0.0, stream=None):
+        map_update(self.ctx, occ, q_mask, inflate, stream)
+
+    def robot_mask(self, occ, q, inflate=0.0, stream=None):
+        robot_mask(self.ctx, occ, q, inflate, stream)
 
     def smpc_iterate(self, *a, **kw):
         smpc_iterate(self.ctx, *a, **kw)

@@ -101,6 +101,9 @@ SIGNATURES = {
     "pm_submit": (C.c_int, [_V, C.POINTER(PmRequest), C.POINTER(C.c_uint64)]),
     "pm_submit_many": (C.c_int, [_V, C.POINTER(PmRequest), C.c_int, C.POINTER(C.c_uint64)]),
     "pm_fp32_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "pm_edt_squared": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, _V, _V]),
+    "pm_robot_mask": (C.c_int, [_V, _V, _V, C.c_float, _V]),
+    "pm_map_update": (C.c_int, [_V, _V, C.c_int, _V, C.c_float, _V]),
     "pm_poll": (C.c_int, [_V, C.c_uint64, C.POINTER(PmResult)]),
     "pm_wait": (C.c_int, [_V, C.c_uint64, C.c_uint32, C.POINTER(PmResult)]),
     "pm_server_get_stats": (C.c_int, [_V, C.POINTER(PmServerStats)]),

@@ -13,6 +13,8 @@ struct pm_ctx {
     int n_sm = 0;
     pm::RobotConst rc{};
     pm::RobotConst *d_rc = nullptr;     // device copy (read by the batched kernels)
+    unsigned char *d_map_occ = nullptr; // mapping scratch: occupancy copy, two int32 EDT buffers
+    int *d_map_a = nullptr, *d_map_b = nullptr;
     unsigned *d_self_pairs = nullptr;   // self-collision pairs, grouped (rc.self_pairs)
     float *d_self_rsum = nullptr;       // their radius sums (rc.self_rsum)
     pm_grid_desc gd{};
@@ -43,7 +45,8 @@ struct pm_ctx {
     float *d_part = nullptr;            // block partials
     size_t cap_part = 0;
 
-    float *d_c0 = nullptr;              // [c0, best, q(8), qd(8), u0(8)]
+    float *d_c0 = nullptr;              // small scratch: [0] c0, [1] best, [8, 32) replan q, qd, u0,
+                                        // [32, 40) the robot mask's configuration
     pm::TileShape forced{0, 0, 0};          // tile shape set by pm_set_tile_shape (0 = default)
     unsigned long long *d_gathers = nullptr;  // 8-corner lookups, counted while enabled
     bool count_gathers = false;
@@ -58,6 +61,25 @@ struct pm_ctx {
 
 
 namespace pm {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// After d_grid holds a new field: its cell minima, the texture's array, and
+// has_grid; enqueued on s (called with the context's lock held).
+pm_status finish_distance_field(pm_ctx *c, cudaStream_t s);
 
 // Kernel view of a context's distance field.
 inline GridConst grid_const(const pm_ctx *c)

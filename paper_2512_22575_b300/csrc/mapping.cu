@@ -1,0 +1,308 @@
+// Mapping side of the path (Sec. III-B, Sec. IV-B-2 Remark 2): the exact
+// Euclidean distance transform of an occupancy grid on the GPU, the
+// robot-masked occupancy reset, and the update of a context's distance
+// field from an occupancy grid.
+//
+// EDT: the separable three-pass squared transform, one 1-D
+// Felzenszwalb-Huttenlocher lower envelope of parabolas per grid line, along
+// y, then x, then z, on the native [z][y][x] layout.  Each thread owns one
+// line: it gathers the line (stride 1, nx or nx*ny) into its own column of
+// shared memory, builds the envelope there and writes the line back -- no
+// transposition of the grid.  Envelope boundaries are kept as exact
+// fractions (numerator, denominator) and compared by 64-bit cross
+// multiplication, so the result is the exact integer squared distance.
+#include "ctx_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+using namespace pm;
+
+namespace {
+
+constexpr int kEdtInf = 0x7fffffff;      // no site on the line (yet)
+constexpr int kEdtMaxExtent = 1 << 14;
+
+// A line of the pass: n elements base + i*se, base = a*sa + b*sb for line
+// l = b*na + a.
+struct EdtPass {
+    int n, na, n_lines;
+    long long sa, sb, se;
+};
+
+// Per-thread shared-memory column of element i: buf[i * T + t].
+template <bool FROM_OCC>
+__global__ void edt_pass_kernel(const void *in, int *out, EdtPass ps)
+{
+    extern __shared__ int s_edt[];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int line = blockIdx.x * T + t;
+    if (line >= ps.n_lines) return;
+    const int n = ps.n;
+    int *f = s_edt;                                  // [n][T] input values
+    int *zn = s_edt + n * T;                         // [n][T] boundary numerators
+    short *v = reinterpret_cast<short *>(s_edt + 2 * n * T);    // [n][T] sites
+    unsigned short *zd = reinterpret_cast<unsigned short *>(v + n * T);   // [n][T] boundary denominators
+    const long long a = line % ps.na, b = line / ps.na;
+    const long long base = a * ps.sa + b * ps.sb;
+
+    // gather the line into this thread's column
+    for (int i = 0; i < n; ++i) {
+        const long long idx = base + i * ps.se;
+        int x;
+        if (FROM_OCC) x = static_cast<const unsigned char *>(in)[idx] ? 0 : kEdtInf;
+        else x = static_cast<const int *>(in)[idx];
+        f[i * T + t] = x;
+    }
+    // lower envelope of the parabolas y = (x - q)^2 + f[q] over the sites
+    int k = -1;
+    for (int q = 0; q < n; ++q) {
+        const int fq = f[q * T + t];
+        if (fq == kEdtInf) continue;
+        const long long hq = fq + static_cast<long long>(q) * q;
+        while (k >= 1) {
+            // the new parabola meets v[k]'s at s = (hq - h_v) / (2 (q - v));
+            // v[k] leaves the envelope when s <= its left boundary zn/zd
+            const int vk = v[k * T + t];
+            const long long num = hq - (f[vk * T + t] + static_cast<long long>(vk) * vk);
+            const long long den = 2LL * (q - vk);
+            if (num * zd[k * T + t] > static_cast<long long>(zn[k * T + t]) * den) break;
+            --k;
+        }
+        ++k;
+        v[k * T + t] = static_cast<short>(q);
+        if (k > 0) {
+            const int vp = v[(k - 1) * T + t];
+            zn[k * T + t] = static_cast<int>(hq - (f[vp * T + t] + static_cast<long long>(vp) * vp));
+            zd[k * T + t] = static_cast<unsigned short>(2 * (q - vp));
+        }
+    }
+    // evaluate the envelope at every element
+    int j = 0;
+    for (int q = 0; q < n; ++q) {
+        int d = kEdtInf;
+        if (k >= 0) {
+            while (j < k && static_cast<long long>(zn[(j + 1) * T + t]) < static_cast<long long>(q) * zd[(j + 1) * T + t])
+                ++j;
+            const int vj = v[j * T + t];
+            d = f[vj * T + t] + (q - vj) * (q - vj);
+        }
+        out[base + q * ps.se] = d;
+    }
+}
+
+// Shared memory per thread of a pass over lines of n elements.
+size_t edt_bytes_per_thread(int n) { return static_cast<size_t>(n) * (4 + 4 + 2 + 2); }
+
+// Threads per block: as many lines as fit 96 KiB of shared memory, a
+// multiple of 32 when possible.
+int edt_threads(int n)
+{
+    const size_t per = edt_bytes_per_thread(n);
+    int T = static_cast<int>(std::min<size_t>(128, (96u << 10) / per));
+    if (T >= 32) T -= T % 32;
+    return std::max(T, 1);
+}
+
+template <bool FROM_OCC>
+cudaError_t run_pass(const void *in, int *out, const EdtPass &ps, cudaStream_t s)
+{
+    const int T = edt_threads(ps.n);
+    const size_t smem = edt_bytes_per_thread(ps.n) * T;
+    cudaError_t e = cudaFuncSetAttribute(edt_pass_kernel<FROM_OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    edt_pass_kernel<FROM_OCC><<<(ps.n_lines + T - 1) / T, T, smem, s>>>(in, out, ps);
+    return cudaGetLastError();
+}
+
+// Squared EDT of occ [nz][ny][nx] into d2 (int32, kEdtInf without any site);
+// tmp is scratch of the same size (y pass into d2, x pass into tmp, z pass
+// back into d2).
+cudaError_t edt3d(const unsigned char *occ, int nx, int ny, int nz, int *d2, int *tmp, cudaStream_t s)
+{
+    const long long sy = nx, sz = static_cast<long long>(nx) * ny;
+    // y lines (x, z), x fastest across threads: coalesced gathers
+    EdtPass py{ny, nx, nx * nz, 1, sz, sy};
+    // x lines (y, z): each thread reads its own contiguous line
+    EdtPass px{nx, ny, ny * nz, sy, sz, 1};
+    // z lines (x, y): coalesced
+    EdtPass pz{nz, nx, nx * ny, 1, sy, sz};
+    cudaError_t e = run_pass<true>(occ, d2, py, s);
+    if (e == cudaSuccess) e = run_pass<false>(d2, tmp, px, s);
+    if (e == cudaSuccess) e = run_pass<false>(tmp, d2, pz, s);
+    return e;
+}
+
+// phi = res sqrt(D) in metres, rounded once from FP64 to the storage type;
+// without any occupied voxel phi = kFarField.
+constexpr double kFarField = 1e10;
+
+__global__ void d2_to_phi_kernel(const int *d2, void *phi, size_t n, double res, int dtype)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int d = d2[i];
+        const double m = d == kEdtInf ? kFarField : res * sqrt(static_cast<double>(d));
+        const float v = static_cast<float>(m);
+        if (dtype == PM_F32) static_cast<float *>(phi)[i] = v;
+        else if (dtype == PM_F16) static_cast<__half *>(phi)[i] = __float2half_rn(v);
+        else static_cast<__nv_bfloat16 *>(phi)[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Robot mask: block s clears the voxels of sphere s (centre at configuration
+// q, radius + inflate) whose centres lie in the closed ball.
+__global__ void robot_mask_kernel(const RobotConst rc, const float *q, unsigned char *occ, int nx, int ny,
+                                  int nz, float res, float ox, float oy, float oz, float inflate)
+{
+    const int s = blockIdx.x;
+    __shared__ float c[4];
+    __shared__ int box[6];
+    if (threadIdx.x == 0) {
+        int link = 0;
+        while (link < kNJ && rc.link_begin[link + 2] <= s) ++link;   // sphere s lies on frame link + 1
+        Frame F = base_frame();
+        for (int j = 0; j <= link; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
+        const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+        const float r = rc.sph_r[s] + inflate;
+        c[0] = p.x; c[1] = p.y; c[2] = p.z; c[3] = r;
+        // voxel index range whose centres can lie within r (one voxel of slack)
+        const float lo[3] = {(p.x - r - ox) / res - 1.5f, (p.y - r - oy) / res - 1.5f, (p.z - r - oz) / res - 1.5f};
+        const float hi[3] = {(p.x + r - ox) / res + 0.5f, (p.y + r - oy) / res + 0.5f, (p.z + r - oz) / res + 0.5f};
+        const int n[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; ++a) {
+            box[a] = static_cast<int>(fminf(fmaxf(floorf(lo[a]), 0.f), static_cast<float>(n[a])));
+            box[3 + a] = static_cast<int>(fminf(fmaxf(ceilf(hi[a]), 0.f), static_cast<float>(n[a])));
+        }
+    }
+    __syncthreads();
+    const int bx = box[3] - box[0], by = box[4] - box[1], bz = box[5] - box[2];
+    if (bx <= 0 || by <= 0 || bz <= 0) return;
+    const long long cnt = static_cast<long long>(bx) * by * bz;
+    const float r2 = c[3] * c[3];
+    for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int i = box[0] + static_cast<int>(t % bx);
+        const int j = box[1] + static_cast<int>((t / bx) % by);
+        const int l = box[2] + static_cast<int>(t / (static_cast<long long>(bx) * by));
+        const float dx = fmaf(static_cast<float>(i) + 0.5f, res, ox) - c[0];
+        const float dy = fmaf(static_cast<float>(j) + 0.5f, res, oy) - c[1];
+        const float dz = fmaf(static_cast<float>(l) + 0.5f, res, oz) - c[2];
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= r2) occ[(static_cast<size_t>(l) * ny + j) * nx + i] = 0;
+    }
+}
+
+pm_status map_err(pm_ctx *c, pm_status st, const char *msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+} // namespace
+
+extern "C" {
+
+pm_status pm_edt_squared(const uint8_t *occ, int nx, int ny, int nz, int32_t *d2, void *cuda_stream)
+{
+    // extents up to 2^14 keep every squared distance, parabola height and
+    // boundary numerator inside int32 and every site index in a short
+    if (!occ || !d2 || nx < 1 || ny < 1 || nz < 1 || nx > kEdtMaxExtent || ny > kEdtMaxExtent ||
+        nz > kEdtMaxExtent)
+        return PM_EINVAL;
+    const size_t n = static_cast<size_t>(nx) * ny * nz;
+    if (n >= (1ull << 31)) return PM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, n * sizeof(int), s);
+    if (e == cudaSuccess) e = edt3d(occ, nx, ny, nz, d2, tmp, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    }
+    return PM_OK;
+}
+
+pm_status pm_robot_mask(pm_ctx *c, uint8_t *occ, const float *q, float inflate, void *cuda_stream)
+{
+    if (!c) return PM_EINVAL;
+    if (!occ || !q) return map_err(c, PM_EINVAL, "NULL occupancy or configuration");
+    if (!std::isfinite(inflate) || inflate < 0.f) return map_err(c, PM_EINVAL, "inflate must be finite and >= 0");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+    // q: host or device [7]
+    cudaPointerAttributes pa{};
+    const bool dq = cudaPointerGetAttributes(&pa, q) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    const float *qd = q;
+    if (!dq) {
+        for (int j = 0; j < kNJ; ++j)
+            if (!std::isfinite(q[j])) return map_err(c, PM_EINVAL, "q has a non-finite entry");
+        float *slot = c->d_c0 + 32;            // the mask's slot of the context's small scratch
+        if (cudaMemcpyAsync(slot, q, kNJ * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return map_err(c, PM_ECUDA, "copy of q failed");
+        }
+        qd = slot;
+    }
+    if (c->rc.n_spheres > 0) {
+        robot_mask_kernel<<<c->rc.n_spheres, 256, 0, s>>>(c->rc, qd, occ, c->gd.nx, c->gd.ny, c->gd.nz, c->gd.res,
+                                                         c->gd.origin[0], c->gd.origin[1], c->gd.origin[2], inflate);
+        if (cudaGetLastError() != cudaSuccess) return map_err(c, PM_ECUDA, "robot mask launch failed");
+    }
+    if (!dq && cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return map_err(c, PM_ECUDA, "robot mask failed");
+    }
+    return PM_OK;
+}
+
+pm_status pm_map_update(pm_ctx *c, const uint8_t *occ, int occ_is_device, const float *q_mask, float inflate,
+                        void *cuda_stream)
+{
+    if (!c) return PM_EINVAL;
+    if (!occ) return map_err(c, PM_EINVAL, "occupancy is NULL");
+    const size_t n = c->grid_elems;
+    if (c->gd.nx > kEdtMaxExtent || c->gd.ny > kEdtMaxExtent || c->gd.nz > kEdtMaxExtent)
+        return map_err(c, PM_EINVAL, "grid extent above 16384 for the transform");
+    cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        DeviceGuard dg(c->device);
+        if (!c->d_map_occ) {
+            cudaError_t e = cudaMalloc(&c->d_map_occ, n);
+            if (e == cudaSuccess) e = cudaMalloc(&c->d_map_a, n * sizeof(int));
+            if (e == cudaSuccess) e = cudaMalloc(&c->d_map_b, n * sizeof(int));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return map_err(c, PM_ENOMEM, "mapping scratch allocation failed");
+            }
+        }
+        if (cudaMemcpyAsync(c->d_map_occ, occ, n, occ_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s) != cudaSuccess) {
+            cudaGetLastError();
+            return map_err(c, PM_ECUDA, "occupancy copy failed");
+        }
+    }
+    if (q_mask) {
+        const pm_status st = pm_robot_mask(c, c->d_map_occ, q_mask, inflate, s);
+        if (st != PM_OK) return st;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    cudaError_t e = edt3d(c->d_map_occ, c->gd.nx, c->gd.ny, c->gd.nz, c->d_map_a, c->d_map_b, s);
+    if (e == cudaSuccess) {
+        d2_to_phi_kernel<<<static_cast<unsigned>(std::min<size_t>((n + 255) / 256, 8u * c->n_sm)), 256, 0, s>>>(
+            c->d_map_a, c->d_grid, n, static_cast<double>(c->gd.res), c->gd.dtype);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return map_err(c, PM_ECUDA, "distance transform failed");
+    }
+    return finish_distance_field(c, s);
+}
+
+} // extern "C"

@@ -45,21 +45,6 @@ pm_status set_err(pm_ctx *ctx, pm_status st, const char *fmt, ...)
                            __LINE__);                                                     \
     } while (0)
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 bool finite_all(const float *p, int n)
 {
     for (int i = 0; i < n; ++i)
@@ -488,6 +473,30 @@ int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
     return n;
 }
 
+pm_status pm::finish_distance_field(pm_ctx *c, cudaStream_t s)
+{
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((c->grid_elems + 255) / 256, 8u * c->n_sm));
+    if (c->gd.dtype == PM_F32)
+        cell_min_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(c->d_grid), c->d_cmin,
+                                              c->gd.nx, c->gd.ny, c->gd.nz);
+    else if (c->gd.dtype == PM_F16)
+        cell_min_kernel<<<blocks, 256, 0, s>>>(static_cast<const __half *>(c->d_grid), c->d_cmin,
+                                              c->gd.nx, c->gd.ny, c->gd.nz);
+    else
+        cell_min_kernel<<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->d_grid),
+                                              c->d_cmin, c->gd.nx, c->gd.ny, c->gd.nz);
+    PM_CUDA(c, cudaGetLastError());
+    // cell minima into the texture's array
+    cudaMemcpy3DParms cp{};
+    cp.srcPtr = make_cudaPitchedPtr(c->d_cmin, c->gd.nx * sizeof(float), c->gd.nx - 1, c->gd.ny);
+    cp.dstArray = c->cmin_arr;
+    cp.extent = make_cudaExtent(c->gd.nx - 1, c->gd.ny - 1, c->gd.nz - 1);
+    cp.kind = cudaMemcpyDeviceToDevice;
+    PM_CUDA(c, cudaMemcpy3DAsync(&cp, s));
+    c->has_grid = true;
+    return PM_OK;
+}
+
 pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &in, float *U, int K, int H,
                                   int n_iters, float dt, float lambda, uint64_t seed, uint32_t iter0,
                                   float *part, size_t part_floats, float *c0, float *q_out, float *qd_out,
@@ -706,8 +715,8 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
 
         !ck(cudaMalloc(&c->d_gathers, sizeof(unsigned long long)), "counter alloc") ||
         !ck(cudaMemset(c->d_gathers, 0, sizeof(unsigned long long)), "counter zero") ||
-        !ck(cudaMalloc(&c->d_c0, 32 * sizeof(float)), "c0") ||
-        !ck(cudaMemset(c->d_c0, 0, 32 * sizeof(float)), "c0 zero"))
+        !ck(cudaMalloc(&c->d_c0, 48 * sizeof(float)), "c0") ||
+        !ck(cudaMemset(c->d_c0, 0, 48 * sizeof(float)), "c0 zero"))
         return fail(c->err.find("alloc") != std::string::npos ? PM_ENOMEM : PM_ECUDA);
     {
         // cell minima: 3-D array + point-sampled, clamped texture
@@ -772,27 +781,9 @@ pm_status pm_set_distance_field(pm_ctx *c, const float *grid, int grid_is_device
         cudaFree(tmp);
         PM_CUDA(c, e);
     }
-    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((c->grid_elems + 255) / 256, 8u * c->n_sm));
-    if (c->gd.dtype == PM_F32)
-        cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->d_grid), c->d_cmin,
-                                                      c->gd.nx, c->gd.ny, c->gd.nz);
-    else if (c->gd.dtype == PM_F16)
-        cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const __half *>(c->d_grid), c->d_cmin,
-                                                      c->gd.nx, c->gd.ny, c->gd.nz);
-    else
-        cell_min_kernel<<<blocks, 256, 0, c->stream>>>(static_cast<const __nv_bfloat16 *>(c->d_grid),
-                                                      c->d_cmin, c->gd.nx, c->gd.ny, c->gd.nz);
-    PM_CUDA(c, cudaGetLastError());
-    // cell minima into the texture's array
-    cudaMemcpy3DParms cp{};
-    cp.srcPtr = make_cudaPitchedPtr(c->d_cmin, c->gd.nx * sizeof(float), c->gd.nx - 1, c->gd.ny);
-    cp.dstArray = c->cmin_arr;
-    cp.extent = make_cudaExtent(c->gd.nx - 1, c->gd.ny - 1, c->gd.nz - 1);
-    cp.kind = cudaMemcpyDeviceToDevice;
-    cudaError_t e = cudaMemcpy3DAsync(&cp, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    PM_CUDA(c, e);
-    c->has_grid = true;
+    pm_status st = finish_distance_field(c, c->stream);
+    if (st != PM_OK) return st;
+    PM_CUDA(c, cudaStreamSynchronize(c->stream));
     return PM_OK;
 }
 
@@ -1063,6 +1054,9 @@ void pm_destroy(pm_ctx *c)
         if (c->stream) cudaStreamSynchronize(c->stream);
         cudaFree(c->d_grid);
         cudaFree(c->d_rc);
+        cudaFree(c->d_map_occ);
+        cudaFree(c->d_map_a);
+        cudaFree(c->d_map_b);
         cudaFree(c->d_self_pairs);
         cudaFree(c->d_self_rsum);
         cudaFree(c->d_cmin);

@@ -570,3 +570,31 @@ def test_replan_shift_and_state_advance(R, cfg1):
     qd_ref = sc["qd0"].astype(np.float64) + dt * U[0]
     assert np.allclose(qd, qd_ref, atol=0) and np.allclose(q, sc["q0"] + dt * qd_ref, atol=0)
     assert np.array_equal(Un[:-1], U[1:]) and np.array_equal(Un[-1], U[-1])
+
+
+def test_robot_mask_single_sphere():
+    """One sphere at the origin of frame 1, which sits at (0, 0, d_1) for every
+    q: the mask clears exactly the voxels whose centres lie in that closed
+    ball (radius + inflate) and nothing else."""
+    rb = workloads.panda_robot()
+    one = dict(rb)
+    one["sphere_link"] = np.array([1], np.int32)
+    one["sphere_offset"] = np.zeros((1, 3), np.float32)
+    one["sphere_radius"] = np.array([0.05], np.float32)
+    one["self_pairs"] = np.zeros((0, 2), np.int32)
+    R1 = oracle.make_robot(one)
+    g = workloads.GridDesc(nx=24, ny=20, nz=30, res=0.01, origin=(-0.12, -0.1, 0.2))
+    rng = np.random.default_rng(4)
+    occ = (rng.random(g.shape) < 0.5).astype(np.uint8)
+    centre = np.array([0.0, 0.0, float(rb["d"][0])])
+    l, j, i = np.meshgrid(np.arange(g.nz), np.arange(g.ny), np.arange(g.nx), indexing="ij")
+    cx = g.origin[0] + (i + 0.5) * g.res
+    cy = g.origin[1] + (j + 0.5) * g.res
+    cz = g.origin[2] + (l + 0.5) * g.res
+    d2 = (cx - centre[0]) ** 2 + (cy - centre[1]) ** 2 + (cz - centre[2]) ** 2
+    for inflate in (0.0, 0.013):
+        q = rng.uniform(-1.0, 1.0, 7)
+        got = oracle.robot_mask(R1, g, q, occ, inflate)
+        inside = d2 <= (float(np.float32(0.05)) + inflate) ** 2
+        assert inside.sum() > 100
+        assert np.array_equal(got, np.where(inside, 0, occ))
