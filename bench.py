@@ -319,6 +319,83 @@ def bench_self_collision(pm, torch, dev, stream, w, Ts, n_replans=100, min_link_
             "kernel_ms_per_launch": kms / max(kn, 1), "replans": n_replans}
 
 
+def bench_episodes(pm, torch, dev, stream, K=4096, H=32, n_iters=8, max_replans=1000):
+    """The evaluation protocol (Sec. V-A) on the synthetic scenes: from each
+    cfg1 start state (10 scenes) and the replanning scene, replan at 50 Hz
+    (dt = 0.02 s) to the fixed goal until the objective's relative
+    improvement is below 1% and the flange is within 10 mm for 5 replans in
+    a row.  Pose weights 10x the parity workload's.  Reports the averages the
+    paper's Table I reports (planning time per replan, motion time, path
+    length, position and orientation error) and how many converged."""
+    import workloads
+    base = workloads.default_cost_params(np.zeros(7))
+    over = {"Q": base["Q"] * 10, "QH": base["QH"] * 10}
+    rows = []
+    for name in [f"cfg1_seed{i}" for i in range(10)] + ["cfg2"]:
+        sc = workloads.load_scene(name)
+        cp = workloads.default_cost_params(sc["q0"])
+        cp.update(over)
+        p = pm.Planner(workloads.panda_robot(), sc["grid"], cp, device=dev.index or 0)
+        p.set_distance_field(workloads.build_scene_grid(sc))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = p.plan_episode(sc["q0"], sc["qd0"], sc["T_goal"].ravel(), K, H, n_iters, 0.02, 0.05,
+                           np.full(7, 0.5, np.float32), 7, max_replans=max_replans, pos_tol=0.01,
+                           rel_tol=0.01, n_stable=5, stream=stream)
+        wall = time.perf_counter() - t0
+        p.close()
+        rows.append((r, wall))
+    conv = [r for r, _ in rows if r["converged"]]
+    mean = (lambda xs: float(np.mean(xs)) if xs else None)
+    return {"workload": f"11 scenes (10 plain + the replanning scene), K={K}, H={H}, {n_iters} iterations per "
+                        f"replan, dt = 0.02 s, convergence: <1% objective improvement and <10 mm, 5 replans",
+            "converged": len(conv), "episodes": len(rows),
+            "planning_ms_per_replan": mean([1e3 * w / r["replans"] for r, w in rows]),
+            "motion_time_s": mean([r["motion_time"] for r in conv]),
+            "path_length_rad": mean([r["path_length"] for r in conv]),
+            "e_pos_mm": mean([1e3 * r["e_pos"] for r in conv]),
+            "e_ori_rad": mean([r["e_ori"] for r in conv]),
+            "replans": [int(r["replans"]) for r, _ in rows]}
+
+
+def bench_mapping(pm, torch, dev, stream, w, reps=50):
+    """Mapping on the replanning grid (160 x 160 x 120 voxels at 1 cm):
+    pm_edt_squared alone, and pm_map_update (occupancy copy, robot mask at
+    the start configuration, transform, metres, cell minima), CUDA events on
+    the stream.  The transform's traffic model is 21 B per voxel (occupancy
+    byte in; three passes of an int32 read and write, the first without the
+    read)."""
+    import workloads
+    sc = w["scene"]
+    g = sc["grid"]
+    occ = torch.from_numpy(workloads.occupancy_grid(sc["obstacles"], g)).to(dev)
+    d2 = torch.empty(occ.shape, dtype=torch.int32, device=dev)
+    p = pm.Planner(w["robot"], g, w["cp"], device=dev.index or 0)
+    q0 = torch.from_numpy(sc["q0"].astype(np.float32)).to(dev)
+    n_vox = occ.numel()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_edt = timed(lambda: pm.edt_squared(occ, d2, stream=stream))
+    ms_upd = timed(lambda: p.map_update(occ, q_mask=q0, inflate=0.02, stream=stream))
+    p.close()
+    return {"workload": f"{g.nx}x{g.ny}x{g.nz} voxels at {g.res:g} m, {len(sc['obstacles'])} obstacles",
+            "edt_ms": ms_edt, "edt_voxels_per_s": n_vox / (ms_edt * 1e-3),
+            "edt_gbs_model": 21.0 * n_vox / (ms_edt * 1e-3) / 1e9,
+            "map_update_ms": ms_upd, "map_update_voxels_per_s": n_vox / (ms_upd * 1e-3)}
+
+
 def kernel_traffic_bytes():
     """DRAM bytes (read + write) per launch of the iteration kernel from the
     committed ncu counters, or None when the kernel sources changed since
@@ -702,6 +779,8 @@ def run_ours(args, rank, world, local):
     line["precision_variants"] = variants
     line["latency_cfg1"] = bench_latency_cfg1(pm, torch, dev, stream)
     line["self_collision"] = bench_self_collision(pm, torch, dev, stream, w, Ts)
+    line["episodes"] = bench_episodes(pm, torch, dev, stream)
+    line["mapping"] = bench_mapping(pm, torch, dev, stream, w)
     if not args.no_batched:
         line["batched"] = bench_batched(pm, torch, dev, stream)
     if not args.no_serving:

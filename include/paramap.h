@@ -354,6 +354,47 @@ pm_status pm_server_get_stats(pm_server *server, pm_server_stats *out);
 void pm_server_destroy(pm_server *server);
 
 /*
+ * Planning episode with the evaluation's convergence test (Sec. V-A): from
+ * (q0, qd0) replan against the fixed goal T_goal -- n_iters SMPC iterations,
+ * execute u0*, shift the sequence (pm_replan; replan t uses iteration
+ * indices t n_iters + it) -- until, for n_stable consecutive replans, the
+ * relative improvement of the objective (min S of the replan's last
+ * iteration) is below rel_tol and the position error is below pos_tol, or
+ * max_replans replans have run.  U0: initial sequence [H][7] (host or
+ * device) or NULL for zeros (Algorithm 1).  Metrics of the executed state
+ * after each replan: e_pos = |p_g - p| (flange), e_ori = 2 arccos |q_g . q|
+ * (computed as the angle of R_g^T R), path length = sum over replans and
+ * joints of |q_{t+1} - q_t|, motion time = replans dt.  q_final, qd_final
+ * (host or device, may be NULL) receive the final state; log (host, may be
+ * NULL) receives [max_replans][4] rows (e_pos, e_ori, objective, path so
+ * far) for the replans run.  Synchronous (one small read-back per replan
+ * decides termination).  Errors: as pm_replan, plus PM_EINVAL for bad
+ * settings.  The paper's loop runs at 50 Hz with pos_tol = 10 mm and
+ * n_stable = 5; rel_tol is not given (see the design notes).
+ */
+typedef struct {
+    int max_replans;
+    float pos_tol;          /* m                                           */
+    float rel_tol;          /* relative objective improvement              */
+    int n_stable;
+} pm_converge_cfg;
+
+typedef struct {
+    int converged;          /* 1 if the test held for n_stable replans     */
+    int replans;
+    float e_pos, e_ori;     /* final pose error (m, rad)                   */
+    float path_length;      /* rad                                          */
+    float motion_time;      /* s                                            */
+    float best_cost;        /* objective of the last replan                */
+} pm_episode;
+
+pm_status pm_plan_episode(pm_ctx *ctx, const float *q0, const float *qd0, const float *T_goal,
+                          const float *U0, int K, int H, int n_iters, float dt, float lambda,
+                          const float *sigma, uint64_t seed, const pm_converge_cfg *cfg,
+                          float *q_final, float *qd_final, pm_episode *out, float *log,
+                          void *cuda_stream);
+
+/*
  * Mapping (Sec. III-B; Sec. IV-B-2, Remark 2).
  *
  * pm_edt_squared: exact squared Euclidean distance transform of an

@@ -78,6 +78,7 @@ def lib():
         L.or_replan.restype = C.c_int
         L.or_edt_bruteforce.argtypes = [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int,
                                         C.POINTER(C.c_int64)]
+        L.or_pose_metrics.argtypes = [C.POINTER(OrRobot), _PD, _PD, _PD]
         L.or_robot_mask.argtypes = [C.POINTER(OrRobot), _PD, C.c_int, C.c_int, C.c_int, C.c_double,
                                     _PD, C.c_double, C.POINTER(C.c_uint8)]
         _lib = L
@@ -292,4 +293,12 @@ def robot_mask(robot, grid_desc, q, occ, inflate=0.0):
     lib().or_robot_mask(C.byref(robot), _dp(_f64(q)), nx, ny, nz, float(grid_desc.res), _dp(origin),
                         float(inflate), out.ctypes.data_as(C.POINTER(C.c_uint8)))
     return out
+
+
+def pose_metrics(robot, q, Tg):
+    """(e_pos [m], e_ori [rad]) of configuration q against the goal pose Tg
+    (Sec. V-A pose error metrics)."""
+    out = np.empty(2)
+    lib().or_pose_metrics(C.byref(robot), _dp(_f64(q)), _dp(_f64(Tg).reshape(16).copy()), _dp(out))
+    return float(out[0]), float(out[1])
 

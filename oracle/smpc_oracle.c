@@ -551,3 +551,56 @@ void or_robot_mask(const or_robot *rb, const double *q, int nx, int ny, int nz, 
             }
 }
 
+/* Unit quaternion (w, x, y, z) of a rotation matrix (Shepperd's method:
+ * the largest of 1 + tr, 1 + 2 R_ii - tr picks the stable formula). */
+static void rot_to_quat(const double R[3][3], double q[4])
+{
+    const double tr = R[0][0] + R[1][1] + R[2][2];
+    if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) {
+        const double w = 0.5 * sqrt(1.0 + tr);
+        q[0] = w;
+        q[1] = (R[2][1] - R[1][2]) / (4.0 * w);
+        q[2] = (R[0][2] - R[2][0]) / (4.0 * w);
+        q[3] = (R[1][0] - R[0][1]) / (4.0 * w);
+    } else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) {
+        const double x = 0.5 * sqrt(1.0 + 2.0 * R[0][0] - tr);
+        q[1] = x;
+        q[0] = (R[2][1] - R[1][2]) / (4.0 * x);
+        q[2] = (R[0][1] + R[1][0]) / (4.0 * x);
+        q[3] = (R[0][2] + R[2][0]) / (4.0 * x);
+    } else if (R[1][1] >= R[2][2]) {
+        const double y = 0.5 * sqrt(1.0 + 2.0 * R[1][1] - tr);
+        q[2] = y;
+        q[0] = (R[0][2] - R[2][0]) / (4.0 * y);
+        q[1] = (R[0][1] + R[1][0]) / (4.0 * y);
+        q[3] = (R[1][2] + R[2][1]) / (4.0 * y);
+    } else {
+        const double z = 0.5 * sqrt(1.0 + 2.0 * R[2][2] - tr);
+        q[3] = z;
+        q[0] = (R[1][0] - R[0][1]) / (4.0 * z);
+        q[1] = (R[0][2] + R[2][0]) / (4.0 * z);
+        q[2] = (R[1][2] + R[2][1]) / (4.0 * z);
+    }
+}
+
+/* Final pose error of configuration q against the goal Tg (row-major 4x4),
+ * as the evaluation defines it (Sec. V-A, pose error metrics):
+ * e_pos = |p_g - p|, e_ori = 2 arccos |q_g . q| with unit quaternions. */
+void or_pose_metrics(const or_robot *rb, const double *q, const double *Tg, double out[2])
+{
+    double T[OR_MAX_J + 2][4][4];
+    or_fk(rb, q, T);
+    const int n = rb->n_joints;
+    double dx = T[n + 1][0][3] - Tg[3], dy = T[n + 1][1][3] - Tg[7], dz = T[n + 1][2][3] - Tg[11];
+    out[0] = sqrt(dx * dx + dy * dy + dz * dz);
+    double Ra[3][3], Rb[3][3], qa[4], qb[4];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { Ra[i][j] = Tg[4 * i + j]; Rb[i][j] = T[n + 1][i][j]; }
+    rot_to_quat(Ra, qa);
+    rot_to_quat(Rb, qb);
+    double na = 0.0, nb = 0.0, d = 0.0;
+    for (int k = 0; k < 4; ++k) { na += qa[k] * qa[k]; nb += qb[k] * qb[k]; d += qa[k] * qb[k]; }
+    d = fabs(d) / sqrt(na * nb);
+    out[1] = 2.0 * acos(d > 1.0 ? 1.0 : d);
+}
+

@@ -16,7 +16,8 @@ import os
 
 import numpy as np
 
-from ._abi import (PM_BF16, PM_F16, PM_F32, PmBatchItem, PmCostParams, PmError, PmGridDesc,
+from ._abi import (PM_BF16, PM_F16, PM_F32, PmBatchItem, PmConvergeCfg, PmCostParams, PmEpisode, PmError,
+                   PmGridDesc,
                    PmRequest, PmResult, PmRobot, PmServerConfig, PmServerStats, STATUS_NAMES, lib,
                    lib_path)
 
@@ -188,6 +189,36 @@ def rollout_trace(ctx, q0, qd0, T_goal, U, K, dt, sigma, seed, iter_index, trace
                                   _ptr(U, n=7 * H), int(K), H, float(dt), _ptr(sigma),
                                   C.c_uint64(int(seed)), C.c_uint32(int(iter_index)),
                                   _ptr(trace, n=int(K) * (H + 1) * 8, writable=True)), ctx)
+
+
+def plan_episode(ctx, q0, qd0, T_goal, K, H, n_iters, dt, lam, sigma, seed, max_replans=500, pos_tol=0.01,
+                 rel_tol=0.01, n_stable=5, U0=None, with_log=False, stream=None):
+    """pm_plan_episode: replan to a fixed goal until the convergence test
+    holds; returns a dict with converged, replans, e_pos, e_ori, path_length,
+    motion_time, best_cost, q_final, qd_final and (with_log) log [replans][4]."""
+    H = int(H)
+    cfg = PmConvergeCfg(int(max_replans), float(pos_tol), float(rel_tol), int(n_stable))
+    ep = PmEpisode()
+    qf, qdf = np.empty(7, np.float32), np.empty(7, np.float32)
+    log = np.zeros((int(max_replans), 4), np.float32) if with_log else None
+    sigma = _f32(sigma, 7)
+    U0p = None
+    if U0 is not None:
+        U0 = U0 if hasattr(U0, "data_ptr") else np.ascontiguousarray(np.asarray(U0, np.float32))
+        U0p = _ptr(U0, n=7 * H)
+    q0 = q0 if hasattr(q0, "data_ptr") else _f32(q0, 7)
+    qd0 = qd0 if hasattr(qd0, "data_ptr") else _f32(qd0, 7)
+    T = T_goal if hasattr(T_goal, "data_ptr") else _f32(T_goal, 16)
+    _check(lib().pm_plan_episode(ctx, _ptr(q0, n=7), _ptr(qd0, n=7), _ptr(T, n=16), U0p, int(K), H, int(n_iters),
+                                 float(dt), float(lam), _ptr(sigma), C.c_uint64(int(seed)), C.byref(cfg),
+                                 _ptr(qf, writable=True), _ptr(qdf, writable=True), C.byref(ep),
+                                 _ptr(log, writable=True) if log is not None else None, _stream(stream)), ctx)
+    r = {n: getattr(ep, n) for n, _ in PmEpisode._fields_}
+    r["converged"] = bool(r["converged"])
+    r["q_final"], r["qd_final"] = qf, qdf
+    if log is not None:
+        r["log"] = log[:ep.replans].copy()
+    return r
 
 
 def edt_squared(occ, d2, stream=None):
@@ -468,6 +499,9 @@ class Planner:
 
     def robot_mask(self, occ, q, inflate=0.0, stream=None):
         robot_mask(self.ctx, occ, q, inflate, stream)
+
+    def plan_episode(self, *a, **kw):
+        return plan_episode(self.ctx, *a, **kw)
 
     def smpc_iterate(self, *a, **kw):
         smpc_iterate(self.ctx, *a, **kw)

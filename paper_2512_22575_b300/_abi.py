@@ -64,6 +64,15 @@ class PmResult(C.Structure):
                 ("queue_us", C.c_double), ("batch_size", C.c_int)]
 
 
+class PmConvergeCfg(C.Structure):
+    _fields_ = [("max_replans", C.c_int), ("pos_tol", C.c_float), ("rel_tol", C.c_float), ("n_stable", C.c_int)]
+
+
+class PmEpisode(C.Structure):
+    _fields_ = [("converged", C.c_int), ("replans", C.c_int), ("e_pos", C.c_float), ("e_ori", C.c_float),
+                ("path_length", C.c_float), ("motion_time", C.c_float), ("best_cost", C.c_float)]
+
+
 class PmServerStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "rejected", "deferred",
                                           "batches", "batched_requests")] + \
@@ -101,6 +110,8 @@ SIGNATURES = {
     "pm_submit": (C.c_int, [_V, C.POINTER(PmRequest), C.POINTER(C.c_uint64)]),
     "pm_submit_many": (C.c_int, [_V, C.POINTER(PmRequest), C.c_int, C.POINTER(C.c_uint64)]),
     "pm_fp32_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "pm_plan_episode": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, _V,
+                                  C.c_uint64, C.POINTER(PmConvergeCfg), _V, _V, C.POINTER(PmEpisode), _V, _V]),
     "pm_edt_squared": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, _V, _V]),
     "pm_robot_mask": (C.c_int, [_V, _V, _V, C.c_float, _V]),
     "pm_map_update": (C.c_int, [_V, _V, C.c_int, _V, C.c_float, _V]),

@@ -46,7 +46,8 @@ struct pm_ctx {
     size_t cap_part = 0;
 
     float *d_c0 = nullptr;              // small scratch: [0] c0, [1] best, [8, 32) replan q, qd, u0,
-                                        // [32, 40) the robot mask's configuration
+                                        // [32, 40) the robot mask's configuration,
+                                        // [48, 84) an episode's q, qd, goal and metrics
     pm::TileShape forced{0, 0, 0};          // tile shape set by pm_set_tile_shape (0 = default)
     unsigned long long *d_gathers = nullptr;  // 8-corner lookups, counted while enabled
     bool count_gathers = false;

@@ -275,6 +275,50 @@ __global__ void replan_advance_kernel(const float *q0, const float *qd0, float *
     if (threadIdx.x == 0 && best_out) *best_out = c0[1];
 }
 
+// One step of a planning episode (Sec. IV-C receding horizon, Sec. V-A
+// metrics), one block: execute u0* (advance q, qd in place), shift U, and
+// report [e_pos, e_ori, min S, sum_j |q_{t+1} - q_t|] of the new state
+// against the goal.  e_ori is the angle of R_g^T R, which equals
+// 2 arccos |q_g . q| of the unit quaternions.
+__global__ void episode_step_kernel(const RobotConst rc, const float *Tg, float *q, float *qd, float *U, int H,
+                                    float dt, const float *c0, float *metrics)
+{
+    grid_dependency_prologue();
+    __shared__ float sU[kMaxHorizon * kNJ];
+    __shared__ float s_dq[kNJ], s_q[kNJ];
+    const int n = H * kNJ;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sU[i] = U[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) U[i] = (i < n - kNJ) ? sU[i + kNJ] : sU[i];
+    if (threadIdx.x < kNJ) {
+        const int j = threadIdx.x;
+        const float qd1 = fmaf(dt, sU[j], qd[j]);
+        const float q1 = fmaf(dt, qd1, q[j]);
+        s_dq[j] = fabsf(q1 - q[j]);
+        s_q[j] = q1;
+        q[j] = q1;
+        qd[j] = qd1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Frame F = base_frame();
+        for (int j = 0; j < kNJ; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], s_q[j] + rc.th0[j]);
+        const f3 t = axpy(rc.flange_d, F.c3, F.t);
+        const f3 e = sub(t, mk(Tg[3], Tg[7], Tg[11]));
+        // R_d = R_g^T R: entries from the goal's columns and the frame's columns
+        const f3 g0 = mk(Tg[0], Tg[4], Tg[8]), g1 = mk(Tg[1], Tg[5], Tg[9]), g2 = mk(Tg[2], Tg[6], Tg[10]);
+        const float r00 = dot(g0, F.c1), r11 = dot(g1, F.c2), r22 = dot(g2, F.c3);
+        const f3 vee = mk(dot(g2, F.c2) - dot(g1, F.c3), dot(g0, F.c3) - dot(g2, F.c1),
+                          dot(g1, F.c1) - dot(g0, F.c2));
+        metrics[0] = sqrtf(dot(e, e));
+        metrics[1] = atan2f(0.5f * sqrtf(dot(vee, vee)), 0.5f * (r00 + r11 + r22 - 1.0f));
+        metrics[2] = c0[1];
+        float path = 0.f;
+        for (int j = 0; j < kNJ; ++j) path += s_dq[j];
+        metrics[3] = path;
+    }
+}
+
 // ------------------------------------------------------------ helpers
 pm_status ensure_capacity(pm_ctx *c, int K, int H, int nb)
 {
@@ -715,8 +759,8 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
 
         !ck(cudaMalloc(&c->d_gathers, sizeof(unsigned long long)), "counter alloc") ||
         !ck(cudaMemset(c->d_gathers, 0, sizeof(unsigned long long)), "counter zero") ||
-        !ck(cudaMalloc(&c->d_c0, 48 * sizeof(float)), "c0") ||
-        !ck(cudaMemset(c->d_c0, 0, 48 * sizeof(float)), "c0 zero"))
+        !ck(cudaMalloc(&c->d_c0, 96 * sizeof(float)), "c0") ||
+        !ck(cudaMemset(c->d_c0, 0, 96 * sizeof(float)), "c0 zero"))
         return fail(c->err.find("alloc") != std::string::npos ? PM_ENOMEM : PM_ECUDA);
     {
         // cell minima: 3-D array + point-sampled, clamped texture
@@ -877,6 +921,96 @@ pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *
         if (best_cost && !dbest) *best_cost = h[24];
         if (!dU) std::memcpy(U, c->h_U, sizeof(float) * H * kNJ);
     }
+    return PM_OK;
+}
+
+pm_status pm_plan_episode(pm_ctx *c, const float *q0, const float *qd0, const float *T_goal, const float *U0,
+                          int K, int H, int n_iters, float dt, float lambda, const float *sigma, uint64_t seed,
+                          const pm_converge_cfg *cfg, float *q_final, float *qd_final, pm_episode *out,
+                          float *log, void *cuda_stream)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    if (!cfg || !out) return set_err(c, PM_EINVAL, "NULL cfg or out");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    const float Uchk = 0.f;
+    pm_status st = check_call(c, q0, qd0, T_goal, U0 ? U0 : &Uchk, K, H, dt, lambda, sigma, true);
+    if (st != PM_OK) return st;
+    if (n_iters < 1 || n_iters > 1024) return set_err(c, PM_EINVAL, "n_iters=%d out of [1, 1024]", n_iters);
+    if (cfg->max_replans < 1 || cfg->n_stable < 1 || !std::isfinite(cfg->pos_tol) || !(cfg->pos_tol > 0.f) ||
+        !std::isfinite(cfg->rel_tol) || cfg->rel_tol < 0.f)
+        return set_err(c, PM_EINVAL, "bad convergence settings");
+    if (U0 && !is_device_ptr(U0) && !finite_all(U0, H * kNJ)) return set_err(c, PM_EINVAL, "U0 has a non-finite entry");
+    cudaStream_t s = pick_stream(c, cuda_stream);
+    st = ensure_capacity(c, K, H, 1);
+    if (st != PM_OK) return st;
+    // device state: q [48, 56), qd [56, 64), goal [64, 80), metrics [80, 84) of the small scratch
+    float *dq = c->d_c0 + 48, *dqd = c->d_c0 + 56, *dT = c->d_c0 + 64, *dm = c->d_c0 + 80;
+    const cudaMemcpyKind k_q = is_device_ptr(q0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind k_qd = is_device_ptr(qd0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind k_T = is_device_ptr(T_goal) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (k_q == cudaMemcpyHostToDevice && !finite_all(q0, kNJ)) return set_err(c, PM_EINVAL, "q0 not finite");
+    PM_CUDA(c, cudaMemcpyAsync(dq, q0, kNJ * sizeof(float), k_q, s));
+    PM_CUDA(c, cudaMemcpyAsync(dqd, qd0, kNJ * sizeof(float), k_qd, s));
+    PM_CUDA(c, cudaMemcpyAsync(dT, T_goal, 16 * sizeof(float), k_T, s));
+    float *Ud = c->d_U;
+    if (U0) PM_CUDA(c, cudaMemcpyAsync(Ud, U0, sizeof(float) * H * kNJ,
+                                       is_device_ptr(U0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    else PM_CUDA(c, cudaMemsetAsync(Ud, 0, sizeof(float) * H * kNJ, s));   // Algorithm 1 initialisation
+    CallInputs in{};
+    in.q0 = dq;
+    in.qd0 = dqd;
+    in.Tg = dT;
+    for (int j = 0; j < 8; ++j) in.sigma[j] = j < kNJ ? sigma[j] : 0.f;
+    pm_episode ep{};
+    float *h = c->h_out;
+    float prev_best = 0.f;
+    int stable = 0;
+    for (int t = 0; t < cfg->max_replans; ++t) {
+        for (int it = 0; it < n_iters; ++it) {
+            st = launch_iteration(c, s, in, Ud, Ud, nullptr, K, H, dt, lambda, seed,
+                                  static_cast<uint32_t>(t) * static_cast<uint32_t>(n_iters) + static_cast<uint32_t>(it),
+                                  false, nullptr);
+            if (st != PM_OK) return st;
+        }
+        PM_CUDA(c, launch_dependent(episode_step_kernel, dim3(1), dim3(256), 0, s, c->rc,
+                                    static_cast<const float *>(dT), dq, dqd, Ud, H, dt,
+                                    static_cast<const float *>(c->d_c0), dm));
+        PM_CUDA(c, cudaMemcpyAsync(h, dm, 4 * sizeof(float), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(c, cudaStreamSynchronize(s));
+        ep.replans = t + 1;
+        ep.e_pos = h[0];
+        ep.e_ori = h[1];
+        ep.best_cost = h[2];
+        ep.path_length += h[3];
+        if (log) {
+            log[4 * t] = h[0];
+            log[4 * t + 1] = h[1];
+            log[4 * t + 2] = h[2];
+            log[4 * t + 3] = ep.path_length;
+        }
+        // convergence (Sec. V-A): relative improvement of the objective below
+        // rel_tol and position error below pos_tol, n_stable replans in a row
+        const bool small_gain = t > 0 && (prev_best - h[2]) < cfg->rel_tol * std::fabs(prev_best);
+        stable = (small_gain && h[0] < cfg->pos_tol) ? stable + 1 : 0;
+        prev_best = h[2];
+        if (stable >= cfg->n_stable) {
+            ep.converged = 1;
+            break;
+        }
+    }
+    ep.motion_time = static_cast<float>(ep.replans) * dt;
+    PM_CUDA(c, cudaMemcpyAsync(h, dq, 16 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    PM_CUDA(c, cudaStreamSynchronize(s));
+    if (q_final) {
+        if (is_device_ptr(q_final)) PM_CUDA(c, cudaMemcpy(q_final, dq, kNJ * sizeof(float), cudaMemcpyDeviceToDevice));
+        else std::memcpy(q_final, h, kNJ * sizeof(float));
+    }
+    if (qd_final) {
+        if (is_device_ptr(qd_final)) PM_CUDA(c, cudaMemcpy(qd_final, dqd, kNJ * sizeof(float), cudaMemcpyDeviceToDevice));
+        else std::memcpy(qd_final, h + 8, kNJ * sizeof(float));
+    }
+    *out = ep;
     return PM_OK;
 }
 

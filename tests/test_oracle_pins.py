@@ -598,3 +598,25 @@ def test_robot_mask_single_sphere():
         inside = d2 <= (float(np.float32(0.05)) + inflate) ** 2
         assert inside.sum() > 100
         assert np.array_equal(got, np.where(inside, 0, occ))
+
+
+def test_pose_metrics_against_scipy_rotations(R):
+    """e_pos is the flange distance; e_ori = 2 arccos|q_g . q| equals the
+    magnitude of the relative rotation R_g^T R (scipy), including near pi."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(8)
+    for t in range(20):
+        q = rng.uniform(-2.0, 2.0, 7)
+        T = oracle.fk(R, q)[-1]
+        if t < 10:
+            rot = Rotation.from_rotvec(rng.normal(size=3) * (0.3 + 0.3 * t))
+        else:   # near pi
+            ax = rng.normal(size=3)
+            rot = Rotation.from_rotvec(ax / np.linalg.norm(ax) * (np.pi - 10.0 ** -(t - 8)))
+        Tg = np.eye(4)
+        Tg[:3, :3] = T[:3, :3] @ rot.as_matrix()
+        Tg[:3, 3] = T[:3, 3] + rng.normal(size=3) * 0.05
+        e_pos, e_ori = oracle.pose_metrics(R, q, Tg)
+        assert math.isclose(e_pos, np.linalg.norm(Tg[:3, 3] - T[:3, 3]), rel_tol=1e-12)
+        ref = Rotation.from_matrix(Tg[:3, :3].T @ T[:3, :3]).magnitude()
+        assert abs(e_ori - ref) <= 2e-7, (t, e_ori, ref)
