@@ -8,9 +8,9 @@
 // y, then x, then z, on the native [z][y][x] layout.  Each thread owns one
 // line: it gathers the line (stride 1, nx or nx*ny) into its own column of
 // shared memory, builds the envelope there and writes the line back -- no
-// transposition of the grid.  Envelope boundaries are kept as exact
-// fractions (numerator, denominator) and compared by 64-bit cross
-// multiplication, so the result is the exact integer squared distance.
+// transposition of the grid.  Envelope boundaries are exact fractions of
+// integers, compared by 64-bit cross multiplication, so the result is the
+// exact integer squared distance.
 #include "ctx_internal.h"
 
 #include <algorithm>
@@ -31,7 +31,10 @@ struct EdtPass {
     long long sa, sb, se;
 };
 
-// Per-thread shared-memory column of element i: buf[i * T + t].
+// Per-thread shared-memory columns of element i: f[i * T + t] (the line's
+// values) and v[i * T + t] (the envelope's sites).  The envelope's
+// boundaries are recomputed from neighbouring sites when needed, so a line
+// costs 6 bytes of shared memory per element.
 template <bool FROM_OCC>
 __global__ void edt_pass_kernel(const void *in, int *out, EdtPass ps)
 {
@@ -40,14 +43,13 @@ __global__ void edt_pass_kernel(const void *in, int *out, EdtPass ps)
     const int line = blockIdx.x * T + t;
     if (line >= ps.n_lines) return;
     const int n = ps.n;
-    int *f = s_edt;                                  // [n][T] input values
-    int *zn = s_edt + n * T;                         // [n][T] boundary numerators
-    short *v = reinterpret_cast<short *>(s_edt + 2 * n * T);    // [n][T] sites
-    unsigned short *zd = reinterpret_cast<unsigned short *>(v + n * T);   // [n][T] boundary denominators
+    int *f = s_edt;                                               // [n][T] input values
+    short *v = reinterpret_cast<short *>(s_edt + n * T);          // [n][T] sites
     const long long a = line % ps.na, b = line / ps.na;
     const long long base = a * ps.sa + b * ps.sb;
 
-    // gather the line into this thread's column
+    // gather the line into this thread's column (8 loads in flight)
+#pragma unroll 8
     for (int i = 0; i < n; ++i) {
         const long long idx = base + i * ps.se;
         int x;
@@ -55,52 +57,71 @@ __global__ void edt_pass_kernel(const void *in, int *out, EdtPass ps)
         else x = static_cast<const int *>(in)[idx];
         f[i * T + t] = x;
     }
-    // lower envelope of the parabolas y = (x - q)^2 + f[q] over the sites
-    int k = -1;
+    // Lower envelope of the parabolas y = (x - q)^2 + f[q] over the sites.
+    // Parabolas u < w meet at s(u, w) = (h_w - h_u) / (2 (w - u)), h = f + q^2;
+    // site v[k] covers [s(v[k-1], v[k]), s(v[k], v[k+1])).  The top two sites
+    // stay in registers (vt, ht) and (vp, hp).
+    int k = -1, vt = 0, vp = 0;
+    long long ht = 0, hp = 0;
     for (int q = 0; q < n; ++q) {
         const int fq = f[q * T + t];
         if (fq == kEdtInf) continue;
         const long long hq = fq + static_cast<long long>(q) * q;
-        while (k >= 1) {
-            // the new parabola meets v[k]'s at s = (hq - h_v) / (2 (q - v));
-            // v[k] leaves the envelope when s <= its left boundary zn/zd
-            const int vk = v[k * T + t];
-            const long long num = hq - (f[vk * T + t] + static_cast<long long>(vk) * vk);
-            const long long den = 2LL * (q - vk);
-            if (num * zd[k * T + t] > static_cast<long long>(zn[k * T + t]) * den) break;
+        // pop v[k] while s(v[k], q) <= s(v[k-1], v[k]), i.e.
+        // (hq - ht) * 2 (vt - vp) <= (ht - hp) * 2 (q - vt)
+        while (k >= 1 && (hq - ht) * (vt - vp) <= (ht - hp) * (q - vt)) {
             --k;
+            vt = vp;
+            ht = hp;
+            if (k >= 1) {
+                vp = v[(k - 1) * T + t];
+                hp = f[vp * T + t] + static_cast<long long>(vp) * vp;
+            }
         }
         ++k;
         v[k * T + t] = static_cast<short>(q);
-        if (k > 0) {
-            const int vp = v[(k - 1) * T + t];
-            zn[k * T + t] = static_cast<int>(hq - (f[vp * T + t] + static_cast<long long>(vp) * vp));
-            zd[k * T + t] = static_cast<unsigned short>(2 * (q - vp));
-        }
+        vp = vt;
+        hp = ht;
+        vt = q;
+        ht = hq;
     }
-    // evaluate the envelope at every element
+    // evaluate the envelope at every element, advancing while the next
+    // site's left boundary s(v[j], v[j+1]) lies below q
     int j = 0;
+    int vj = k >= 0 ? v[t] : 0, vn = 0;
+    long long hj = k >= 0 ? f[vj * T + t] + static_cast<long long>(vj) * vj : 0, hn = 0;
+    if (k >= 1) {
+        vn = v[T + t];
+        hn = f[vn * T + t] + static_cast<long long>(vn) * vn;
+    }
     for (int q = 0; q < n; ++q) {
         int d = kEdtInf;
         if (k >= 0) {
-            while (j < k && static_cast<long long>(zn[(j + 1) * T + t]) < static_cast<long long>(q) * zd[(j + 1) * T + t])
+            while (j < k && hn - hj < 2LL * q * (vn - vj)) {   // s(vj, vn) < q
                 ++j;
-            const int vj = v[j * T + t];
-            d = f[vj * T + t] + (q - vj) * (q - vj);
+                vj = vn;
+                hj = hn;
+                if (j < k) {
+                    vn = v[(j + 1) * T + t];
+                    hn = f[vn * T + t] + static_cast<long long>(vn) * vn;
+                }
+            }
+            d = static_cast<int>(hj - static_cast<long long>(vj) * vj) + (q - vj) * (q - vj);
         }
         out[base + q * ps.se] = d;
     }
 }
 
-// Shared memory per thread of a pass over lines of n elements.
-size_t edt_bytes_per_thread(int n) { return static_cast<size_t>(n) * (4 + 4 + 2 + 2); }
+// Shared memory per thread of a pass over lines of n elements (f, v and
+// alignment slack).
+size_t edt_bytes_per_thread(int n) { return static_cast<size_t>(n) * (4 + 2) + 4; }
 
-// Threads per block: as many lines as fit 96 KiB of shared memory, a
-// multiple of 32 when possible.
+// Threads per block: as many lines as fit 112 KiB of shared memory (two
+// blocks per SM), a multiple of 32 when possible.
 int edt_threads(int n)
 {
     const size_t per = edt_bytes_per_thread(n);
-    int T = static_cast<int>(std::min<size_t>(128, (96u << 10) / per));
+    int T = static_cast<int>(std::min<size_t>(256, (112u << 10) / per));
     if (T >= 32) T -= T % 32;
     return std::max(T, 1);
 }
