@@ -78,6 +78,7 @@ def lib():
         L.or_replan.restype = C.c_int
         L.or_edt_bruteforce.argtypes = [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int,
                                         C.POINTER(C.c_int64)]
+        L.or_eps_range.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, C.c_int, _PD, _PD]
         L.or_pose_metrics.argtypes = [C.POINTER(OrRobot), _PD, _PD, _PD]
         L.or_robot_mask.argtypes = [C.POINTER(OrRobot), _PD, C.c_int, C.c_int, C.c_int, C.c_double,
                                     _PD, C.c_double, C.POINTER(C.c_uint8)]
@@ -171,6 +172,14 @@ def normals(seed, it, m, k):
     z = np.empty(8)
     lib().or_normals(int(seed), int(it), int(m), int(k), _dp(z))
     return z
+
+
+def eps_range(seed, it, m0, count, H, sigma, n=7):
+    """eps of roll-outs m0 .. m0+count-1: array (count, H, n), as eps_tensor."""
+    sig = _f64(sigma)
+    out = np.empty((int(count), int(H), n))
+    lib().or_eps_range(int(seed), int(it), int(m0), int(count), int(H), n, _dp(sig), _dp(out))
+    return out
 
 
 def eps_tensor(seed, it, K, H, sigma, n=7):

@@ -604,3 +604,20 @@ void or_pose_metrics(const or_robot *rb, const double *q, const double *Tg, doub
     out[1] = 2.0 * acos(d > 1.0 ? 1.0 : d);
 }
 
+/* eps[i][k][j] = sigma_j z_j(m0 + i, k) for i < count, k < H, j < n (the
+ * sampling step of Algorithm 1 over a range of roll-outs; OpenMP). */
+void or_eps_range(uint64_t seed, uint32_t iter, uint32_t m0, int count, int H, int n, const double *sigma,
+                  double *eps)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int i = 0; i < count; ++i) {
+        double z[8];
+        for (int k = 0; k < H; ++k) {
+            or_normals(seed, iter, m0 + (uint32_t)i, (uint32_t)k, z);
+            for (int j = 0; j < n; ++j) eps[((size_t)i * H + k) * n + j] = sigma[j] * z[j];
+        }
+    }
+}
+

@@ -86,6 +86,8 @@ int    or_replan(const or_robot *rb, const or_grid *g, const or_cost *c,
                  uint64_t seed, uint32_t replan_index, int n_iters,
                  double *u0_out, double *best_cost, int n_threads);
 void   or_edt_bruteforce(const uint8_t *occ, int nx, int ny, int nz, int64_t *D);
+void   or_eps_range(uint64_t seed, uint32_t iter, uint32_t m0, int count, int H, int n, const double *sigma,
+                    double *eps);
 void   or_pose_metrics(const or_robot *rb, const double *q, const double *Tg, double out[2]);
 void   or_robot_mask(const or_robot *rb, const double *q, int nx, int ny, int nz, double res,
                      const double *origin, double inflate, uint8_t *occ);

@@ -326,6 +326,34 @@ def test_cfg2_full_size_iteration(cfg2):
     assert np.abs(Ug - Uo).max() <= U_ABS
 
 
+def test_large_K_sampled_rollouts_and_isolated_update(cfg2):
+    """K = 2^18 roll-outs at H = 64 on the full-size grid (the launch runs
+    several tiles per warp): 48 sampled roll-outs' costs against the oracle
+    one by one, and U* against the FP64 update recomputed from the GPU's own
+    costs and the oracle's noise (the reduction over 262144 roll-outs)."""
+    K, H, seed, it = 1 << 18, 64, 4242, 5
+    rng = np.random.default_rng(11)
+    U = (rng.normal(size=(H, 7)) * 0.2).astype(np.float32)
+    p = cfg2.planner()
+    Ug = U.copy()
+    Sg = np.empty(K, np.float32)
+    p.smpc_iterate(cfg2.q0, cfg2.qd0, cfg2.T, Ug, K, 0.02, 0.05, SIGMA, seed, it, costs_out=Sg)
+    p.close()
+    picks = np.unique(np.concatenate([[0, 1, 31, 32, K // 2, K - 2, K - 1], rng.integers(0, K, 41)]))
+    for m in picks:
+        eps = oracle.eps_range(seed, it, int(m), 1, H, SIGMA)[0]
+        So = oracle.rollout_cost(cfg2.R, cfg2.G, cfg2.C, cfg2.q0, cfg2.qd0, cfg2.T, U + eps, 0.02)
+        assert abs(Sg[m] - So) <= S_REL * abs(So), (m, Sg[m], So)
+    S = Sg.astype(np.float64)
+    w = np.exp(-(S - S.min()) / 0.05)
+    acc = np.zeros((H, 7))
+    for m0 in range(0, K, 1 << 14):
+        e = oracle.eps_range(seed, it, m0, 1 << 14, H, SIGMA)
+        acc += np.einsum("m,mkj->kj", w[m0:m0 + (1 << 14)], e)
+    Uiso = U.astype(np.float64) + acc / w.sum()
+    assert np.abs(Ug - Uiso).max() <= U_ISO
+
+
 def test_cfg2_one_replan(cfg2):
     """pm_replan (8 iterations + execute + shift) against the oracle's replan."""
     K, H, iters = cfg2.sc["K"], cfg2.sc["H"], cfg2.sc["iters"]

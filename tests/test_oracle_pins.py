@@ -620,3 +620,9 @@ def test_pose_metrics_against_scipy_rotations(R):
         assert math.isclose(e_pos, np.linalg.norm(Tg[:3, 3] - T[:3, 3]), rel_tol=1e-12)
         ref = Rotation.from_matrix(Tg[:3, :3].T @ T[:3, :3]).magnitude()
         assert abs(e_ori - ref) <= 2e-7, (t, e_ori, ref)
+
+
+def test_eps_range_equals_eps_tensor():
+    sig = np.array([0.5, 0.1, 1.0, 2.0, 0.25, 0.75, 1.5])
+    full = oracle.eps_tensor(99, 4, 12, 9, sig)
+    assert np.array_equal(oracle.eps_range(99, 4, 5, 6, 9, sig), full[5:11])
