@@ -278,7 +278,8 @@ SERVE_RATES = (500, 1000, 2000, 3000, 4000, 6000)
 
 def bench_self_collision(pm, torch, dev, stream, w, Ts, n_replans=100, min_link_gap=2):
     """The replanning workload with the self-collision term on (Eqs. 18-20):
-    sphere pairs on frames at least two apart (240 pairs), w_self = 1.
+    sphere pairs on frames at least min_link_gap apart (2: 240 pairs, the
+    wrist's always in contact; 3: 160 pairs), w_self = 1.
     Replans timed with events per replan, then the iteration kernel alone."""
     import workloads
     sc = w["scene"]
@@ -779,6 +780,7 @@ def run_ours(args, rank, world, local):
     line["precision_variants"] = variants
     line["latency_cfg1"] = bench_latency_cfg1(pm, torch, dev, stream)
     line["self_collision"] = bench_self_collision(pm, torch, dev, stream, w, Ts)
+    line["self_collision_gap3"] = bench_self_collision(pm, torch, dev, stream, w, Ts, min_link_gap=3)
     line["episodes"] = bench_episodes(pm, torch, dev, stream)
     line["mapping"] = bench_mapping(pm, torch, dev, stream, w)
     if not args.no_batched:

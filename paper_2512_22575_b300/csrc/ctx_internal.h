@@ -15,8 +15,7 @@ struct pm_ctx {
     pm::RobotConst *d_rc = nullptr;     // device copy (read by the batched kernels)
     unsigned char *d_map_occ = nullptr; // mapping scratch: occupancy copy, two int32 EDT buffers
     int *d_map_a = nullptr, *d_map_b = nullptr;
-    unsigned *d_self_pairs = nullptr;   // self-collision pairs, grouped (rc.self_pairs)
-    float *d_self_rsum = nullptr;       // their radius sums (rc.self_rsum)
+    float4 *d_self_pairs = nullptr;     // self-collision pairs, grouped (rc.self_pairs)
     pm_grid_desc gd{};
     size_t grid_elems = 0;
     void *d_grid = nullptr;

@@ -681,8 +681,7 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     r.flange_d = rb->flange_d;
     // self-collision set: pairs in internal sphere order, grouped by their
     // frames (fa <= fb); each frame's bounding sphere around its spheres
-    std::vector<unsigned> self_pairs;
-    std::vector<float> self_rsum;
+    std::vector<float4> self_pairs;
     if (cp->w_self > 0.f && rb->n_self_pairs > 0) {
         std::vector<int> inv(rb->n_spheres);
         for (int i = 0; i < rb->n_spheres; ++i) inv[order[i]] = i;
@@ -707,8 +706,11 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
             if (fa > fb) { std::swap(a, b); std::swap(fa, fb); }
             ps.push_back(P{fa, fb, a, b});
         }
-        std::stable_sort(ps.begin(), ps.end(),
-                         [](const P &x, const P &y) { return x.fa != y.fa ? x.fa < y.fa : x.fb < y.fb; });
+        std::stable_sort(ps.begin(), ps.end(), [](const P &x, const P &y) {
+            if (x.fa != y.fa) return x.fa < y.fa;
+            if (x.fb != y.fb) return x.fb < y.fb;
+            return x.a != y.a ? x.a < y.a : x.b < y.b;
+        });
         int g = -1;
         for (size_t i = 0; i < ps.size(); ++i) {
             if (g < 0 || ps[i].fa != r.grp_fa[g] || ps[i].fb != r.grp_fb[g]) {
@@ -721,8 +723,14 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
                 const double thr = R + 1e-4 + 1e-5 * R;
                 r.grp_thr2[g] = std::nextafter(static_cast<float>(thr * thr), INFINITY);
             }
-            self_pairs.push_back(static_cast<unsigned>(ps[i].a) | (static_cast<unsigned>(ps[i].b) << 8));
-            self_rsum.push_back(r.sph_r[ps[i].a] + r.sph_r[ps[i].b]);
+            const unsigned ab = static_cast<unsigned>(ps[i].a) | (static_cast<unsigned>(ps[i].b) << 8);
+            const float rs = r.sph_r[ps[i].a] + r.sph_r[ps[i].b];
+            // apart beyond (r_a + r_b + 1e-5 m)^2, rounded up: sqrt of any larger
+            // FP32 squared distance exceeds r_a + r_b
+            const double t = static_cast<double>(rs) + 1e-5;
+            float bits;
+            std::memcpy(&bits, &ab, sizeof(bits));
+            self_pairs.push_back(make_float4(bits, rs, std::nextafter(static_cast<float>(t * t), INFINITY), 0.f));
         }
         r.n_self_groups = g + 1;
         r.grp_begin[g + 1] = static_cast<unsigned short>(ps.size());
@@ -783,16 +791,12 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         if (!ck(cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming), "event"))
             return fail(PM_ECUDA);
     if (!self_pairs.empty()) {
-        if (!ck(cudaMalloc(&c->d_self_pairs, self_pairs.size() * sizeof(unsigned)), "self pairs alloc") ||
-            !ck(cudaMalloc(&c->d_self_rsum, self_rsum.size() * sizeof(float)), "self radii alloc"))
+        if (!ck(cudaMalloc(&c->d_self_pairs, self_pairs.size() * sizeof(float4)), "self pairs alloc"))
             return fail(PM_ENOMEM);
-        if (!ck(cudaMemcpy(c->d_self_pairs, self_pairs.data(), self_pairs.size() * sizeof(unsigned),
-                           cudaMemcpyHostToDevice), "self pairs copy") ||
-            !ck(cudaMemcpy(c->d_self_rsum, self_rsum.data(), self_rsum.size() * sizeof(float),
-                           cudaMemcpyHostToDevice), "self radii copy"))
+        if (!ck(cudaMemcpy(c->d_self_pairs, self_pairs.data(), self_pairs.size() * sizeof(float4),
+                           cudaMemcpyHostToDevice), "self pairs copy"))
             return fail(PM_ECUDA);
         c->rc.self_pairs = c->d_self_pairs;
-        c->rc.self_rsum = c->d_self_rsum;
     }
     if (!ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy"))
         return fail(PM_ECUDA);
@@ -1192,7 +1196,6 @@ void pm_destroy(pm_ctx *c)
         cudaFree(c->d_map_a);
         cudaFree(c->d_map_b);
         cudaFree(c->d_self_pairs);
-        cudaFree(c->d_self_rsum);
         cudaFree(c->d_cmin);
         if (c->cmin_tex) cudaDestroyTextureObject(c->cmin_tex);
         if (c->cmin_arr) cudaFreeArray(c->cmin_arr);

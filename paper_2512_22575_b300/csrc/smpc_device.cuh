@@ -56,8 +56,10 @@ struct RobotConst {
     unsigned short grp_begin[kMaxSelfGroups + 1];                    // pairs of group g
     float grp_thr2[kMaxSelfGroups];
     float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
-    const unsigned *self_pairs;   // device [n]: internal sphere a | b << 8, grouped
-    const float *self_rsum;       // device [n]: r_a + r_b
+    // device [n], grouped and ordered by (a, b) within a group: x = bits of
+    // the internal sphere indices a | b << 8, y = r_a + r_b, z = a squared
+    // distance above which the pair is apart (its violation is exactly 0)
+    const float4 *self_pairs;
 };
 
 // Per-lane shared-memory slots of the self-collision term: the world

@@ -140,15 +140,26 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
         const float gy = sp[(fa + 1) * 32] - sp[(fb + 1) * 32];
         const float gz = sp[(fa + 2) * 32] - sp[(fb + 2) * 32];
         if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > rc.grp_thr2[gi]) continue;   // exact zero
+        int a_prev = -1;
+        float ax = 0.f, ay = 0.f, az = 0.f;
         for (int p = rc.grp_begin[gi]; p < rc.grp_begin[gi + 1]; ++p) {
-            const unsigned ab = __ldg(rc.self_pairs + p);
+            const float4 pr = __ldg(rc.self_pairs + p);
+            const unsigned ab = __float_as_uint(pr.x);
             const int a = 3 * static_cast<int>(ab & 0xffu), b = 3 * static_cast<int>(ab >> 8);
-            const float ex = sp[a * 32] - sp[b * 32];
-            const float ey = sp[(a + 1) * 32] - sp[(b + 1) * 32];
-            const float ez = sp[(a + 2) * 32] - sp[(b + 2) * 32];
-            const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) - __ldg(rc.self_rsum + p);
-            const float del = fmaxf(-d, 0.f);
-            acc = fmaf(del, del, acc);
+            if (a != a_prev) {          // pairs run by a: its centre is reused
+                ax = sp[a * 32];
+                ay = sp[(a + 1) * 32];
+                az = sp[(a + 2) * 32];
+                a_prev = a;
+            }
+            const float ex = ax - sp[b * 32];
+            const float ey = ay - sp[(b + 1) * 32];
+            const float ez = az - sp[(b + 2) * 32];
+            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (d2 <= pr.z) {           // otherwise |c_a - c_b| > r_a + r_b: exactly 0
+                const float del = fmaxf(pr.y - sqrtf(d2), 0.f);
+                acc = fmaf(del, del, acc);
+            }
         }
     }
     return rc.w_self * acc;
