@@ -53,6 +53,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over the ranks (all_reduce MAX; NCCL wants a CUDA
+    device, gloo the CPU); x itself for one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, max_seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank runs the same workload)."""
+    return units_per_rank * world / max_seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
@@ -673,13 +691,8 @@ def run_ours(args, rank, world, local):
     gathers_per_launch = planner.profile_gathers(reset=True) / (n_count * iters)
     planner.profile_enable(0)
     step_ms = np.array([s.elapsed_time(e) for s, e in ev])
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = K * H * iters * args.steps * world
-    value = units / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(step_ms.sum()), world, dev)
+    value = whole_job_value(K * H * iters * args.steps, world, total_ms / 1e3)
 
     # end to end through the C ABI with host buffers (copies inside the region)
     n_e2e = min(args.steps, args.e2e_steps)
@@ -700,12 +713,8 @@ def run_ours(args, rank, world, local):
             qh[:] = sc["q0"]; qdh[:] = sc["qd0"]; Uh[:] = 0
         planner.replan(qh, qdh, Ts_host[r], Uh, K, iters, dt, lam, sigma, seed, r,
                        u0_out=u0h, best_cost=besth)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = K * H * iters * n_e2e * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = whole_job_value(K * H * iters * n_e2e, world, e2e_s)
     state_bytes = 36 * 4                    # q0, qd0, R_g, t_g, sigma as staged
     h2d = state_bytes + H * 7 * 4           # + U
     d2h = 25 * 4 + H * 7 * 4                # q, qd, u0, best + U
@@ -740,7 +749,8 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": n_e2e,
                 "ms_per_step": 1e3 * e2e_s / n_e2e},
-        "gpu_launches": args.steps * (iters + 1),
+        # per replan: n_iters x (iteration kernel + merge) + the replan step
+        "gpu_launches": args.steps * (2 * iters + 1),
         "roofline": roofline,
         "clocks": clk,
     }
