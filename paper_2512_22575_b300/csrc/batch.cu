@@ -48,7 +48,7 @@ struct BatchArgs {
     uint32_t it;              // iteration offset added to every instance's iter
 };
 
-template <typename GT>
+template <typename GT, bool SELF>
 __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_constant__ BatchArgs ba)
 {
     extern __shared__ float s_dyn[];
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
         job.c0 = s_inst.c0;
         const int C = s_inst.C;
         BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
-                     s_rc.n_self_groups > 0 ? s_dyn + 2 * kWarps * kBatchCMax * kNJ * 32 : nullptr};
+                     (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kBatchCMax * kNJ * 32 : nullptr};
         unsigned ngath = 0;
-        run_block<GT, false>(s_rc, s_inst.g, st, job, nullptr, C, s_inst.L, s_inst.P, w.y, sm, ngath);
+        run_block<GT, false, SELF>(s_rc, s_inst.g, st, job, nullptr, C, s_inst.L, s_inst.P, w.y, sm, ngath);
     }
 }
 
@@ -407,7 +407,8 @@ pm_status enqueue_batch(pm_batch *b, int n, int n_work, int n_rows, int n_iters,
     const int grid = std::max(1, std::min(n_work, b->n_sm * b->bps_call));
     for (int itn = 0; itn < n_iters; ++itn) {
         BatchArgs a{b->d_inst, b->d_work, n_work, b->d_queue + itn, static_cast<uint32_t>(itn)};
-        smpc_batch_kernel<float><<<grid, kBlock, b->smem_call, s>>>(a);
+        if (b->smem_call > batch_smem()) smpc_batch_kernel<float, true><<<grid, kBlock, b->smem_call, s>>>(a);
+        else smpc_batch_kernel<float, false><<<grid, kBlock, b->smem_call, s>>>(a);
         PM_BCUDA(b, cudaGetLastError());
         batch_merge_kernel<<<n_rows, 32 * kBatchMergeWarps, 0, s>>>(b->d_inst, b->d_rows);
         PM_BCUDA(b, cudaGetLastError());
@@ -524,8 +525,8 @@ pm_status pm_batch_create(int device, pm_batch **out)
         cudaGetLastError();
         return fail(PM_ECUDA);
     }
-    b->blocks_per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float>), kBlock,
-                                              batch_smem());
+    b->blocks_per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float, false>),
+                                              kBlock, batch_smem());
     if (b->blocks_per_sm < 1) return fail(PM_ECUDA);
     b->bps_call = b->blocks_per_sm;
     b->smem_call = batch_smem();
@@ -551,8 +552,10 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
         b->pending = false;
     }
     b->smem_call = call_smem(items, n);
-    b->bps_call = resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float>), kBlock,
-                                         b->smem_call);
+    b->bps_call = b->smem_call > batch_smem()
+                      ? resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float, true>), kBlock,
+                                               b->smem_call)
+                      : b->blocks_per_sm;
     if (b->bps_call < 1) return berr(b, PM_ECUDA, "cannot give the batch kernel %zu bytes of shared memory", b->smem_call);
     const std::string key = structure_key(items, n, n_iters, flags);
     auto pit = b->plans.find(key);

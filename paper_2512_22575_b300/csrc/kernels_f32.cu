@@ -1,4 +1,4 @@
 // SMPC iteration kernels with a float distance field (see smpc_kernels.cuh).
 #include "smpc_dispatch.h"
 
-PM_INSTANTIATE_ITERATION_TABLE(iteration_kernel_f32, float, true)
+PM_INSTANTIATE_ITERATION_TABLE(iteration_kernel_f32, float, true, false)

@@ -63,12 +63,12 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-IterKernel lookup_kernel(int dtype, TileShape s, bool trace)
+IterKernel lookup_kernel(int dtype, TileShape s, bool trace, bool self)
 {
     switch (dtype) {
-    case PM_F32: return iteration_kernel_f32(s.C, s.L, s.P, trace);
-    case PM_F16: return iteration_kernel_f16(s.C, s.L, s.P, trace);
-    case PM_BF16: return iteration_kernel_bf16(s.C, s.L, s.P, trace);
+    case PM_F32: return (self ? iteration_kernel_f32_self : iteration_kernel_f32)(s.C, s.L, s.P, trace);
+    case PM_F16: return (self ? iteration_kernel_f16_self : iteration_kernel_f16)(s.C, s.L, s.P, trace);
+    case PM_BF16: return (self ? iteration_kernel_bf16_self : iteration_kernel_bf16)(s.C, s.L, s.P, trace);
     default: return nullptr;
     }
 }
@@ -471,7 +471,7 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
     TileShape sh;
     pm_status pst = pick_shape(c, H, sh);
     if (pst != PM_OK) return pst;
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace);
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace, c->rc.n_self_groups > 0);
     if (!fn) return set_err(c, trace ? PM_EINVAL : PM_EINTERNAL, "no %s kernel for C=%d L=%d P=%d",
                             trace ? "trace" : "iteration", sh.C, sh.L, sh.P);
     const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
@@ -550,7 +550,7 @@ pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &i
     TileShape sh;
     pm_status st = pick_shape(c, H, sh);
     if (st != PM_OK) return st;
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false, c->rc.n_self_groups > 0);
     if (!fn) return set_err(c, PM_EINTERNAL, "no iteration kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
     const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
     const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
@@ -1277,7 +1277,7 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
     TileShape sh;
     st = pick_shape(c, H, sh);
     if (st != PM_OK) return st;
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false);
+    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false, c->rc.n_self_groups > 0);
     if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
     const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
     const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);

@@ -29,32 +29,36 @@ inline TileShape default_shape(int H)
     return {4, 32, 2};
 }
 
-// Kernel for a tile shape and storage type (nullptr if not instantiated;
-// trace kernels exist for the float field only).
+// Kernel for a tile shape and storage type, without or with the
+// self-collision term (nullptr if not instantiated; trace kernels exist for
+// the float field only).
 IterKernel iteration_kernel_f32(int C, int L, int P, bool trace);
 IterKernel iteration_kernel_f16(int C, int L, int P, bool trace);
 IterKernel iteration_kernel_bf16(int C, int L, int P, bool trace);
+IterKernel iteration_kernel_f32_self(int C, int L, int P, bool trace);
+IterKernel iteration_kernel_f16_self(int C, int L, int P, bool trace);
+IterKernel iteration_kernel_bf16_self(int C, int L, int P, bool trace);
 
 } // namespace pm
 
-#define PM_KERNEL_CASE(C_, L_, P_, GT, WITH_TRACE)                                          \
+#define PM_KERNEL_CASE(C_, L_, P_, GT, WITH_TRACE, SELF)                                    \
     if (C == C_ && L == L_ && P == P_)                                                   \
-        return trace ? (WITH_TRACE ? smpc_iteration_kernel<C_, L_, P_, GT, WITH_TRACE> : nullptr) \
-                     : smpc_iteration_kernel<C_, L_, P_, GT, false>;
+        return trace ? (WITH_TRACE ? smpc_iteration_kernel<C_, L_, P_, GT, WITH_TRACE, SELF> : nullptr) \
+                     : smpc_iteration_kernel<C_, L_, P_, GT, false, SELF>;
 
-#define PM_INSTANTIATE_ITERATION_TABLE(NAME, GT, WITH_TRACE)                               \
+#define PM_INSTANTIATE_ITERATION_TABLE(NAME, GT, WITH_TRACE, SELF)                         \
     namespace pm {                                                                     \
     IterKernel NAME(int C, int L, int P, bool trace)                                   \
     {                                                                                  \
-        PM_KERNEL_CASE(1, 16, 1, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(1, 32, 1, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(3, 16, 1, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(2, 32, 1, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(4, 32, 1, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(8, 32, 1, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(1, 32, 2, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(2, 32, 2, GT, WITH_TRACE)                                       \
-        PM_KERNEL_CASE(4, 32, 2, GT, WITH_TRACE)                                       \
+        PM_KERNEL_CASE(1, 16, 1, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(1, 32, 1, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(3, 16, 1, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(2, 32, 1, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(4, 32, 1, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(8, 32, 1, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(1, 32, 2, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(2, 32, 2, GT, WITH_TRACE, SELF)                                     \
+        PM_KERNEL_CASE(4, 32, 2, GT, WITH_TRACE, SELF)                                     \
         return nullptr;                                                                \
     }                                                                                  \
     }

@@ -90,7 +90,7 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 // together through the texture unit; a sphere whose minimum is above its
 // skip threshold contributes exactly 0 and needs no gathers, the others are
 // located exactly and interpolated from their 8 corners.
-template <typename GT>
+template <typename GT, bool SELF>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
                                           const Frame &F, int b, int e, unsigned &ngath, float *sp)
 {
@@ -101,7 +101,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
             const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-            if (sp) {                           // kept for the self-collision term
+            if (SELF && sp) {                   // kept for the self-collision term
                 sp[(3 * s) * 32] = p.x;
                 sp[(3 * s + 1) * 32] = p.y;
                 sp[(3 * s + 2) * 32] = p.z;
@@ -168,13 +168,13 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
 // State terms at a step (Eqs. 16, 19-20, 22, 24), or the terminal cost (Eq. 25).
 // Forward kinematics runs frame by frame; the spheres of each frame are
 // looked up as soon as it is known.
-template <typename GT, bool TRACE>
+template <typename GT, bool TRACE, bool SELF>
 __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
                                             const InstanceState &st, const float *q,
                                             const float *qd, bool terminal, float *tr,
                                             unsigned &ngath, float *sp)
 {
-    if (terminal) sp = nullptr;
+    if (!SELF || terminal) sp = nullptr;
     float lq = 0.f, lqd = 0.f, ns = 0.f;
     if (!terminal) {
 #pragma unroll
@@ -200,8 +200,8 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], qr[0] + rc.th0[j]);
 #pragma unroll
         for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
-        if (!terminal) env += link_env<GT>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
-        if (sp) {
+        if (!terminal) env += link_env<GT, SELF>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
+        if (SELF && sp) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
             const int t = 3 * rc.n_spheres + 3 * j;
             sp[t * 32] = c.x;
@@ -222,7 +222,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     lq *= rc.w_q;
     lqd *= rc.w_qd;
     ns *= rc.w_ns;
-    const float self = sp ? self_cost(rc, sp) : 0.f;
+    const float self = (SELF && sp) ? self_cost(rc, sp) : 0.f;
     if (TRACE) { tr[0] = pose; tr[1] = env; tr[2] = self; tr[3] = lq; tr[4] = lqd; tr[7] = ns; }
     return pose + env + self + lq + lqd + ns;
 }
@@ -286,7 +286,7 @@ struct BlockSmem {
 // block partial (m_b, z_b, acc_b) into job.part.  Tile shape (C, L, P) as
 // described at the top of this file; called by every thread of the block.
 // With constant arguments (the single-instance kernel) the shape folds away.
-template <typename GT, bool TRACE>
+template <typename GT, bool TRACE, bool SELF>
 __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst &g,
                                           const InstanceState &st, const TileJob &job,
                                           float *trace, const int C, const int L, const int P,
@@ -305,8 +305,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 
     float run_m = CUDART_INF_F, run_z = 0.f;
     const float dt = job.dt, dt2 = job.dt * job.dt;
-    float *sp = (rc.n_self_groups > 0 && sm.self) ? sm.self + warp * self_slots(rc.n_spheres) * 32 + lane
-                                                  : nullptr;
+    float *sp = (SELF && rc.n_self_groups > 0 && sm.self)
+                    ? sm.self + warp * self_slots(rc.n_spheres) * 32 + lane : nullptr;
     const int half = (P == 2) ? (warp & 1) : 0;
     const int pr = warp >> 1;
     const int kbase = half * 32 * C;
@@ -413,7 +413,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 tr_x = tr_u + kTraceCols;
             }
             const unsigned ng0 = ngath;
-            const float sc = state_cost<GT, TRACE>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp);
+            const float sc = state_cost<GT, TRACE, SELF>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp);
             if (extra) {
                 ngath = ng0;        // lookups of the roll-outs only
                 *job.c0 = sc;
@@ -514,11 +514,13 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 }
 
 // ------------------------------------------------------------------ kernel
-// P = 1: a warp tile holds R = 32/L roll-outs of up to C*L steps.
+// P = 1: a warp tile holds R = 32/L roll-outs of up to C*L steps.  SELF
+// compiles the self-collision term in (kernels without it carry none of
+// its code).
 // P = 2 (L = 32): two warps of a block share one roll-out, warp 2p taking
 // steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
 // totals of the first half and their partial costs through shared memory.
-template <int C, int L, int P, typename GT, bool TRACE>
+template <int C, int L, int P, typename GT, bool TRACE, bool SELF>
 __global__ void __launch_bounds__(kBlock, 5)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
                       const __grid_constant__ IterArgs a)
@@ -552,9 +554,9 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     job.inv_lambda = a.inv_lambda;
     job.noise_dtype = a.noise_dtype;
     BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
-                 rc.n_self_groups > 0 ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr};
+                 (SELF && rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr};
     unsigned ngath = 0;
-    run_block<GT, TRACE>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
+    run_block<GT, TRACE, SELF>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
     if (!TRACE && a.gathers) {
         const int lane = threadIdx.x & 31;
         unsigned n = ngath;
