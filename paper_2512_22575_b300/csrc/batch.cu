@@ -12,6 +12,7 @@
 // cached per batch structure; a structure's sequence of launches can be
 // captured once as a CUDA graph and replayed.
 #include "ctx_internal.h"
+#include "softmin_merge.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -94,40 +95,16 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     }
 }
 
-constexpr int kBatchMergeWarps = 8;
-
-// Merge rows: (instance, first output).  One warp per output of U*, as the
-// single-instance merge; the instance's first row also writes min S and adds
-// the k = 0 terms to its costs.
-__global__ void __launch_bounds__(32 * kBatchMergeWarps)
+// Merge items: (instance, first output); one block per kMergeRows outputs
+// of an instance's U*, as the single-instance merge (merge_rows).  The
+// instance's first item also writes min S and adds the k = 0 terms to its
+// costs.
+__global__ void __launch_bounds__(kMergeThreads)
 batch_merge_kernel(const BatchInstance *inst, const int2 *rows)
 {
     const int2 row = rows[blockIdx.x];
     const BatchInstance &I = inst[row.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nb = I.job.nb, na = I.job.H * kNJ;
-    const float inv_lambda = I.job.inv_lambda;
-    const float *pm_ = I.job.part, *pz = pm_ + nb, *pacc = pm_ + 2 * static_cast<size_t>(nb);
-    float lm = CUDART_INF_F;
-    for (int b = lane; b < nb; b += 32) lm = fminf(lm, pm_[b]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
-    const float M = lm;
-    float lz = 0.f;
-    for (int b = lane; b < nb; b += 32) lz = fmaf(weight_factor(pm_[b], M, inv_lambda), pz[b], lz);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lz += __shfl_xor_sync(0xffffffffu, lz, off);
-    const float Z = __shfl_sync(0xffffffffu, lz, 0);
-    const int t = row.y + warp;
-    if (t < na && warp < kBatchMergeWarps) {
-        const float *r = pacc + static_cast<size_t>(t) * nb;
-        float la = 0.f;
-        for (int b = lane; b < nb; b += 32) la = fmaf(weight_factor(pm_[b], M, inv_lambda), r[b], la);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) la += __shfl_xor_sync(0xffffffffu, la, off);
-        la = __shfl_sync(0xffffffffu, la, 0);
-        if (lane == 0) I.Uout[t] = I.job.Ubar[t] + la / Z;
-    }
+    const float M = merge_rows(I.job.part, I.job.nb, I.job.H * kNJ, row.y, I.job.inv_lambda, I.job.Ubar, I.Uout);
     if (row.y == 0) {
         const float k0 = I.c0[0];
         if (threadIdx.x == 0) I.c0[1] = M + k0;
@@ -321,7 +298,7 @@ pm_status stage_batch(pm_batch *b, const pm_batch_item *it, int n, const Plan &p
     for (int i = 0; i < n; ++i) {
         const size_t na = static_cast<size_t>(it[i].H) * kNJ;
         part += static_cast<size_t>(p.nb[i]) * (2 + na);
-        rows += (na + kBatchMergeWarps - 1) / kBatchMergeWarps;
+        rows += (na + kMergeRows - 1) / kMergeRows;
         work += p.nb[i];
         tune_f += na + static_cast<size_t>(it[i].K) + 32;
     }
@@ -386,7 +363,7 @@ pm_status stage_batch(pm_batch *b, const pm_batch_item *it, int n, const Plan &p
             toff += na + x.K + 32;
         }
         off += static_cast<size_t>(p.nb[i]) * (2 + na);
-        for (int t = 0; t < static_cast<int>(na); t += kBatchMergeWarps) b->h_rows[ri++] = int2{i, t};
+        for (int t = 0; t < static_cast<int>(na); t += kMergeRows) b->h_rows[ri++] = int2{i, t};
     }
     for (int i : order)
         for (int lb = 0; lb < p.nb[i]; ++lb) b->h_work[wi++] = int2{i, lb};
@@ -410,7 +387,7 @@ pm_status enqueue_batch(pm_batch *b, int n, int n_work, int n_rows, int n_iters,
         if (b->smem_call > batch_smem()) smpc_batch_kernel<float, true><<<grid, kBlock, b->smem_call, s>>>(a);
         else smpc_batch_kernel<float, false><<<grid, kBlock, b->smem_call, s>>>(a);
         PM_BCUDA(b, cudaGetLastError());
-        batch_merge_kernel<<<n_rows, 32 * kBatchMergeWarps, 0, s>>>(b->d_inst, b->d_rows);
+        batch_merge_kernel<<<n_rows, kMergeThreads, 0, s>>>(b->d_inst, b->d_rows);
         PM_BCUDA(b, cudaGetLastError());
     }
     if (!tune) {
@@ -487,7 +464,7 @@ pm_status pm::batch_reserve(pm_batch *b, int max_items, int flags)
     const size_t n = static_cast<size_t>(max_items);
     const double scale = (flags & PM_BATCH_AUTOTUNE) ? 4.0 : 1.0;
     const size_t work = static_cast<size_t>(scale * b->n_sm * b->blocks_per_sm) + 2 * n;
-    const size_t rows = n * ((kBatchMaxSteps * kNJ + kBatchMergeWarps - 1) / kBatchMergeWarps);
+    const size_t rows = n * ((kBatchMaxSteps * kNJ + kMergeRows - 1) / kMergeRows);
     pm_status st;
     if ((st = grow_dev(b, &b->d_inst, &b->cap_inst, n)) != PM_OK) return st;
     if ((st = grow_host(b, &b->h_inst, &b->cap_hinst, n)) != PM_OK) return st;

@@ -2,6 +2,7 @@
 // host<->device staging and kernel dispatch.  The arithmetic lives in
 // smpc_device.cuh / smpc_kernels.cuh.
 #include "ctx_internal.h"
+#include "softmin_merge.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -204,46 +205,15 @@ __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint3
     }
 }
 
-// Soft-min merge (Eqs. 29-30) of the iteration kernel's nb block partials
-// (m [nb], z [nb], acc [na][nb]): one warp per output t of U*.  Every warp
-// forms M = min_b m_b and Z = sum_b f_b z_b, f_b = exp((M - m_b)/lambda), the
-// same way (lane-strided sums in ascending b, then a fixed butterfly, lane
-// 0's value), then U*[t] = Ubar[t] + sum_b f_b acc_b[t] / Z.  Block 0 also
-// writes min S = M + c0 and adds the k = 0 terms c0 to the costs.
-constexpr int kMergeWarps = 8;
-
-__device__ __forceinline__ float warp_sum_lane0(float v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return __shfl_sync(0xffffffffu, v, 0);
-}
-
-__global__ void __launch_bounds__(32 * kMergeWarps)
+// Soft-min merge (Eqs. 29-30) of the iteration kernel's nb block partials:
+// block x produces outputs kMergeRows x .. of U* (merge_rows).  Block 0 also
+// writes min S = M + c0, and the k = 0 terms c0 are added to the costs.
+__global__ void __launch_bounds__(kMergeThreads)
 softmin_merge_kernel(const float *part, int nb, int na, const float *Ubar, float *Uout,
                      float inv_lambda, float *c0, float *costs, int K)
 {
     grid_dependency_prologue();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float *pm_ = part, *pz = part + nb, *pacc = part + 2 * static_cast<size_t>(nb);
-    float lm = CUDART_INF_F;
-    for (int b = lane; b < nb; b += 32) lm = fminf(lm, __ldg(pm_ + b));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, off));
-    const float M = lm;
-    // Z = sum_b f_b z_b and this warp's row sum_b f_b acc_b in one pass,
-    // f_b = exp((M - m_b) / lambda), each sum in lane-strided then fixed tree order
-    const int t = blockIdx.x * kMergeWarps + warp;
-    const float *row = pacc + static_cast<size_t>(t < na ? t : 0) * nb;
-    float lz = 0.f, la = 0.f;
-    for (int b = lane; b < nb; b += 32) {
-        const float f = weight_factor(__ldg(pm_ + b), M, inv_lambda);
-        lz = fmaf(f, __ldg(pz + b), lz);
-        if (t < na) la = fmaf(f, __ldg(row + b), la);
-    }
-    const float Z = warp_sum_lane0(lz);
-    const float acc = warp_sum_lane0(la);
-    if (t < na && lane == 0) Uout[t] = Ubar[t] + acc / Z;
+    const float M = merge_rows(part, nb, na, blockIdx.x * kMergeRows, inv_lambda, Ubar, Uout);
     const float k0 = __ldg(c0);
     if (blockIdx.x == 0 && threadIdx.x == 0) c0[1] = M + k0;
     if (costs)
@@ -456,8 +426,8 @@ pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, si
     }
     if (!trace) {
         const int na = H * kNJ;
-        PM_CUDA(c, launch_dependent(softmin_merge_kernel, dim3((na + kMergeWarps - 1) / kMergeWarps),
-                                    dim3(32 * kMergeWarps), 0, s, static_cast<const float *>(part), nb, na,
+        PM_CUDA(c, launch_dependent(softmin_merge_kernel, dim3((na + kMergeRows - 1) / kMergeRows),
+                                    dim3(kMergeThreads), 0, s, static_cast<const float *>(part), nb, na,
                                     Ubar, Uout, a.inv_lambda, c0, costs, K));
         PM_CUDA(c, cudaGetLastError());
     }
