@@ -313,7 +313,17 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     const int unit = (lb * kWarps + warp) / P;
     const int n_units = job.nb * kWarps / P;
     const int n_tiles = (job.K + R - 1) / R;
-    for (int tile = unit; tile < n_tiles; tile += n_units) {
+    // The state terms of k = 0 are the same for every roll-out: one lane
+    // evaluates them once, in an extra pass through the step code (so they
+    // add no code to the kernel), into job.c0; the merge adds them to S.
+    // When the tiles do not divide evenly over the units, that pass runs as
+    // a tile of its own (index n_tiles, no roll-outs) on the unit that would
+    // take tile n_tiles, one with a tile fewer than the busiest units, so it
+    // does not lengthen the launch; otherwise it follows the steps of the
+    // last tile.
+    const bool with_c0 = !TRACE && job.c0;
+    const int c0_tile = (with_c0 && n_tiles % n_units != 0) ? n_tiles : n_tiles - 1;
+    for (int tile = unit; tile <= c0_tile; tile += n_units) {
         const int m = tile * R + seg;
         const bool active = m < job.K;
 
@@ -370,12 +380,9 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             }
         }
 
-        // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25).
-        // The state terms of k = 0 are the same for every roll-out: the lane
-        // holding step 0 of the last tile evaluates them once, in an extra
-        // pass through the same code (so they add no code to the kernel),
-        // into job.c0; the merge adds them to S.
-        const bool c0_lane = !TRACE && job.c0 && tile == n_tiles - 1 && seg == 0 && sl == 0 && half == 0;
+        // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25),
+        // then, on lane 0 of tile c0_tile, the k = 0 pass
+        const bool c0_lane = with_c0 && tile == c0_tile && seg == 0 && sl == 0 && half == 0;
         float lsum = 0.f, lcomp = 0.f;
         float runU[kNJ], runB[kNJ];
 #pragma unroll
