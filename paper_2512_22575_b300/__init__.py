@@ -51,6 +51,16 @@ def _ptr(x, dtype=np.float32, n=None, writable=False):
     """Raw address of a numpy array / torch tensor (None -> NULL)."""
     if x is None:
         return None
+    if type(x) is np.ndarray:   # the common host case, kept cheap (it runs per call)
+        if x.dtype != dtype or not x.flags.c_contiguous:
+            raise ValueError(f"expected a C-contiguous numpy {np.dtype(dtype).name} array")
+        if n is not None and x.size < n:
+            raise ValueError(f"array has {x.size} elements, need {n}")
+        if x.flags.writeable and x.nbytes > 0:
+            return C.addressof(C.c_char.from_buffer(x))
+        if writable:
+            raise ValueError("output array is read-only")
+        return x.ctypes.data
     if hasattr(x, "data_ptr"):  # torch tensor
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
@@ -316,6 +326,9 @@ def _stream(stream):
     if stream is None:
         torch = sys.modules.get("torch")
         if torch is not None and torch.cuda.is_initialized():
+            raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+            if raw is not None:     # the handle without building a Stream object
+                return raw(torch.cuda.current_device())
             return C.c_void_p(torch.cuda.current_stream().cuda_stream)
         return None
     if hasattr(stream, "cuda_stream"):

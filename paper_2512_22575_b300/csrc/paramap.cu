@@ -349,13 +349,26 @@ pm_status check_call(pm_ctx *c, const float *q0, const float *qd0, const float *
     return PM_OK;
 }
 
+// Pinned staging slots (host and device mirrors): [0, 32) the inputs q0,
+// qd0, T_goal; [32, 64) a call's small outputs; [64, ...) U.  Inputs, and U
+// when it is on the host, go to the device in one copy; a replan's outputs
+// and U come back in one copy.
 constexpr int kSlots = 16;
-constexpr int kSlotFloats = 32;
+constexpr int kSlotIn = 32;
+constexpr int kSlotOut = 32;
+constexpr int kSlotFloats = kSlotIn + kSlotOut + kMaxHorizon * kNJ;
+
+struct SlotIO {
+    float *d = nullptr;   // device [kSlotOut] outputs, then U
+    float *h = nullptr;   // its pinned host mirror
+};
 
 // Resolve q0, qd0, T_goal into device pointers: device inputs are used in
-// place, host inputs are copied through the next pinned staging slot.
+// place, host inputs are copied through the next pinned staging slot.  With
+// U_host (nU floats), U is staged too, at io->d + kSlotOut.
 pm_status stage_inputs(pm_ctx *c, cudaStream_t s, const float *q0, const float *qd0,
-                       const float *T_goal, const float *sigma, CallInputs &in)
+                       const float *T_goal, const float *sigma, CallInputs &in,
+                       const float *U_host = nullptr, int nU = 0, SlotIO *io = nullptr)
 {
     const int k = c->slot;
     c->slot = (c->slot + 1) % kSlots;
@@ -376,8 +389,18 @@ pm_status stage_inputs(pm_ctx *c, cudaStream_t s, const float *q0, const float *
     in.qd0 = place(qd0, kNJ, 8);
     in.Tg = place(T_goal, 16, 16);
     for (int j = 0; j < 8; ++j) in.sigma[j] = j < kNJ ? sigma[j] : 0.f;
+    size_t n_copy = kSlotIn;
+    if (U_host) {
+        std::memcpy(h + kSlotIn + kSlotOut, U_host, nU * sizeof(float));
+        n_copy = kSlotIn + kSlotOut + nU;
+        any_host = true;
+    }
+    if (io) {
+        io->d = d + kSlotIn;
+        io->h = h + kSlotIn;
+    }
     if (any_host) {
-        PM_CUDA(c, cudaMemcpyAsync(d, h, kSlotFloats * sizeof(float), cudaMemcpyHostToDevice, s));
+        PM_CUDA(c, cudaMemcpyAsync(d, h, n_copy * sizeof(float), cudaMemcpyHostToDevice, s));
         PM_CUDA(c, cudaEventRecord(c->slot_ev[k], s));
         c->slot_pending[k] = true;
     }
@@ -861,39 +884,34 @@ pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *
     st = ensure_capacity(c, K, H, 1);
     if (st != PM_OK) return st;
     CallInputs in{};
-    st = stage_inputs(c, s, q, qd, T_goal, sigma, in);
+    SlotIO io;
+    st = stage_inputs(c, s, q, qd, T_goal, sigma, in, dU ? nullptr : U, H * kNJ, &io);
     if (st != PM_OK) return st;
-    float *Ud = U;
-    if (!dU) {
-        std::memcpy(c->h_U, U, sizeof(float) * H * kNJ);
-        PM_CUDA(c, cudaMemcpyAsync(c->d_U, c->h_U, sizeof(float) * H * kNJ, cudaMemcpyHostToDevice, s));
-        Ud = c->d_U;
-    }
+    float *Ud = dU ? U : io.d + kSlotOut;
     for (int it = 0; it < n_iters; ++it) {
         st = launch_iteration(c, s, in, Ud, Ud, nullptr, K, H, dt, lambda, seed,
                               replan_index * static_cast<uint32_t>(n_iters) + static_cast<uint32_t>(it),
                               false, nullptr);
         if (st != PM_OK) return st;
     }
-    float *small = c->d_c0 + 8;  // [q 8][qd 8][u0 8] device scratch
+    float *small = io.d;  // [q 8][qd 8][u0 8][min S] for host outputs, then U when staged
     PM_CUDA(c, launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, Ud, H, dt,
                                 dq ? q : small, dqd ? qd : small + 8,
                                 u0_out ? (du0 ? u0_out : small + 16) : static_cast<float *>(nullptr),
                                 static_cast<const float *>(c->d_c0),
-                                best_cost ? (dbest ? best_cost : c->d_c0 + 2) : static_cast<float *>(nullptr)));
+                                best_cost ? (dbest ? best_cost : small + 24) : static_cast<float *>(nullptr)));
     PM_CUDA(c, cudaGetLastError());
     const bool host_out = !dU || !dq || !dqd || (u0_out && !du0) || (best_cost && !dbest);
     if (host_out) {
-        float *h = c->h_out;  // >= 4096 floats
-        PM_CUDA(c, cudaMemcpyAsync(h, small, 24 * sizeof(float), cudaMemcpyDeviceToHost, s));
-        PM_CUDA(c, cudaMemcpyAsync(h + 24, c->d_c0 + 2, sizeof(float), cudaMemcpyDeviceToHost, s));
-        if (!dU) PM_CUDA(c, cudaMemcpyAsync(c->h_U, c->d_U, sizeof(float) * H * kNJ, cudaMemcpyDeviceToHost, s));
+        const float *h = io.h;
+        const size_t n_back = kSlotOut + (dU ? 0 : static_cast<size_t>(H) * kNJ);
+        PM_CUDA(c, cudaMemcpyAsync(io.h, io.d, n_back * sizeof(float), cudaMemcpyDeviceToHost, s));
         PM_CUDA(c, cudaStreamSynchronize(s));
         if (!dq) std::memcpy(q, h, kNJ * sizeof(float));
         if (!dqd) std::memcpy(qd, h + 8, kNJ * sizeof(float));
         if (u0_out && !du0) std::memcpy(u0_out, h + 16, kNJ * sizeof(float));
         if (best_cost && !dbest) *best_cost = h[24];
-        if (!dU) std::memcpy(U, c->h_U, sizeof(float) * H * kNJ);
+        if (!dU) std::memcpy(U, h + kSlotOut, sizeof(float) * H * kNJ);
     }
     return PM_OK;
 }
