@@ -727,6 +727,18 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         }
         r.n_self_groups = g + 1;
         r.grp_begin[g + 1] = static_cast<unsigned short>(ps.size());
+        // dense groups: exactly the pairs (a, b) of frame fa's x frame fb's
+        // spheres, fa != fb, at most kSelfDense spheres each, in (a, b) order
+        for (int k = 0; k <= g; ++k) {
+            const int fa = r.grp_fa[k], fb = r.grp_fb[k];
+            const int a_lo = r.link_begin[fa + 1], na = r.link_begin[fa + 2] - a_lo;
+            const int b_lo = r.link_begin[fb + 1], nb = r.link_begin[fb + 2] - b_lo;
+            const int p0 = r.grp_begin[k], np = r.grp_begin[k + 1] - p0;
+            bool dense = fa != fb && na >= 1 && nb >= 1 && na <= kSelfDense && nb <= kSelfDense && np == na * nb;
+            for (int i = 0; dense && i < np; ++i)
+                dense = ps[p0 + i].a == a_lo + i / nb && ps[p0 + i].b == b_lo + i % nb;
+            r.grp_dense[k] = dense ? 1 : 0;
+        }
     }
     for (int i = 0; i < 6; ++i) { r.Q[i] = cp->Q[i]; r.QH[i] = cp->QH[i]; }
     r.w_env = cp->w_env; r.d_act = cp->d_act; r.w_self = cp->w_self;

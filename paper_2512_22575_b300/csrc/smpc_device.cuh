@@ -24,6 +24,7 @@ constexpr int kMaxSpheres = 64;
 constexpr int kMaxHorizon = 256;
 constexpr int kMaxSelfGroups = (kNJ * (kNJ + 1)) / 2;   // frame pairs (a <= b) of the self-collision set
 constexpr int kMaxSelfPairs = 4096;
+constexpr int kSelfDense = 4;        // spheres per frame of a dense self-collision group
 
 // Arm + cost constants, passed by value as a kernel parameter (constant bank).
 struct RobotConst {
@@ -54,6 +55,9 @@ struct RobotConst {
     int n_self_groups;
     unsigned char grp_fa[kMaxSelfGroups], grp_fb[kMaxSelfGroups];   // frame index - 1
     unsigned short grp_begin[kMaxSelfGroups + 1];                    // pairs of group g
+    // 1: group g holds every pair of its two frames' spheres (at most
+    // kSelfDense each), in (a, b) order, so it is evaluated as a dense block
+    unsigned char grp_dense[kMaxSelfGroups];
     float grp_thr2[kMaxSelfGroups];
     float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
     // device [n], grouped and ordered by (a, b) within a group: x = bits of

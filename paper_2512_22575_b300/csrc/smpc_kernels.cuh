@@ -140,6 +140,38 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
         const float gy = sp[(fa + 1) * 32] - sp[(fb + 1) * 32];
         const float gz = sp[(fa + 2) * 32] - sp[(fb + 2) * 32];
         if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > rc.grp_thr2[gi]) continue;   // exact zero
+        if (rc.grp_dense[gi]) {
+            // every pair of the two frames: b's centres and radii in
+            // registers, a pair's term skipped only where it is exactly 0
+            // (then sqrt(d2) >= t > r_a + r_b), in (a, b) order as listed
+            const int a_lo = rc.link_begin[rc.grp_fa[gi] + 1], a_hi = rc.link_begin[rc.grp_fa[gi] + 2];
+            const int b_lo = rc.link_begin[rc.grp_fb[gi] + 1], nb = rc.link_begin[rc.grp_fb[gi] + 2] - b_lo;
+            float bx[kSelfDense], by[kSelfDense], bz[kSelfDense], br[kSelfDense];
+#pragma unroll
+            for (int i = 0; i < kSelfDense; ++i) {
+                const int b = 3 * (b_lo + min(i, nb - 1));
+                bx[i] = sp[b * 32];
+                by[i] = sp[(b + 1) * 32];
+                bz[i] = sp[(b + 2) * 32];
+                br[i] = rc.sph_r[b_lo + min(i, nb - 1)];
+            }
+            for (int a = a_lo; a < a_hi; ++a) {
+                const float ax = sp[(3 * a) * 32], ay = sp[(3 * a + 1) * 32], az = sp[(3 * a + 2) * 32];
+                const float ra = rc.sph_r[a];
+#pragma unroll
+                for (int i = 0; i < kSelfDense; ++i) {
+                    const float ex = ax - bx[i], ey = ay - by[i], ez = az - bz[i];
+                    const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const float rs = ra + br[i];
+                    const float t = __fadd_ru(rs, 1e-5f);
+                    if (i < nb && d2 <= __fmul_ru(t, t)) {
+                        const float del = fmaxf(rs - sqrtf(d2), 0.f);
+                        acc = fmaf(del, del, acc);
+                    }
+                }
+            }
+            continue;
+        }
         int a_prev = -1;
         float ax = 0.f, ay = 0.f, az = 0.f;
         for (int p = rc.grp_begin[gi]; p < rc.grp_begin[gi + 1]; ++p) {
