@@ -61,6 +61,26 @@ def test_self_terms_match_oracle_trace(min_gap):
     assert np.allclose(tr, ref, rtol=1e-4, atol=1e-7)
 
 
+def test_partial_pair_sets_match_oracle_trace():
+    """A seeded half of the adjacent-frame set, some pairs listed as (b, a):
+    no group holds every pair of its two frames, so each is evaluated from
+    its pair list rather than as a dense block."""
+    sc = Scene("cfg1_seed7", cost_overrides={"w_self": np.float32(0.5)})
+    sc.robot = dict(sc.robot)
+    full = workloads.self_collision_pairs(sc.robot, min_link_gap=1)
+    rng = np.random.default_rng(17)
+    pick = full[rng.permutation(len(full))[: len(full) // 2]].copy()
+    flip = rng.random(len(pick)) < 0.5
+    pick[flip] = pick[flip][:, ::-1]
+    sc.robot["self_pairs"] = np.ascontiguousarray(pick, dtype=np.int32)
+    sc.R = oracle.make_robot(sc.robot)
+    sc.C = oracle.make_cost(sc.cp)
+    tr, ref = trace_both(sc, 8, 32, SIGMA, 9)
+    assert (ref[:, 1:32, 2] > 0).any()
+    assert np.array_equal(tr[:, 1:32, 2] == 0, ref[:, 1:32, 2] == 0)
+    assert np.allclose(tr, ref, rtol=1e-4, atol=1e-7)
+
+
 def test_far_groups_are_skipped_exactly():
     """Pairs on frames >= 3 apart under large noise: the arm folds in some
     steps (about one in eight here); where the oracle's self term is 0 the
