@@ -98,7 +98,13 @@ long long launch_blocks(long long K, TileShape sh, long long resident)
     const int R = 32 / sh.L;
     const long long tiles = (K + R - 1) / R;
     const long long need = (tiles * sh.P + kWarps - 1) / kWarps;
-    return std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)}));
+    long long nb = std::max(1LL, std::min({need, resident, static_cast<long long>(kMaxBlocks)}));
+    // When the tiles divide evenly over the units, the k = 0 pass would
+    // follow a unit's last tile; one more block, where it still fits, gives
+    // the pass a unit of its own that runs beside the tiles (its partial is
+    // empty: m = inf, z = 0).
+    if (tiles % (nb * kWarps / sh.P) == 0 && nb < resident && nb < kMaxBlocks) ++nb;
+    return nb;
 }
 
 size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : 2; }
