@@ -3,9 +3,10 @@
 // robot-masked occupancy reset, and the update of a context's distance
 // field from an occupancy grid.
 //
-// EDT: the separable three-pass squared transform, one 1-D
-// Felzenszwalb-Huttenlocher lower envelope of parabolas per grid line, along
-// y, then x, then z, on the native [z][y][x] layout.  Each thread owns one
+// EDT: the separable three-pass squared transform along y, then x, then z,
+// on the native [z][y][x] layout; each pass is the 1-D transform of every
+// grid line, by a Felzenszwalb-Huttenlocher lower envelope of parabolas or,
+// for short lines, by the direct minimum over the line (below).  Each thread owns one
 // line: it gathers the line (stride 1, nx or nx*ny) into its own column of
 // shared memory, builds the envelope there and writes the line back -- no
 // transposition of the grid.  Envelope boundaries are exact fractions of
@@ -138,6 +139,156 @@ cudaError_t run_pass(const void *in, int *out, const EdtPass &ps, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Short lines (n <= kEdtBfMax) take a direct pass instead of the envelope:
+// a block stages 32 neighbouring lines as h_i = f_i + i^2 in shared memory,
+// as floats, and every output d(x) = min_i (h_i - 2 x i) + x^2 is one FMA and
+// one min per candidate i.  All values are integers below 2^24 (the caller
+// checks the bound), so FP32 computes them exactly and the result equals
+// the envelope's.  The work is O(n^2) per line against the envelope's O(n),
+// but every (line, x) is independent, where the envelope walks its line
+// with one thread.  Lines are staged along the line when it is contiguous
+// and across lines otherwise, so loads and stores stay coalesced.
+constexpr int kEdtBfMax = 256;
+constexpr int kEdtBfLines = 32;
+constexpr int kEdtBfPitch = kEdtBfLines + 1;   // shared-memory row pitch (no bank conflicts)
+constexpr int kEdtBfWarps = 8;
+constexpr int kEdtBfOut = 8;                   // outputs per thread per sweep over the candidates
+
+template <bool FROM_OCC>
+__global__ void __launch_bounds__(kEdtBfWarps * 32)
+edt_pass_direct_kernel(const void *in, int *out, EdtPass ps)
+{
+    extern __shared__ float s_bf[];
+    const int n = ps.n;
+    float *h = s_bf;                                                  // [n][pitch] h_i
+    int *d = reinterpret_cast<int *>(s_bf + n * kEdtBfPitch);         // [n][pitch] outputs
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long line0 = static_cast<long long>(blockIdx.x) * kEdtBfLines;
+    auto base_of = [&](long long l) { return (l % ps.na) * ps.sa + (l / ps.na) * ps.sb; };
+    auto h_of = [&](long long idx, int i) -> float {
+        if (FROM_OCC) return static_cast<const unsigned char *>(in)[idx] ? static_cast<float>(i * i) : CUDART_INF_F;
+        const int x = static_cast<const int *>(in)[idx];
+        return x == kEdtInf ? CUDART_INF_F : static_cast<float>(x) + static_cast<float>(i * i);
+    };
+    if (ps.se == 1) {
+        for (int li = warp; li < kEdtBfLines; li += kEdtBfWarps) {
+            const long long l = line0 + li;
+            const bool ok = l < ps.n_lines;
+            const long long base = ok ? base_of(l) : 0;
+            for (int i = lane; i < n; i += 32) h[i * kEdtBfPitch + li] = ok ? h_of(base + i, i) : CUDART_INF_F;
+        }
+    } else {
+        const long long l = line0 + lane;
+        const bool ok = l < ps.n_lines;
+        const long long base = ok ? base_of(l) : 0;
+        for (int i = warp; i < n; i += kEdtBfWarps)
+            h[i * kEdtBfPitch + lane] = ok ? h_of(base + i * ps.se, i) : CUDART_INF_F;
+    }
+    __syncthreads();
+    // lane: line; a warp takes kEdtBfOut consecutive outputs per sweep
+    for (int x0 = warp * kEdtBfOut; x0 < n; x0 += kEdtBfWarps * kEdtBfOut) {
+        float m[kEdtBfOut], c[kEdtBfOut];
+#pragma unroll
+        for (int k = 0; k < kEdtBfOut; ++k) {
+            m[k] = CUDART_INF_F;
+            c[k] = -2.0f * static_cast<float>(x0 + k);
+        }
+        float fi = 0.f;
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+            const float hi = h[i * kEdtBfPitch + lane];
+#pragma unroll
+            for (int k = 0; k < kEdtBfOut; ++k) m[k] = fminf(m[k], fmaf(c[k], fi, hi));
+            fi += 1.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kEdtBfOut; ++k) {
+            const int x = x0 + k;
+            if (x < n)
+                d[x * kEdtBfPitch + lane] =
+                    m[k] == CUDART_INF_F ? kEdtInf : static_cast<int>(m[k] + static_cast<float>(x * x));
+        }
+    }
+    __syncthreads();
+    if (ps.se == 1) {
+        for (int li = warp; li < kEdtBfLines; li += kEdtBfWarps) {
+            const long long l = line0 + li;
+            if (l >= ps.n_lines) continue;
+            const long long base = base_of(l);
+            for (int i = lane; i < n; i += 32) out[base + i] = d[i * kEdtBfPitch + li];
+        }
+    } else {
+        const long long l = line0 + lane;
+        if (l < ps.n_lines) {
+            const long long base = base_of(l);
+            for (int i = warp; i < n; i += kEdtBfWarps) out[base + i * ps.se] = d[i * kEdtBfPitch + lane];
+        }
+    }
+}
+
+// The first pass from occupancy, for lines up to kEdtBfMax: the squared
+// distance along the line is to the nearest occupied element on either
+// side, found by a forward and a backward sweep.  One thread per line (a
+// warp takes 32 neighbouring lines, which sit next to each other in memory
+// for the y pass, so the gathers are coalesced); the line's flags are
+// staged in shared memory.
+__global__ void __launch_bounds__(32)
+edt_occ_sweep_kernel(const unsigned char *occ, int *out, EdtPass ps)
+{
+    extern __shared__ int s_sw[];                         // [n][pitch]: occupied, then the forward result
+    const int n = ps.n, lane = threadIdx.x;
+    const long long l = static_cast<long long>(blockIdx.x) * 32 + lane;
+    if (l >= ps.n_lines) return;
+    const long long base = (l % ps.na) * ps.sa + (l / ps.na) * ps.sb;
+    int *c = s_sw + lane;
+    // forward: distance to the nearest occupied element at or before i
+    int last = -1;
+    for (int i = 0; i < n; ++i) {
+        const bool o = occ[base + i * ps.se] != 0;
+        if (o) last = i;
+        c[i * kEdtBfPitch] = last < 0 ? kEdtInf : (i - last) * (i - last);
+    }
+    // backward: the nearest at or after i, and the minimum of the two
+    int next = -1;
+    for (int i = n - 1; i >= 0; --i) {
+        const int f = c[i * kEdtBfPitch];
+        if (f == 0) next = i;
+        const int b = next < 0 ? kEdtInf : (next - i) * (next - i);
+        out[base + i * ps.se] = min(f, b);
+    }
+}
+
+cudaError_t run_occ_sweep(const unsigned char *occ, int *out, const EdtPass &ps, cudaStream_t s)
+{
+    const size_t smem = static_cast<size_t>(ps.n) * kEdtBfPitch * sizeof(int);
+    cudaError_t e = cudaFuncSetAttribute(edt_occ_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int blocks = static_cast<int>((ps.n_lines + 31) / 32);
+    edt_occ_sweep_kernel<<<blocks, 32, smem, s>>>(occ, out, ps);
+    return cudaGetLastError();
+}
+
+// The direct pass is exact when every staged value and every h_i - 2 x i
+// stays below 2^24: inputs up to bound_in, plus at most 3 (n-1)^2.
+bool direct_pass_exact(int n, long long bound_in)
+{
+    const long long m = n - 1;
+    return n <= kEdtBfMax && bound_in + 3 * m * m < (1LL << 24);
+}
+
+template <bool FROM_OCC>
+cudaError_t run_direct_pass(const void *in, int *out, const EdtPass &ps, cudaStream_t s)
+{
+    const size_t smem = 2 * static_cast<size_t>(ps.n) * kEdtBfPitch * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(edt_pass_direct_kernel<FROM_OCC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int blocks = static_cast<int>((ps.n_lines + kEdtBfLines - 1) / kEdtBfLines);
+    edt_pass_direct_kernel<FROM_OCC><<<blocks, kEdtBfWarps * 32, smem, s>>>(in, out, ps);
+    return cudaGetLastError();
+}
+
 // Squared EDT of occ [nz][ny][nx] into d2 (int32, kEdtInf without any site);
 // tmp is scratch of the same size (y pass into d2, x pass into tmp, z pass
 // back into d2).
@@ -150,9 +301,14 @@ cudaError_t edt3d(const unsigned char *occ, int nx, int ny, int nz, int *d2, int
     EdtPass px{nx, ny, ny * nz, sy, sz, 1};
     // z lines (x, y): coalesced
     EdtPass pz{nz, nx, nx * ny, 1, sy, sz};
-    cudaError_t e = run_pass<true>(occ, d2, py, s);
-    if (e == cudaSuccess) e = run_pass<false>(d2, tmp, px, s);
-    if (e == cudaSuccess) e = run_pass<false>(tmp, d2, pz, s);
+    // each pass direct when exact for its line length and input bound, else
+    // the envelope
+    const long long by = static_cast<long long>(ny - 1) * (ny - 1), bx = static_cast<long long>(nx - 1) * (nx - 1);
+    cudaError_t e = ny <= kEdtBfMax ? run_occ_sweep(occ, d2, py, s) : run_pass<true>(occ, d2, py, s);
+    if (e == cudaSuccess)
+        e = direct_pass_exact(nx, by) ? run_direct_pass<false>(d2, tmp, px, s) : run_pass<false>(d2, tmp, px, s);
+    if (e == cudaSuccess)
+        e = direct_pass_exact(nz, by + bx) ? run_direct_pass<false>(tmp, d2, pz, s) : run_pass<false>(tmp, d2, pz, s);
     return e;
 }
 
