@@ -15,6 +15,8 @@ struct pm_ctx {
     pm::RobotConst *d_rc = nullptr;     // device copy (read by the batched kernels)
     unsigned char *d_map_occ = nullptr; // mapping scratch: occupancy copy, two int32 EDT buffers
     int *d_map_a = nullptr, *d_map_b = nullptr;
+    float *d_phi_table = nullptr;       // res * sqrt(D) for D = 0 .. phi_table_n - 1 (or null)
+    size_t phi_table_n = 0;
     float4 *d_self_pairs = nullptr;     // self-collision pairs, grouped (rc.self_pairs)
     pm_grid_desc gd{};
     size_t grid_elems = 0;

@@ -316,16 +316,47 @@ cudaError_t edt3d(const unsigned char *occ, int nx, int ny, int nz, int *d2, int
 // without any occupied voxel phi = kFarField.
 constexpr double kFarField = 1e10;
 
+// The squared distances of a grid take at most (nx-1)^2 + (ny-1)^2 +
+// (nz-1)^2 + 1 values; up to kPhiTableMax of them, a table of their metres,
+// computed with the same FP64 expression, turns the conversion into a
+// gather (FP64 is slow on this GPU).
+constexpr size_t kPhiTableMax = size_t(1) << 22;
+
+__global__ void phi_table_kernel(float *table, size_t n, double res)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        table[i] = static_cast<float>(res * sqrt(static_cast<double>(i)));
+}
+
+__device__ __forceinline__ void store_phi(void *phi, size_t i, float v, int dtype)
+{
+    if (dtype == PM_F32) static_cast<float *>(phi)[i] = v;
+    else if (dtype == PM_F16) static_cast<__half *>(phi)[i] = __float2half_rn(v);
+    else static_cast<__nv_bfloat16 *>(phi)[i] = __float2bfloat16_rn(v);
+}
+
+__global__ void d2_to_phi_table_kernel(const int *d2, void *phi, size_t n, const float *table, size_t table_n,
+                                       double res, int dtype)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int d = d2[i];
+        float v;
+        if (d == kEdtInf) v = static_cast<float>(kFarField);
+        else if (static_cast<size_t>(d) < table_n) v = __ldg(table + d);
+        else v = static_cast<float>(res * sqrt(static_cast<double>(d)));   // not reached for a grid's own transform
+        store_phi(phi, i, v, dtype);
+    }
+}
+
 __global__ void d2_to_phi_kernel(const int *d2, void *phi, size_t n, double res, int dtype)
 {
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const int d = d2[i];
         const double m = d == kEdtInf ? kFarField : res * sqrt(static_cast<double>(d));
-        const float v = static_cast<float>(m);
-        if (dtype == PM_F32) static_cast<float *>(phi)[i] = v;
-        else if (dtype == PM_F16) static_cast<__half *>(phi)[i] = __float2half_rn(v);
-        else static_cast<__nv_bfloat16 *>(phi)[i] = __float2bfloat16_rn(v);
+        store_phi(phi, i, static_cast<float>(m), dtype);
     }
 }
 
@@ -452,6 +483,18 @@ pm_status pm_map_update(pm_ctx *c, const uint8_t *occ, int occ_is_device, const 
             cudaError_t e = cudaMalloc(&c->d_map_occ, n);
             if (e == cudaSuccess) e = cudaMalloc(&c->d_map_a, n * sizeof(int));
             if (e == cudaSuccess) e = cudaMalloc(&c->d_map_b, n * sizeof(int));
+            const size_t nt = static_cast<size_t>(c->gd.nx - 1) * (c->gd.nx - 1) +
+                              static_cast<size_t>(c->gd.ny - 1) * (c->gd.ny - 1) +
+                              static_cast<size_t>(c->gd.nz - 1) * (c->gd.nz - 1) + 1;
+            if (e == cudaSuccess && nt <= kPhiTableMax) {
+                e = cudaMalloc(&c->d_phi_table, nt * sizeof(float));
+                if (e == cudaSuccess) {
+                    c->phi_table_n = nt;
+                    phi_table_kernel<<<static_cast<unsigned>(std::min<size_t>((nt + 255) / 256, 4u * c->n_sm)), 256, 0,
+                                       s>>>(c->d_phi_table, nt, static_cast<double>(c->gd.res));
+                    e = cudaGetLastError();
+                }
+            }
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return map_err(c, PM_ENOMEM, "mapping scratch allocation failed");
@@ -471,8 +514,13 @@ pm_status pm_map_update(pm_ctx *c, const uint8_t *occ, int occ_is_device, const 
     DeviceGuard dg(c->device);
     cudaError_t e = edt3d(c->d_map_occ, c->gd.nx, c->gd.ny, c->gd.nz, c->d_map_a, c->d_map_b, s);
     if (e == cudaSuccess) {
-        d2_to_phi_kernel<<<static_cast<unsigned>(std::min<size_t>((n + 255) / 256, 8u * c->n_sm)), 256, 0, s>>>(
-            c->d_map_a, c->d_grid, n, static_cast<double>(c->gd.res), c->gd.dtype);
+        const unsigned blocks = static_cast<unsigned>(std::min<size_t>((n + 255) / 256, 8u * c->n_sm));
+        if (c->d_phi_table)
+            d2_to_phi_table_kernel<<<blocks, 256, 0, s>>>(c->d_map_a, c->d_grid, n, c->d_phi_table, c->phi_table_n,
+                                                          static_cast<double>(c->gd.res), c->gd.dtype);
+        else
+            d2_to_phi_kernel<<<blocks, 256, 0, s>>>(c->d_map_a, c->d_grid, n, static_cast<double>(c->gd.res),
+                                                    c->gd.dtype);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
