@@ -16,6 +16,7 @@ struct pm_ctx {
     unsigned char *d_map_occ = nullptr; // mapping scratch: occupancy copy, two int32 EDT buffers
     int *d_map_a = nullptr, *d_map_b = nullptr;
     float *d_phi_table = nullptr;       // res * sqrt(D) for D = 0 .. phi_table_n - 1 (or null)
+    float4 *d_mask_spheres = nullptr;   // robot mask: sphere centres and radii [kMaxSpheres]
     size_t phi_table_n = 0;
     float4 *d_self_pairs = nullptr;     // self-collision pairs, grouped (rc.self_pairs)
     pm_grid_desc gd{};

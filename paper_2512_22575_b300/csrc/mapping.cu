@@ -360,44 +360,50 @@ __global__ void d2_to_phi_kernel(const int *d2, void *phi, size_t n, double res,
     }
 }
 
-// Robot mask: block s clears the voxels of sphere s (centre at configuration
-// q, radius + inflate) whose centres lie in the closed ball.
-__global__ void robot_mask_kernel(const RobotConst rc, const float *q, unsigned char *occ, int nx, int ny,
-                                  int nz, float res, float ox, float oy, float oz, float inflate)
+// Robot mask: the world centre and radius (+ inflate) of every sphere at
+// configuration q, one thread per sphere; then blocks (s, z) clear the
+// voxels of sphere s's bounding box, z-slices z, z + gridDim.y, ..., whose
+// centres lie in the closed ball.
+__global__ void sphere_world_kernel(const RobotConst rc, const float *q, float inflate, float4 *out)
 {
-    const int s = blockIdx.x;
-    __shared__ float c[4];
-    __shared__ int box[6];
-    if (threadIdx.x == 0) {
-        int link = 0;
-        while (link < kNJ && rc.link_begin[link + 2] <= s) ++link;   // sphere s lies on frame link + 1
-        Frame F = base_frame();
-        for (int j = 0; j <= link; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
-        const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-        const float r = rc.sph_r[s] + inflate;
-        c[0] = p.x; c[1] = p.y; c[2] = p.z; c[3] = r;
-        // voxel index range whose centres can lie within r (one voxel of slack)
-        const float lo[3] = {(p.x - r - ox) / res - 1.5f, (p.y - r - oy) / res - 1.5f, (p.z - r - oz) / res - 1.5f};
-        const float hi[3] = {(p.x + r - ox) / res + 0.5f, (p.y + r - oy) / res + 0.5f, (p.z + r - oz) / res + 0.5f};
-        const int n[3] = {nx, ny, nz};
-        for (int a = 0; a < 3; ++a) {
-            box[a] = static_cast<int>(fminf(fmaxf(floorf(lo[a]), 0.f), static_cast<float>(n[a])));
-            box[3 + a] = static_cast<int>(fminf(fmaxf(ceilf(hi[a]), 0.f), static_cast<float>(n[a])));
-        }
+    const int s = threadIdx.x;
+    if (s >= rc.n_spheres) return;
+    int link = 0;
+    while (link < kNJ && rc.link_begin[link + 2] <= s) ++link;   // sphere s lies on frame link + 1
+    Frame F = base_frame();
+    for (int j = 0; j <= link; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j]);
+    const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+    out[s] = make_float4(p.x, p.y, p.z, rc.sph_r[s] + inflate);
+}
+
+constexpr int kMaskSlices = 8;
+
+__global__ void robot_mask_kernel(const float4 *spheres, unsigned char *occ, int nx, int ny, int nz, float res,
+                                  float ox, float oy, float oz)
+{
+    const float4 c = spheres[blockIdx.x];
+    const float r = c.w;
+    // voxel index range whose centres can lie within r (one voxel of slack)
+    const float lo[3] = {(c.x - r - ox) / res - 1.5f, (c.y - r - oy) / res - 1.5f, (c.z - r - oz) / res - 1.5f};
+    const float hi[3] = {(c.x + r - ox) / res + 0.5f, (c.y + r - oy) / res + 0.5f, (c.z + r - oz) / res + 0.5f};
+    const int n[3] = {nx, ny, nz};
+    int b0[3], b1[3];
+    for (int a = 0; a < 3; ++a) {
+        b0[a] = static_cast<int>(fminf(fmaxf(floorf(lo[a]), 0.f), static_cast<float>(n[a])));
+        b1[a] = static_cast<int>(fminf(fmaxf(ceilf(hi[a]), 0.f), static_cast<float>(n[a])));
     }
-    __syncthreads();
-    const int bx = box[3] - box[0], by = box[4] - box[1], bz = box[5] - box[2];
-    if (bx <= 0 || by <= 0 || bz <= 0) return;
-    const long long cnt = static_cast<long long>(bx) * by * bz;
-    const float r2 = c[3] * c[3];
-    for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int i = box[0] + static_cast<int>(t % bx);
-        const int j = box[1] + static_cast<int>((t / bx) % by);
-        const int l = box[2] + static_cast<int>(t / (static_cast<long long>(bx) * by));
-        const float dx = fmaf(static_cast<float>(i) + 0.5f, res, ox) - c[0];
-        const float dy = fmaf(static_cast<float>(j) + 0.5f, res, oy) - c[1];
-        const float dz = fmaf(static_cast<float>(l) + 0.5f, res, oz) - c[2];
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= r2) occ[(static_cast<size_t>(l) * ny + j) * nx + i] = 0;
+    const int bx = b1[0] - b0[0], by = b1[1] - b0[1];
+    if (bx <= 0 || by <= 0) return;
+    const int cnt = bx * by;
+    const float r2 = r * r;
+    for (int l = b0[2] + static_cast<int>(blockIdx.y); l < b1[2]; l += gridDim.y) {
+        const float dz = fmaf(static_cast<float>(l) + 0.5f, res, oz) - c.z;
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int i = b0[0] + t % bx, j = b0[1] + t / bx;
+            const float dx = fmaf(static_cast<float>(i) + 0.5f, res, ox) - c.x;
+            const float dy = fmaf(static_cast<float>(j) + 0.5f, res, oy) - c.y;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= r2) occ[(static_cast<size_t>(l) * ny + j) * nx + i] = 0;
+        }
     }
 }
 
@@ -456,8 +462,14 @@ pm_status pm_robot_mask(pm_ctx *c, uint8_t *occ, const float *q, float inflate, 
         qd = slot;
     }
     if (c->rc.n_spheres > 0) {
-        robot_mask_kernel<<<c->rc.n_spheres, 256, 0, s>>>(c->rc, qd, occ, c->gd.nx, c->gd.ny, c->gd.nz, c->gd.res,
-                                                         c->gd.origin[0], c->gd.origin[1], c->gd.origin[2], inflate);
+        if (!c->d_mask_spheres && cudaMalloc(&c->d_mask_spheres, kMaxSpheres * sizeof(float4)) != cudaSuccess) {
+            cudaGetLastError();
+            return map_err(c, PM_ENOMEM, "robot mask scratch allocation failed");
+        }
+        sphere_world_kernel<<<1, 64, 0, s>>>(c->rc, qd, inflate, c->d_mask_spheres);
+        robot_mask_kernel<<<dim3(c->rc.n_spheres, kMaskSlices), 256, 0, s>>>(
+            c->d_mask_spheres, occ, c->gd.nx, c->gd.ny, c->gd.nz, c->gd.res, c->gd.origin[0], c->gd.origin[1],
+            c->gd.origin[2]);
         if (cudaGetLastError() != cudaSuccess) return map_err(c, PM_ECUDA, "robot mask launch failed");
     }
     if (!dq && cudaStreamSynchronize(s) != cudaSuccess) {

@@ -1202,6 +1202,7 @@ void pm_destroy(pm_ctx *c)
         cudaFree(c->d_map_a);
         cudaFree(c->d_map_b);
         cudaFree(c->d_phi_table);
+        cudaFree(c->d_mask_spheres);
         cudaFree(c->d_self_pairs);
         cudaFree(c->d_cmin);
         if (c->cmin_tex) cudaDestroyTextureObject(c->cmin_tex);
