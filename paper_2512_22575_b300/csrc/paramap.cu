@@ -143,20 +143,22 @@ __global__ void convert_grid_kernel(const float *src, void *dst, size_t n, int d
 // cmin[l][j][i] = min of the 8 corners (i..i+1, j..j+1, l..l+1) of the
 // stored field (cells with a base on the last plane of an axis are never
 // looked up and get 0, i.e. never skipped).
+// Blocks take grid rows (j, l), threads run along x: the index arithmetic
+// is one 32-bit division per row.
 template <typename T>
 __global__ void cell_min_kernel(const T *phi, float *cmin, int nx, int ny, int nz)
 {
-    const size_t n = static_cast<size_t>(nx) * ny * nz;
-    for (size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; id < n;
-         id += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(id % nx);
-        const int j = static_cast<int>((id / nx) % ny);
-        const int l = static_cast<int>(id / (static_cast<size_t>(nx) * ny));
-        if (i >= nx - 1 || j >= ny - 1 || l >= nz - 1) {
+    const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
+    const int rows = ny * nz;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+      const int j = r % ny, l = r / ny;
+      const bool edge_row = j >= ny - 1 || l >= nz - 1;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const size_t id = static_cast<size_t>(r) * nx + i;
+        if (edge_row || i >= nx - 1) {
             cmin[id] = 0.f;
             continue;
         }
-        const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
         float m = grid_load(phi + id);
         m = fminf(m, grid_load(phi + id + 1));
         m = fminf(m, grid_load(phi + id + sy));
@@ -166,6 +168,7 @@ __global__ void cell_min_kernel(const T *phi, float *cmin, int nx, int ny, int n
         m = fminf(m, grid_load(phi + id + sz + sy));
         m = fminf(m, grid_load(phi + id + sz + sy + 1));
         cmin[id] = m;
+      }
     }
 }
 
@@ -518,15 +521,17 @@ int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
 
 pm_status pm::finish_distance_field(pm_ctx *c, cudaStream_t s)
 {
-    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((c->grid_elems + 255) / 256, 8u * c->n_sm));
+    const int rows = c->gd.ny * c->gd.nz;
+    const unsigned blocks = static_cast<unsigned>(std::min(rows, 64 * c->n_sm));
+    const int threads = std::min(256, (c->gd.nx + 31) / 32 * 32);
     if (c->gd.dtype == PM_F32)
-        cell_min_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(c->d_grid), c->d_cmin,
-                                              c->gd.nx, c->gd.ny, c->gd.nz);
+        cell_min_kernel<<<blocks, threads, 0, s>>>(static_cast<const float *>(c->d_grid), c->d_cmin,
+                                                  c->gd.nx, c->gd.ny, c->gd.nz);
     else if (c->gd.dtype == PM_F16)
-        cell_min_kernel<<<blocks, 256, 0, s>>>(static_cast<const __half *>(c->d_grid), c->d_cmin,
-                                              c->gd.nx, c->gd.ny, c->gd.nz);
+        cell_min_kernel<<<blocks, threads, 0, s>>>(static_cast<const __half *>(c->d_grid), c->d_cmin,
+                                                  c->gd.nx, c->gd.ny, c->gd.nz);
     else
-        cell_min_kernel<<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->d_grid),
+        cell_min_kernel<<<blocks, threads, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->d_grid),
                                               c->d_cmin, c->gd.nx, c->gd.ny, c->gd.nz);
     PM_CUDA(c, cudaGetLastError());
     // cell minima into the texture's array
