@@ -415,10 +415,9 @@ def bench_mapping(pm, torch, dev, stream, w, reps=50):
             "map_update_ms": ms_upd, "map_update_voxels_per_s": n_vox / (ms_upd * 1e-3)}
 
 
-def kernel_traffic_bytes():
-    """DRAM bytes (read + write) per launch of the iteration kernel from the
-    committed ncu counters, or None when the kernel sources changed since
-    they were captured."""
+def kernel_counters():
+    """The committed ncu counters of the iteration kernel, or None when the
+    kernel sources changed since they were captured."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "smpc_iteration_kernel_cfg2_counters.json")
     try:
@@ -426,11 +425,18 @@ def kernel_traffic_bytes():
         h = hashlib.sha256()
         for f in rec["sources"]:
             h.update(open(os.path.join(ROOT, f), "rb").read())
-        if h.hexdigest() != rec["sources_sha256"]:
-            return None
-        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+        return rec if h.hexdigest() == rec["sources_sha256"] else None
     except (OSError, KeyError, ValueError):
         return None
+
+
+def kernel_traffic_bytes():
+    """DRAM bytes (read + write) per launch of the iteration kernel from the
+    committed ncu counters, or None when they are stale."""
+    rec = kernel_counters()
+    if rec is None:
+        return None
+    return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
 
 
 def bench_latency_cfg1(pm, torch, dev, stream, reps=200):
@@ -736,6 +742,9 @@ def run_ours(args, rank, world, local):
                 "kernel_timing": f"CUDA events around each iteration kernel on its stream, second timed "
                                  f"pass of {n_count} replans",
                 "flops_per_launch": flops_launch,
+                # the binding unit is instruction issue: share of issue slots busy
+                # in the committed ncu capture (None when stale)
+                "issue_slots_busy_ncu": (kernel_counters() or {}).get("issue_active_frac"),
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
                               f"x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (unit counts and max clock)"}
 
