@@ -71,6 +71,33 @@ def test_edt_scene_grids_match_scipy():
     assert np.array_equal(gpu_edt(occ2).astype(np.int64), ref)
 
 
+def scipy_edt(occ):
+    d = ndimage.distance_transform_edt(occ == 0)
+    return np.rint(d * d).astype(np.int64)
+
+
+@pytest.mark.parametrize("shape,seed", [((6, 10, 300), 7), ((300, 8, 5), 8), ((5, 300, 7), 9)])
+def test_edt_long_lines_take_the_envelope(shape, seed):
+    """Lines over 256 voxels (x, z, then the first pass along y) go through
+    the lower-envelope kernel, the others through the direct passes."""
+    occ = random_occ(shape, 0.002, seed)
+    occ.flat[seed % occ.size] = 1
+    assert np.array_equal(gpu_edt(occ).astype(np.int64), scipy_edt(occ))
+
+
+def test_edt_passes_whose_values_could_reach_2_24_take_the_envelope():
+    """4000 x 900 x 2 voxels: the last (z) pass has short lines, but its
+    inputs can reach 899^2 + 3999^2 > 2^24, so it must not use the FP32
+    direct pass.  One occupied corner voxel makes the far corner's squared
+    distance 3999^2 + 899^2 + 1 > 2^24, where FP32 cannot hold every
+    integer."""
+    occ = np.zeros((2, 900, 4000), np.uint8)
+    occ[0, 0, 0] = 1
+    got = gpu_edt(occ).astype(np.int64)
+    assert got.max() == 3999**2 + 899**2 + 1 > 2**24
+    assert np.array_equal(got, scipy_edt(occ))
+
+
 def test_map_update_gives_the_same_field_as_the_host_transform():
     """Iterations on a field built by pm_map_update equal, bit for bit, those
     on the field built on the host (scipy EDT x res, rounded to float32)."""
