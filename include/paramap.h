@@ -400,9 +400,11 @@ pm_status pm_plan_episode(pm_ctx *ctx, const float *q0, const float *qd0, const 
  * pm_edt_squared: exact squared Euclidean distance transform of an
  *   occupancy grid, in voxel units: d2[v] = min over occupied voxels o of
  *   |v - o|^2, or INT32_MAX when no voxel is occupied.  The separable
- *   three-pass transform (1-D Felzenszwalb-Huttenlocher lower envelope along
- *   y, x, then z), each line gathered by one thread into its own
- *   shared-memory column on the native layout (Sec. III-B).  occ: device
+ *   three-pass transform along y, x, then z on the native layout
+ *   (Sec. III-B): lines up to 256 voxels take a nearest-occupied sweep (first
+ *   pass) or a direct minimum over the line in FP32 (later passes, while
+ *   every value stays below 2^24, which keeps it exact); longer lines take
+ *   the 1-D Felzenszwalb-Huttenlocher lower envelope.  occ: device
  *   uint8 [nz][ny][nx] (non-zero = occupied); d2: device int32 [nz][ny][nx].
  *   Each extent 1..16384.  Enqueued on cuda_stream (NULL:
  *   the legacy default stream); allocates its scratch on that stream.
