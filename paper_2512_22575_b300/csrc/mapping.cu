@@ -139,7 +139,8 @@ cudaError_t run_pass(const void *in, int *out, const EdtPass &ps, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Short lines (n <= kEdtBfMax) take a direct pass instead of the envelope:
+// Short lines (n <= kEdtBfMax) of the x and z passes take a direct pass
+// instead of the envelope:
 // a block stages 32 neighbouring lines as h_i = f_i + i^2 in shared memory,
 // as floats, and every output d(x) = min_i (h_i - 2 x i) + x^2 is one FMA and
 // one min per candidate i.  All values are integers below 2^24 (the caller
@@ -154,9 +155,8 @@ constexpr int kEdtBfPitch = kEdtBfLines + 1;   // shared-memory row pitch (no ba
 constexpr int kEdtBfWarps = 8;
 constexpr int kEdtBfOut = 8;                   // outputs per thread per sweep over the candidates
 
-template <bool FROM_OCC>
 __global__ void __launch_bounds__(kEdtBfWarps * 32)
-edt_pass_direct_kernel(const void *in, int *out, EdtPass ps)
+edt_pass_direct_kernel(const int *in, int *out, EdtPass ps)
 {
     extern __shared__ float s_bf[];
     const int n = ps.n;
@@ -166,8 +166,7 @@ edt_pass_direct_kernel(const void *in, int *out, EdtPass ps)
     const long long line0 = static_cast<long long>(blockIdx.x) * kEdtBfLines;
     auto base_of = [&](long long l) { return (l % ps.na) * ps.sa + (l / ps.na) * ps.sb; };
     auto h_of = [&](long long idx, int i) -> float {
-        if (FROM_OCC) return static_cast<const unsigned char *>(in)[idx] ? static_cast<float>(i * i) : CUDART_INF_F;
-        const int x = static_cast<const int *>(in)[idx];
+        const int x = in[idx];
         return x == kEdtInf ? CUDART_INF_F : static_cast<float>(x) + static_cast<float>(i * i);
     };
     if (ps.se == 1) {
@@ -277,15 +276,14 @@ bool direct_pass_exact(int n, long long bound_in)
     return n <= kEdtBfMax && bound_in + 3 * m * m < (1LL << 24);
 }
 
-template <bool FROM_OCC>
-cudaError_t run_direct_pass(const void *in, int *out, const EdtPass &ps, cudaStream_t s)
+cudaError_t run_direct_pass(const int *in, int *out, const EdtPass &ps, cudaStream_t s)
 {
     const size_t smem = 2 * static_cast<size_t>(ps.n) * kEdtBfPitch * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(edt_pass_direct_kernel<FROM_OCC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = cudaFuncSetAttribute(edt_pass_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int blocks = static_cast<int>((ps.n_lines + kEdtBfLines - 1) / kEdtBfLines);
-    edt_pass_direct_kernel<FROM_OCC><<<blocks, kEdtBfWarps * 32, smem, s>>>(in, out, ps);
+    edt_pass_direct_kernel<<<blocks, kEdtBfWarps * 32, smem, s>>>(in, out, ps);
     return cudaGetLastError();
 }
 
@@ -306,9 +304,9 @@ cudaError_t edt3d(const unsigned char *occ, int nx, int ny, int nz, int *d2, int
     const long long by = static_cast<long long>(ny - 1) * (ny - 1), bx = static_cast<long long>(nx - 1) * (nx - 1);
     cudaError_t e = ny <= kEdtBfMax ? run_occ_sweep(occ, d2, py, s) : run_pass<true>(occ, d2, py, s);
     if (e == cudaSuccess)
-        e = direct_pass_exact(nx, by) ? run_direct_pass<false>(d2, tmp, px, s) : run_pass<false>(d2, tmp, px, s);
+        e = direct_pass_exact(nx, by) ? run_direct_pass(d2, tmp, px, s) : run_pass<false>(d2, tmp, px, s);
     if (e == cudaSuccess)
-        e = direct_pass_exact(nz, by + bx) ? run_direct_pass<false>(tmp, d2, pz, s) : run_pass<false>(tmp, d2, pz, s);
+        e = direct_pass_exact(nz, by + bx) ? run_direct_pass(tmp, d2, pz, s) : run_pass<false>(tmp, d2, pz, s);
     return e;
 }
 
