@@ -496,13 +496,17 @@ pm_status pm_map_update(pm_ctx *c, const uint8_t *occ, int occ_is_device, const 
             const size_t nt = static_cast<size_t>(c->gd.nx - 1) * (c->gd.nx - 1) +
                               static_cast<size_t>(c->gd.ny - 1) * (c->gd.ny - 1) +
                               static_cast<size_t>(c->gd.nz - 1) * (c->gd.nz - 1) + 1;
+            // the metres table is optional: without it the conversion takes the
+            // per-voxel FP64 path
             if (e == cudaSuccess && nt <= kPhiTableMax) {
-                e = cudaMalloc(&c->d_phi_table, nt * sizeof(float));
-                if (e == cudaSuccess) {
+                if (cudaMalloc(&c->d_phi_table, nt * sizeof(float)) == cudaSuccess) {
                     c->phi_table_n = nt;
                     phi_table_kernel<<<static_cast<unsigned>(std::min<size_t>((nt + 255) / 256, 4u * c->n_sm)), 256, 0,
                                        s>>>(c->d_phi_table, nt, static_cast<double>(c->gd.res));
                     e = cudaGetLastError();
+                } else {
+                    c->d_phi_table = nullptr;
+                    cudaGetLastError();
                 }
             }
             if (e != cudaSuccess) {
