@@ -144,6 +144,29 @@ def test_same_alone_and_in_the_mix(insts):
     b.close()
 
 
+def test_results_do_not_depend_on_the_order_of_the_batch(insts):
+    """Permuting the instances (and with them the work queue) leaves every
+    result unchanged bit for bit: an instance's blocks, their roll-outs and
+    its merge are fixed by the plan, which depends on the instances and not
+    on their order."""
+    sub = insts[:8]
+    b = pm.Batch()
+    for x in sub:
+        x.reset()
+    b.run([x.item() for x in sub], n_iters=2)
+    torch.cuda.synchronize()
+    first = [(x.U.cpu().numpy().copy(), x.S.cpu().numpy().copy()) for x in sub]
+    perm = [7, 2, 5, 0, 3, 6, 1, 4]
+    for x in sub:
+        x.reset()
+    b.run([sub[i].item() for i in perm], n_iters=2)
+    torch.cuda.synchronize()
+    for x, (U, S) in zip(sub, first):
+        assert np.array_equal(x.U.cpu().numpy(), U), (x.K, x.H)
+        assert np.array_equal(x.S.cpu().numpy(), S), (x.K, x.H)
+    b.close()
+
+
 def test_batch_small_instances_match_oracle(insts):
     small = [x for x in insts if x.K <= 512][:3]
     assert small
