@@ -866,24 +866,22 @@ pm_status pm_smpc_iterate(pm_ctx *c, const float *q0, const float *qd0, const fl
     cudaStream_t s = pick_stream(c, cuda_stream);
     st = ensure_capacity(c, K, H, 1);
     if (st != PM_OK) return st;
+    // a host U travels with the inputs through the staging slot
     CallInputs in{};
-    st = stage_inputs(c, s, q0, qd0, T_goal, sigma, in);
+    SlotIO io;
+    st = stage_inputs(c, s, q0, qd0, T_goal, sigma, in, dU ? nullptr : U, H * kNJ, &io);
     if (st != PM_OK) return st;
-    float *Ud = U;
-    if (!dU) {
-        std::memcpy(c->h_U, U, sizeof(float) * H * kNJ);
-        PM_CUDA(c, cudaMemcpyAsync(c->d_U, c->h_U, sizeof(float) * H * kNJ, cudaMemcpyHostToDevice, s));
-        Ud = c->d_U;
-    }
+    float *Ud = dU ? U : io.d + kSlotOut;
     float *Cd = costs_out ? (dC ? costs_out : c->d_costs) : nullptr;
     st = launch_iteration(c, s, in, Ud, Ud, Cd, K, H, dt, lambda, seed, iter_index, false, nullptr);
     if (st != PM_OK) return st;
-    if (!dU) PM_CUDA(c, cudaMemcpyAsync(c->h_U, c->d_U, sizeof(float) * H * kNJ, cudaMemcpyDeviceToHost, s));
+    if (!dU)
+        PM_CUDA(c, cudaMemcpyAsync(io.h + kSlotOut, Ud, sizeof(float) * H * kNJ, cudaMemcpyDeviceToHost, s));
     if (costs_out && !dC)
         PM_CUDA(c, cudaMemcpyAsync(c->h_out, c->d_costs, sizeof(float) * K, cudaMemcpyDeviceToHost, s));
     if (!dU || (costs_out && !dC)) {
         PM_CUDA(c, cudaStreamSynchronize(s));
-        if (!dU) std::memcpy(U, c->h_U, sizeof(float) * H * kNJ);
+        if (!dU) std::memcpy(U, io.h + kSlotOut, sizeof(float) * H * kNJ);
         if (costs_out && !dC) std::memcpy(costs_out, c->h_out, sizeof(float) * K);
     }
     return PM_OK;
