@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
         job.c0 = s_inst.c0;
         const int C = s_inst.C;
         BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
-                     (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kBatchCMax * kNJ * 32 : nullptr};
+                     (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kBatchCMax * kNJ * 32 : nullptr,
+                     nullptr};
         unsigned ngath = 0;
-        run_block<GT, false, SELF>(s_rc, s_inst.g, st, job, nullptr, C, s_inst.L, s_inst.P, w.y, sm, ngath);
+        run_block<GT, false, SELF, false>(s_rc, s_inst.g, st, job, nullptr, C, s_inst.L, s_inst.P, w.y, sm, ngath);
     }
 }
 

@@ -312,13 +312,17 @@ struct BlockSmem {
     float *blk;                 // [C*L*P*7] block accumulator
     float *wm, *wz;             // [kWarps]
     float *self;                // [kWarps][self_slots][32] when the self term is on, else null
+    float *qs;                  // [kWarps][C][kStageFloats][32]: q, qd, control cost per step (STAGE)
 };
+
+// Floats staged per step: q, qd and the control cost.
+constexpr int kStageFloats = 2 * kNJ + 1;
 
 // Local block lb (of job.nb) of an instance: its roll-out tiles, then its
 // block partial (m_b, z_b, acc_b) into job.part.  Tile shape (C, L, P) as
 // described at the top of this file; called by every thread of the block.
 // With constant arguments (the single-instance kernel) the shape folds away.
-template <typename GT, bool TRACE, bool SELF>
+template <typename GT, bool TRACE, bool SELF, bool STAGE>
 __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst &g,
                                           const InstanceState &st, const TileJob &job,
                                           float *trace, const int C, const int L, const int P,
@@ -415,10 +419,35 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25),
         // then, on lane 0 of tile c0_tile, the k = 0 pass
         const bool c0_lane = with_c0 && tile == c0_tile && seg == 0 && sl == 0 && half == 0;
+        // With STAGE, every step's q, qd and control cost go to shared memory
+        // first, so that the scan state is dead before the kinematics (fewer
+        // registers at their peak, more resident warps); the k = 0 pass then
+        // runs through the same code as the steps.
         float lsum = 0.f, lcomp = 0.f;
         float runU[kNJ], runB[kNJ];
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) { runU[j] = 0.f; runB[j] = B0[j]; }
+        if (STAGE) {
+#pragma unroll 1
+            for (int s = 0; s < C; ++s) {
+                const int k = kbase + sl * C + s;
+                if (!(active && k < H)) break;
+                float u[kNJ];
+                float *qs = sm.qs + ((warp * C + s) * kStageFloats) * 32 + lane;
+                const float kp_dt = static_cast<float>(k + 1) * dt;
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) {
+                    u[j] = __ldg(job.Ubar + k * kNJ + j) + sm.eps[E(warp, s, j) + lane];
+                    runU[j] += u[j];
+                    const float A = A0[j] + runU[j];           // A_{k+1}
+                    runB[j] += A;                               // B_{k+1}
+                    qs[j * 32] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
+                    qs[(kNJ + j) * 32] = fmaf(dt, A, st.qd0[j]);
+                }
+                float *tr_u = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols : nullptr;
+                qs[(2 * kNJ) * 32] = control_cost<TRACE>(rc, u, tr_u);
+            }
+        }
 #pragma unroll 1
         for (int s = 0; s <= C; ++s) {
             const bool extra = (s == C);
@@ -430,8 +459,18 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 s = C - 1;          // no more steps: on to the extra pass
                 continue;
             }
-            float u[kNJ], q[kNJ], qd[kNJ];
-            if (!extra) {
+            float q[kNJ], qd[kNJ], cc = 0.f;
+            float *tr_x = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k + 1) * kTraceCols : nullptr;
+            if (extra) {
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) { q[j] = st.q0[j]; qd[j] = st.qd0[j]; }
+            } else if (STAGE) {
+                const float *qs = sm.qs + ((warp * C + s) * kStageFloats) * 32 + lane;
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) { q[j] = qs[j * 32]; qd[j] = qs[(kNJ + j) * 32]; }
+                cc = qs[(2 * kNJ) * 32];
+            } else {
+                float u[kNJ];
                 const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
@@ -442,14 +481,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                     qd[j] = fmaf(dt, A, st.qd0[j]);
                     q[j] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
                 }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kNJ; ++j) { u[j] = 0.f; q[j] = st.q0[j]; qd[j] = st.qd0[j]; }
-            }
-            float *tr_u = nullptr, *tr_x = nullptr;
-            if (TRACE) {
-                tr_u = trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols;
-                tr_x = tr_u + kTraceCols;
+                float *tr_u = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols : nullptr;
+                cc = control_cost<TRACE>(rc, u, tr_u);
             }
             const unsigned ng0 = ngath;
             const float sc = state_cost<GT, TRACE, SELF>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp);
@@ -457,7 +490,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 ngath = ng0;        // lookups of the roll-outs only
                 *job.c0 = sc;
             } else {
-                kahan_add(lsum, lcomp, control_cost<TRACE>(rc, u, tr_u) + sc);
+                kahan_add(lsum, lcomp, cc + sc);
             }
         }
 
@@ -560,7 +593,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 // steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
 // totals of the first half and their partial costs through shared memory.
 template <int C, int L, int P, typename GT, bool TRACE, bool SELF>
-__global__ void __launch_bounds__(kBlock, 5)
+__global__ void __launch_bounds__(kBlock, C == 1 ? 6 : 5)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
                       const __grid_constant__ IterArgs a)
 {
@@ -573,6 +606,9 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     __shared__ float s_state[kStateFloats];
     __shared__ float s_blk[C * L * P * kNJ];   // block accumulator [k][j], k < C*L*P (>= H, host-checked)
     __shared__ float s_wm[kWarps], s_wz[kWarps];
+    // one-step shapes stage their steps' states (run_block, STAGE)
+    constexpr bool kStage = (C == 1);
+    __shared__ float s_qs[kStage ? kWarps * kStageFloats * 32 : 1];
 
     grid_dependency_prologue();
     load_state(a.in, s_state);
@@ -593,9 +629,9 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     job.inv_lambda = a.inv_lambda;
     job.noise_dtype = a.noise_dtype;
     BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
-                 (SELF && rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr};
+                 (SELF && rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr, s_qs};
     unsigned ngath = 0;
-    run_block<GT, TRACE, SELF>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
+    run_block<GT, TRACE, SELF, kStage>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
     if (!TRACE && a.gathers) {
         const int lane = threadIdx.x & 31;
         unsigned n = ngath;
