@@ -665,6 +665,39 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         for (int s = 0; s < rb->n_spheres; ++s) cnt += (rb->sphere_link[s] < L);
         r.link_begin[L] = cnt;
     }
+    // frames whose sphere offsets lie on one line through the origin: the
+    // direction w is the longest offset, lambda_s = o_s . w / |w|^2, and the
+    // line is taken when every offset is within 1e-7 |w| (about one float32
+    // ulp) of lambda_s w
+    for (int j = 0; j < n; ++j) {
+        const int b = r.link_begin[j + 1], e = r.link_begin[j + 2];
+        double w[3] = {0.0, 0.0, 0.0}, ww = 0.0;
+        for (int i = b; i < e; ++i) {
+            double o2 = 0.0;
+            for (int k = 0; k < 3; ++k) o2 += static_cast<double>(r.sph_off[i][k]) * r.sph_off[i][k];
+            if (o2 > ww) {
+                ww = o2;
+                for (int k = 0; k < 3; ++k) w[k] = r.sph_off[i][k];
+            }
+        }
+        bool line = e > b;
+        for (int i = b; i < e && line; ++i) {
+            double lam = 0.0;
+            if (ww > 0.0) {
+                for (int k = 0; k < 3; ++k) lam += static_cast<double>(r.sph_off[i][k]) * w[k];
+                lam /= ww;
+            }
+            double d2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double dk = r.sph_off[i][k] - lam * w[k];
+                d2 += dk * dk;
+            }
+            line = d2 <= 1e-14 * ww + 1e-24;
+            r.sph_lambda[i] = static_cast<float>(lam);
+        }
+        r.link_line[j] = line ? 1 : 0;
+        for (int k = 0; k < 3; ++k) r.link_w[j][k] = static_cast<float>(w[k]);
+    }
     for (int j = 0; j < n; ++j) {
         r.ca[j] = static_cast<float>(std::cos(static_cast<double>(rb->alpha[j])));
         r.sa[j] = static_cast<float>(std::sin(static_cast<double>(rb->alpha[j])));

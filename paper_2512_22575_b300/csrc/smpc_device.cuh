@@ -38,6 +38,12 @@ struct RobotConst {
     float qdd_lo[kNJ], qdd_hi[kNJ];
     float sph_off[kMaxSpheres][3];
     float sph_r[kMaxSpheres];
+    // A frame whose spheres' offsets lie on one line through its origin,
+    // o_s = lambda_s w (up to one float32 ulp of |w|), has link_line = 1: its
+    // centres are t + lambda_s R w, three FMAs each in grid coordinates.
+    unsigned char link_line[kNJ];
+    float link_w[kNJ][3];
+    float sph_lambda[kMaxSpheres];
     // A sphere whose cell has all 8 corners above sph_skip[s] has
     // d_act - (phi - r) < 0 for every point of the cell, even after FP32
     // rounding of the interpolation: its collision term is exactly 0.
@@ -248,14 +254,20 @@ __device__ __forceinline__ int cell(float g, float gmax, int n, float &f)
 // Cell of a point: base voxel offset and fractions (clamped, Eq. 17 lookup).
 struct Cell { int base; float fx, fy, fz; };
 
-__device__ __forceinline__ Cell locate(const GridConst &g, f3 p)
+// Cell of grid coordinates (gx, gy, gz) = p / res + b.
+__device__ __forceinline__ Cell locate_grid(const GridConst &g, float gx, float gy, float gz)
 {
     Cell c;
-    const int ix = cell(fmaf(p.x, g.inv_res, g.bx), g.mx, g.nx, c.fx);
-    const int iy = cell(fmaf(p.y, g.inv_res, g.by), g.my, g.ny, c.fy);
-    const int iz = cell(fmaf(p.z, g.inv_res, g.bz), g.mz, g.nz, c.fz);
+    const int ix = cell(gx, g.mx, g.nx, c.fx);
+    const int iy = cell(gy, g.my, g.ny, c.fy);
+    const int iz = cell(gz, g.mz, g.nz, c.fz);
     c.base = (iz * g.ny + iy) * g.nx + ix;
     return c;
+}
+
+__device__ __forceinline__ Cell locate(const GridConst &g, f3 p)
+{
+    return locate_grid(g, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by), fmaf(p.z, g.inv_res, g.bz));
 }
 
 // floor(g) + 1/2 for g in [0, 2^23): adding 2^23 rounded down leaves

@@ -92,9 +92,47 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 // located exactly and interpolated from their 8 corners.
 template <typename GT, bool SELF>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
-                                          const Frame &F, int b, int e, unsigned &ngath, float *sp)
+                                          const Frame &F, int j, int b, int e, unsigned &ngath, float *sp)
 {
     float env = 0.f;
+    if (rc.link_line[j]) {
+        // spheres on a line through the frame origin: grid coordinates
+        // gt + lambda_s gv, gt of the origin and gv of the rotated direction
+        const f3 v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
+        const f3 gt = mk(fmaf(F.t.x, g.inv_res, g.bx), fmaf(F.t.y, g.inv_res, g.by), fmaf(F.t.z, g.inv_res, g.bz));
+        const f3 gv = scale(g.inv_res, v);
+        for (int s0 = b; s0 < e; s0 += kSphereBatch) {
+            float mn[kSphereBatch];
+#pragma unroll
+            for (int i = 0; i < kSphereBatch; ++i) {
+                const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
+                const float lam = rc.sph_lambda[s];
+                if (SELF && sp) {                   // kept for the self-collision term
+                    const f3 p = axpy(lam, v, F.t);
+                    sp[(3 * s) * 32] = p.x;
+                    sp[(3 * s + 1) * 32] = p.y;
+                    sp[(3 * s + 2) * 32] = p.z;
+                }
+                mn[i] = tex3D<float>(g.cmin_tex, cell_centre(fmaf(lam, gv.x, gt.x)), cell_centre(fmaf(lam, gv.y, gt.y)),
+                                     cell_centre(fmaf(lam, gv.z, gt.z)));
+            }
+#pragma unroll
+            for (int i = 0; i < kSphereBatch; ++i) {
+                const int s = s0 + i;
+                if (s < e && !(mn[i] > rc.sph_skip[s])) {
+                    ++ngath;
+                    const float lam = rc.sph_lambda[s];
+                    const Cell c = locate_grid(g, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
+                    float vv[8];
+                    corners<GT>(g, c.base, vv);
+                    const float phi = interpolate(vv, c.fx, c.fy, c.fz);
+                    const float dl = fmaxf(rc.d_act - (phi - rc.sph_r[s]), 0.f);
+                    env = fmaf(dl, dl, env);
+                }
+            }
+        }
+        return env;
+    }
     for (int s0 = b; s0 < e; s0 += kSphereBatch) {
         float mn[kSphereBatch];
 #pragma unroll
@@ -232,7 +270,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], qr[0] + rc.th0[j]);
 #pragma unroll
         for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
-        if (!terminal) env += link_env<GT, SELF>(rc, g, F, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
+        if (!terminal) env += link_env<GT, SELF>(rc, g, F, j, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
         if (SELF && sp) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
             const int t = 3 * rc.n_spheres + 3 * j;
