@@ -420,7 +420,7 @@ pm_status pm_plan_episode(pm_ctx *ctx, const float *q0, const float *qd0, const 
  *   is copied, masked at q_mask if it is not NULL (pm_robot_mask with
  *   inflate), transformed on the GPU (pm_edt_squared), converted to metres
  *   phi = res sqrt(d2) (rounded once from FP64 to the field's storage type;
- *   1e10 m if nothing is occupied) and installed with its cell minima, as
+ *   1e10 m if nothing is occupied) and installed with its skip bounds, as
  *   pm_set_distance_field does.  Enqueued on cuda_stream (NULL: the
  *   context's); the scratch (1 + 8 bytes per voxel) is allocated on first
  *   use.  Iterations reading the field on other streams must not overlap it.

@@ -140,35 +140,68 @@ __global__ void convert_grid_kernel(const float *src, void *dst, size_t n, int d
     }
 }
 
-// cmin[l][j][i] = min of the 8 corners (i..i+1, j..j+1, l..l+1) of the
-// stored field (cells with a base on the last plane of an axis are never
-// looked up and get 0, i.e. never skipped).
-// Blocks take grid rows (j, l), threads run along x: the index arithmetic
-// is one 32-bit division per row.
+// Skip bound of cell (i, j, l): the minimum of the stored field over the
+// voxels [max(i-1, 0), i+1] x [max(j-1, 0), j+1] x [max(l-1, 0), l+1],
+// i.e. over the 8 corners of the cell and of its lower neighbours.  The
+// iteration kernel fetches it through the texture unit at the raw grid
+// coordinate: the unit quantises the coordinate to fixed point, and a
+// monotone rounding with an error below one texel never lands below the
+// point's own cell and at most one cell above it on each axis, so the
+// fetched texel's bound covers the point's cell.  Only the
+// (nx-1) x (ny-1) x (nz-1) cells are written (the texture holds no others).
+// A warp takes 30 cells along x (lanes 1..30; lanes 0 and 31 hold the
+// neighbouring voxels), one row j and kBoundZ planes.  Each lane loads its
+// voxel column over rows j-1..j+1 on the kBoundZ + 2 planes it needs, all
+// before the first minimum (one round trip to memory), takes the row
+// minimum per plane, the x window from its neighbours by shuffles and then
+// the z window: about 4 loads per cell.
+constexpr int kBoundZ = 8;
+
 template <typename T>
 __global__ void cell_min_kernel(const T *phi, float *cmin, int nx, int ny, int nz)
 {
+    const int lane = threadIdx.x & 31;
+    const int cx = nx - 1, cy = ny - 1, cz = nz - 1;
+    const int nxs = (cx + 29) / 30, nzc = (cz + kBoundZ - 1) / kBoundZ;
+    const long long items = static_cast<long long>(nxs) * cy * nzc;
     const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
-    const int rows = ny * nz;
-    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-      const int j = r % ny, l = r / ny;
-      const bool edge_row = j >= ny - 1 || l >= nz - 1;
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const size_t id = static_cast<size_t>(r) * nx + i;
-        if (edge_row || i >= nx - 1) {
-            cmin[id] = 0.f;
-            continue;
+    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    for (long long it = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; it < items;
+         it += warps) {
+        const int xs = static_cast<int>(it % nxs);
+        const long long rest = it / nxs;
+        const int j = static_cast<int>(rest % cy), zc = static_cast<int>(rest / cy);
+        const int i = xs * 30 + lane - 1;
+        const bool in_x = i >= 0 && i < nx;
+        const int l_begin = zc * kBoundZ, l_end = min(l_begin + kBoundZ, cz);
+        // plane l_begin - 1 + q for q = 0 .. kBoundZ + 1 (planes below 0 or
+        // above l_end are not needed and stay +inf); rows max(j-1, 0), j, j+1
+        const size_t r0 = static_cast<size_t>(max(j - 1, 0)) * sy, r1 = j * sy, r2 = (j + 1) * sy;
+        float v[kBoundZ + 2][3];
+#pragma unroll
+        for (int q = 0; q < kBoundZ + 2; ++q) {
+            const int ll = l_begin - 1 + q;
+            const bool in = in_x && ll >= 0 && ll <= l_end;
+            const T *col = phi + (in ? ll * sz + i : 0);
+            v[q][0] = in ? grid_load(col + r0) : CUDART_INF_F;
+            v[q][1] = in ? grid_load(col + r1) : CUDART_INF_F;
+            v[q][2] = in ? grid_load(col + r2) : CUDART_INF_F;
         }
-        float m = grid_load(phi + id);
-        m = fminf(m, grid_load(phi + id + 1));
-        m = fminf(m, grid_load(phi + id + sy));
-        m = fminf(m, grid_load(phi + id + sy + 1));
-        m = fminf(m, grid_load(phi + id + sz));
-        m = fminf(m, grid_load(phi + id + sz + 1));
-        m = fminf(m, grid_load(phi + id + sz + sy));
-        m = fminf(m, grid_load(phi + id + sz + sy + 1));
-        cmin[id] = m;
-      }
+        float w[kBoundZ + 2];
+#pragma unroll
+        for (int q = 0; q < kBoundZ + 2; ++q) {
+            const float my = fminf(v[q][0], fminf(v[q][1], v[q][2]));
+            const float left = __shfl_up_sync(0xffffffffu, my, 1);
+            const float right = __shfl_down_sync(0xffffffffu, my, 1);
+            w[q] = fminf(my, fminf(lane > 0 ? left : CUDART_INF_F, lane < 31 ? right : CUDART_INF_F));
+        }
+        if (lane >= 1 && lane <= 30 && i < cx) {
+#pragma unroll
+            for (int t = 0; t < kBoundZ; ++t) {
+                const int l = l_begin + t;     // planes l-1, l, l+1 are w[t], w[t+1], w[t+2]
+                if (l < l_end) cmin[l * sz + j * sy + i] = fminf(w[t], fminf(w[t + 1], w[t + 2]));
+            }
+        }
     }
 }
 
@@ -521,9 +554,10 @@ int pm::resident_blocks_per_sm(const void *fn, int block, size_t smem)
 
 pm_status pm::finish_distance_field(pm_ctx *c, cudaStream_t s)
 {
-    const int rows = c->gd.ny * c->gd.nz;
-    const unsigned blocks = static_cast<unsigned>(std::min(rows, 64 * c->n_sm));
-    const int threads = std::min(256, (c->gd.nx + 31) / 32 * 32);
+    const long long items = static_cast<long long>((c->gd.nx - 1 + 29) / 30) * (c->gd.ny - 1) *
+                            ((c->gd.nz - 1 + kBoundZ - 1) / kBoundZ);
+    const int threads = 128;
+    const unsigned blocks = static_cast<unsigned>(std::min<long long>((items + 3) / 4, 32LL * c->n_sm));
     if (c->gd.dtype == PM_F32)
         cell_min_kernel<<<blocks, threads, 0, s>>>(static_cast<const float *>(c->d_grid), c->d_cmin,
                                                   c->gd.nx, c->gd.ny, c->gd.nz);

@@ -78,12 +78,13 @@ __host__ __device__ constexpr int self_slots(int n_spheres) { return 3 * n_spher
 
 struct GridConst {
     const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16
-    const float *cmin;            // [nz][ny][nx]: min of the 8 corners of the cell
-                                  // with base voxel (i, j, l), as the lookup reads them
+    const float *cmin;            // [nz][ny][nx]: skip bound of the cell with base voxel
+                                  // (i, j, l): min of the field over the voxels
+                                  // [i-1, i+1] x [j-1, j+1] x [l-1, l+1] (clamped at 0)
     // cmin of the (nx-1) x (ny-1) x (nz-1) cells as a point-sampled texture
-    // (clamped addressing, unnormalised coordinates), fetched at the centre
-    // of the cell (see cell_centre), so the texture unit's fixed-point
-    // coordinates cannot round into a neighbouring cell.
+    // (clamped addressing, unnormalised coordinates), fetched at the raw grid
+    // coordinate: the texture unit's fixed-point rounding of a coordinate
+    // may reach the next cell up, whose bound also covers this one.
     cudaTextureObject_t cmin_tex;
     int nx, ny, nz;
     float inv_res;
@@ -268,30 +269,6 @@ __device__ __forceinline__ Cell locate_grid(const GridConst &g, float gx, float 
 __device__ __forceinline__ Cell locate(const GridConst &g, f3 p)
 {
     return locate_grid(g, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by), fmaf(p.z, g.inv_res, g.bz));
-}
-
-// floor(g) + 1/2 for g in [0, 2^23): adding 2^23 rounded down leaves
-// 2^23 + floor(g), and the subtraction is exact.  Below 0 the result is at
-// most 1/2 and above 2^23 it is huge, so the texture's clamp to the first or
-// last cell matches the clamp of cell().
-__device__ __forceinline__ float cell_centre(float g)
-{
-    return __fadd_rd(g, 8388608.0f) - 8388607.5f;
-}
-
-// Index of a coordinate's cell only (no fraction): same clamp and floor as cell().
-__device__ __forceinline__ int cell_index(float g, float gmax, int n)
-{
-    return min(static_cast<int>(fminf(fmaxf(g, 0.0f), gmax)), n - 2);
-}
-
-// Base voxel offset of a point's cell, as locate() finds it.
-__device__ __forceinline__ int cell_base(const GridConst &g, f3 p)
-{
-    const int ix = cell_index(fmaf(p.x, g.inv_res, g.bx), g.mx, g.nx);
-    const int iy = cell_index(fmaf(p.y, g.inv_res, g.by), g.my, g.ny);
-    const int iz = cell_index(fmaf(p.z, g.inv_res, g.bz), g.mz, g.nz);
-    return (iz * g.ny + iy) * g.nx + ix;
 }
 
 // The 8 corner samples of a cell, in the order (x, y, z) = 000, 100, 010,

@@ -86,10 +86,11 @@ __device__ __forceinline__ float control_cost(const RobotConst &rc, const float 
 }
 
 // sum over spheres s in [b, e) of frame F of max(0, d_act - (phi(p_s) - r_s))^2
-// (Eqs. 17, 19).  The cell-corner minima of four spheres are fetched
-// together through the texture unit; a sphere whose minimum is above its
-// skip threshold contributes exactly 0 and needs no gathers, the others are
-// located exactly and interpolated from their 8 corners.
+// (Eqs. 17, 19).  The skip bounds of four spheres (a lower bound of the 8
+// corners of each sphere's cell) are fetched together through the texture
+// unit; a sphere whose bound is above its skip threshold contributes
+// exactly 0 and needs no gathers, the others are located exactly and
+// interpolated from their 8 corners.
 template <typename GT, bool SELF>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
                                           const Frame &F, int j, int b, int e, unsigned &ngath, float *sp)
@@ -113,8 +114,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                     sp[(3 * s + 1) * 32] = p.y;
                     sp[(3 * s + 2) * 32] = p.z;
                 }
-                mn[i] = tex3D<float>(g.cmin_tex, cell_centre(fmaf(lam, gv.x, gt.x)), cell_centre(fmaf(lam, gv.y, gt.y)),
-                                     cell_centre(fmaf(lam, gv.z, gt.z)));
+                mn[i] = tex3D<float>(g.cmin_tex, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
             }
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
@@ -144,8 +144,8 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                 sp[(3 * s + 1) * 32] = p.y;
                 sp[(3 * s + 2) * 32] = p.z;
             }
-            mn[i] = tex3D<float>(g.cmin_tex, cell_centre(fmaf(p.x, g.inv_res, g.bx)),
-                                 cell_centre(fmaf(p.y, g.inv_res, g.by)), cell_centre(fmaf(p.z, g.inv_res, g.bz)));
+            mn[i] = tex3D<float>(g.cmin_tex, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by),
+                                 fmaf(p.z, g.inv_res, g.bz));
         }
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {

@@ -328,6 +328,36 @@ def test_trace_matches_oracle_terms(cfg1):
         assert np.allclose(tr[m], ref, rtol=1e-4, atol=1e-7)
 
 
+def test_skip_is_exact_on_a_rough_field(cfg1):
+    """The skip bounds stay exact on a field far from a distance field: every
+    voxel scaled by its own random factor in [0.25, 0.75], so neighbouring
+    voxels jump by up to a factor of three, and the arm comes close enough
+    that about half the lookups are gathered.  The collision term of every
+    step matches the oracle's full evaluation, and the iteration both skips
+    and gathers lookups on this field."""
+    sc = cfg1[3]
+    rng = np.random.default_rng(7)
+    phi = (sc.phi * rng.uniform(0.25, 0.75, sc.phi.shape)).astype(np.float32)
+    G = oracle.Grid(sc.grid_desc, phi)
+    p = pm.Planner(sc.robot, sc.grid_desc, sc.cp)
+    p.set_distance_field(phi)
+    K, H = 64, 32
+    U = np.zeros((H, 7), np.float32)
+    p.profile_enable(pm.PM_PROFILE_GATHERS)
+    p.profile_gathers(reset=True)
+    p.smpc_iterate(sc.q0, sc.qd0, sc.T, U.copy(), K, 0.02, 0.05, SIGMA, 5, 0)
+    n = p.profile_gathers(reset=True)
+    tr = torch.zeros((K, H + 1, 8), dtype=torch.float32, device=DEV)
+    p.rollout_trace(sc.q0, sc.qd0, sc.T, U, K, 0.02, SIGMA, 5, 0, tr)
+    p.close()
+    assert 0 < n < K * (H - 1) * len(sc.robot["sphere_radius"])
+    tr = tr.cpu().numpy()
+    eps = oracle.eps_tensor(5, 0, K, H, SIGMA)
+    for m in range(K):
+        _, ref = oracle.rollout_cost(sc.R, G, sc.C, sc.q0, sc.qd0, sc.T, U + eps[m], 0.02, trace=True)
+        assert np.allclose(tr[m, 1:H, 1], ref[1:H, 1], rtol=1e-4, atol=1e-7), m
+
+
 # ------------------------------------------------------------ full-size cfg2
 @pytest.fixture(scope="module")
 def cfg2():
