@@ -712,14 +712,18 @@ def run_ours(args, rank, world, local):
     Uh[:] = 0
     if world > 1:
         torch.distributed.barrier()
+    t_call = np.empty(n_e2e + 1)
     t0 = time.perf_counter()
+    t_call[0] = t0
     for i in range(n_e2e):
         r = i % EPISODE
         if r == 0:
             qh[:] = sc["q0"]; qdh[:] = sc["qd0"]; Uh[:] = 0
         planner.replan(qh, qdh, Ts_host[r], Uh, K, iters, dt, lam, sigma, seed, r,
                        u0_out=u0h, best_cost=besth)
+        t_call[i + 1] = time.perf_counter()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_call_ms = np.diff(t_call) * 1e3
     e2e_value = whole_job_value(K * H * iters * n_e2e, world, e2e_s)
     state_bytes = 36 * 4                    # q0, qd0, R_g, t_g, sigma as staged
     h2d = state_bytes + H * 7 * 4           # + U
@@ -757,7 +761,10 @@ def run_ours(args, rank, world, local):
                       "p99": float(np.percentile(step_ms, 99)), "mean": float(step_ms.mean())},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": n_e2e,
-                "ms_per_step": 1e3 * e2e_s / n_e2e},
+                "ms_per_step": 1e3 * e2e_s / n_e2e,
+                "call_ms": {"p50": float(np.percentile(e2e_call_ms, 50)),
+                            "p99": float(np.percentile(e2e_call_ms, 99)),
+                            "max": float(e2e_call_ms.max())}},
         # per replan: n_iters x (iteration kernel + merge) + the replan step
         "gpu_launches": args.steps * (2 * iters + 1),
         "roofline": roofline,

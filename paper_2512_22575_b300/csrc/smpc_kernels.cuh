@@ -116,10 +116,16 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                 }
                 mn[i] = tex3D<float>(g.cmin_tex, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
             }
+            // one branch for the batch: spheres to gather, as bits
+            unsigned need = 0u;
+#pragma unroll
+            for (int i = 0; i < kSphereBatch; ++i)
+                need |= (s0 + i < e && !(mn[i] > rc.sph_skip[min(s0 + i, e - 1)])) ? (1u << i) : 0u;
+            if (need)
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
                 const int s = s0 + i;
-                if (s < e && !(mn[i] > rc.sph_skip[s])) {
+                if (need & (1u << i)) {
                     ++ngath;
                     const float lam = rc.sph_lambda[s];
                     const Cell c = locate_grid(g, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
@@ -147,10 +153,15 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             mn[i] = tex3D<float>(g.cmin_tex, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by),
                                  fmaf(p.z, g.inv_res, g.bz));
         }
+        unsigned need = 0u;
+#pragma unroll
+        for (int i = 0; i < kSphereBatch; ++i)
+            need |= (s0 + i < e && !(mn[i] > rc.sph_skip[min(s0 + i, e - 1)])) ? (1u << i) : 0u;
+        if (need)
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = s0 + i;
-            if (s < e && !(mn[i] > rc.sph_skip[s])) {
+            if (need & (1u << i)) {
                 // the few spheres near an obstacle: locate again with fractions
                 ++ngath;
                 const Cell c = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
