@@ -749,6 +749,10 @@ def run_ours(args, rank, world, local):
                 # the binding unit is instruction issue: share of issue slots busy
                 # in the committed ncu capture (None when stale)
                 "issue_slots_busy_ncu": (kernel_counters() or {}).get("issue_active_frac"),
+                # FP32 work the kernel executes per roll-out step (2 FFMA + FADD +
+                # FMUL, ncu), against the fixed algorithmic count `achieved` uses
+                "executed_fp32_flops_per_step_ncu": (kernel_counters() or {}).get("fp32_flop_equiv_per_step"),
+                "algorithmic_flops_per_step": flops_launch / (K * H),
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
                               f"x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (unit counts and max clock)"}
 

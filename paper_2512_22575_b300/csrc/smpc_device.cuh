@@ -21,6 +21,9 @@ namespace pm {
 
 constexpr int kNJ = 7;            // joints of the compiled kinematic chain
 constexpr int kMaxSpheres = 64;
+// zero entries after the sphere tables: a batch of spheres may read up to
+// kSpherePad - 1 entries past a frame's last sphere (masked, never used)
+constexpr int kSpherePad = 4;
 constexpr int kMaxHorizon = 256;
 constexpr int kMaxSelfGroups = (kNJ * (kNJ + 1)) / 2;   // frame pairs (a <= b) of the self-collision set
 constexpr int kMaxSelfPairs = 4096;
@@ -36,19 +39,19 @@ struct RobotConst {
     float q_lo[kNJ], q_hi[kNJ];   // tightened boxes of Eq. 21
     float qd_lo[kNJ], qd_hi[kNJ];
     float qdd_lo[kNJ], qdd_hi[kNJ];
-    float sph_off[kMaxSpheres][3];
+    float sph_off[kMaxSpheres + kSpherePad][3];
     float sph_r[kMaxSpheres];
     // A frame whose spheres' offsets lie on one line through its origin,
     // o_s = lambda_s w (up to one float32 ulp of |w|), has link_line = 1: its
     // centres are t + lambda_s R w, three FMAs each in grid coordinates.
     unsigned char link_line[kNJ];
     float link_w[kNJ][3];
-    float sph_lambda[kMaxSpheres];
+    float sph_lambda[kMaxSpheres + kSpherePad];
     // A sphere whose cell has all 8 corners above sph_skip[s] has
     // d_act - (phi - r) < 0 for every point of the cell, even after FP32
     // rounding of the interpolation: its collision term is exactly 0.
     // sph_skip[s] = (d_act + r_s)(1 + 1e-6) + 1e-6, rounded up.
-    float sph_skip[kMaxSpheres];
+    float sph_skip[kMaxSpheres + kSpherePad];
     float Q[6], QH[6];
     float w_env, d_act, w_self;
     float w_q, w_qd, w_qdd, w_s, w_ns;

@@ -39,6 +39,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kMaxBlocks = 4096;
 constexpr int kTraceCols = 8;   // pose, env, self, lim_q, lim_qd, lim_qdd, smooth, ns
 constexpr int kSphereBatch = 4;
+static_assert(kSphereBatch - 1 <= kSpherePad, "a batch reads past a frame's spheres into the zero padding");
 
 // Dynamic shared memory of an iteration kernel with C steps per lane: the
 // perturbations and the soft-min accumulators, [kWarps][C][7][32] each.
@@ -106,9 +107,9 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             float mn[kSphereBatch];
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
-                const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
+                const int s = s0 + i;               // past e: zero padding, masked below
                 const float lam = rc.sph_lambda[s];
-                if (SELF && sp) {                   // kept for the self-collision term
+                if (SELF && sp && i < e - s0) {     // kept for the self-collision term
                     const f3 p = axpy(lam, v, F.t);
                     sp[(3 * s) * 32] = p.x;
                     sp[(3 * s + 1) * 32] = p.y;
@@ -120,7 +121,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             unsigned need = 0u;
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i)
-                need |= (s0 + i < e && !(mn[i] > rc.sph_skip[min(s0 + i, e - 1)])) ? (1u << i) : 0u;
+                need |= (i < e - s0 && !(mn[i] > rc.sph_skip[s0 + i])) ? (1u << i) : 0u;
             if (need)
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
@@ -143,9 +144,9 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         float mn[kSphereBatch];
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
-            const int s = min(s0 + i, e - 1);   // repeats the last sphere; masked below
+            const int s = s0 + i;               // past e: zero padding, masked below
             const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-            if (SELF && sp) {                   // kept for the self-collision term
+            if (SELF && sp && i < e - s0) {     // kept for the self-collision term
                 sp[(3 * s) * 32] = p.x;
                 sp[(3 * s + 1) * 32] = p.y;
                 sp[(3 * s + 2) * 32] = p.z;
@@ -156,7 +157,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         unsigned need = 0u;
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i)
-            need |= (s0 + i < e && !(mn[i] > rc.sph_skip[min(s0 + i, e - 1)])) ? (1u << i) : 0u;
+            need |= (i < e - s0 && !(mn[i] > rc.sph_skip[s0 + i])) ? (1u << i) : 0u;
         if (need)
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
