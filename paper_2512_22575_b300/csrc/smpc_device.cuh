@@ -165,7 +165,10 @@ __device__ __forceinline__ float word_to_uniform(uint32_t x)
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1)
 {
     const float u0 = word_to_uniform(w0), u1 = word_to_uniform(w1);
-    const float r = sqrtf(-2.0f * logf(u0));
+    // v = -2 ln u0 lies in [1.2e-7, 33.3] (u0 in [2^-24, 1 - 2^-24]), so
+    // v rsqrt(v) needs no special cases: within 3 ulp of sqrt(v)
+    const float v = -2.0f * logf(u0);
+    const float r = v * rsqrtf(v);
     float s, c;
     sincospif(2.0f * u1, &s, &c);
     z0 = r * c;
