@@ -692,7 +692,7 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         for (int k = 0; k < 3; ++k) r.sph_off[i][k] = rb->sphere_offset[3 * s + k];
         r.sph_r[i] = rb->sphere_radius[s];
         const double thr = (static_cast<double>(cp->d_act) + rb->sphere_radius[s]) * (1.0 + 1e-6) + 1e-6;
-        r.sph_skip[i] = std::nextafter(static_cast<float>(thr), INFINITY);
+        r.sph_ls[i].y = std::nextafter(static_cast<float>(thr), INFINITY);
     }
     for (int L = 1; L <= n + 1; ++L) {
         int cnt = 0;
@@ -727,10 +727,13 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
                 d2 += dk * dk;
             }
             line = d2 <= 1e-14 * ww + 1e-24;
-            r.sph_lambda[i] = static_cast<float>(lam);
+            r.sph_ls[i].x = static_cast<float>(lam);
         }
         r.link_line[j] = line ? 1 : 0;
-        for (int k = 0; k < 3; ++k) r.link_w[j][k] = static_cast<float>(w[k]);
+        for (int k = 0; k < 3; ++k) {
+            r.link_w[j][k] = static_cast<float>(w[k]);
+            r.link_wg[j][k] = static_cast<float>(w[k] / static_cast<double>(gd->res));
+        }
     }
     for (int j = 0; j < n; ++j) {
         r.ca[j] = static_cast<float>(std::cos(static_cast<double>(rb->alpha[j])));

@@ -43,15 +43,17 @@ struct RobotConst {
     float sph_r[kMaxSpheres];
     // A frame whose spheres' offsets lie on one line through its origin,
     // o_s = lambda_s w (up to one float32 ulp of |w|), has link_line = 1: its
-    // centres are t + lambda_s R w, three FMAs each in grid coordinates.
+    // centres are t + lambda_s R w, three FMAs each in grid coordinates
+    // (R link_wg, the direction in grid units, is formed once per frame).
     unsigned char link_line[kNJ];
     float link_w[kNJ][3];
-    float sph_lambda[kMaxSpheres + kSpherePad];
-    // A sphere whose cell has all 8 corners above sph_skip[s] has
-    // d_act - (phi - r) < 0 for every point of the cell, even after FP32
-    // rounding of the interpolation: its collision term is exactly 0.
-    // sph_skip[s] = (d_act + r_s)(1 + 1e-6) + 1e-6, rounded up.
-    float sph_skip[kMaxSpheres + kSpherePad];
+    float link_wg[kNJ][3];        // link_w / res: the direction in grid units
+    // sph_ls[s] = (lambda_s, skip threshold of sphere s).  A sphere whose
+    // cell has all 8 corners above its threshold has d_act - (phi - r) < 0
+    // for every point of the cell, even after FP32 rounding of the
+    // interpolation: its collision term is exactly 0.  The threshold is
+    // (d_act + r_s)(1 + 1e-6) + 1e-6, rounded up.
+    float2 sph_ls[kMaxSpheres + kSpherePad];
     float Q[6], QH[6];
     float w_env, d_act, w_self;
     float w_q, w_qd, w_qdd, w_s, w_ns;

@@ -100,15 +100,18 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
     if (rc.link_line[j]) {
         // spheres on a line through the frame origin: grid coordinates
         // gt + lambda_s gv, gt of the origin and gv of the rotated direction
-        const f3 v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
+        const f3 gv = axpy(rc.link_wg[j][2], F.c3, axpy(rc.link_wg[j][1], F.c2, scale(rc.link_wg[j][0], F.c1)));
         const f3 gt = mk(fmaf(F.t.x, g.inv_res, g.bx), fmaf(F.t.y, g.inv_res, g.by), fmaf(F.t.z, g.inv_res, g.bz));
-        const f3 gv = scale(g.inv_res, v);
+        f3 v{};
+        if (SELF && sp) v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
         for (int s0 = b; s0 < e; s0 += kSphereBatch) {
             float mn[kSphereBatch];
+            float2 ls[kSphereBatch];
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
                 const int s = s0 + i;               // past e: zero padding, masked below
-                const float lam = rc.sph_lambda[s];
+                ls[i] = rc.sph_ls[s];
+                const float lam = ls[i].x;
                 if (SELF && sp && i < e - s0) {     // kept for the self-collision term
                     const f3 p = axpy(lam, v, F.t);
                     sp[(3 * s) * 32] = p.x;
@@ -121,14 +124,14 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             unsigned need = 0u;
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i)
-                need |= (i < e - s0 && !(mn[i] > rc.sph_skip[s0 + i])) ? (1u << i) : 0u;
+                need |= (i < e - s0 && !(mn[i] > ls[i].y)) ? (1u << i) : 0u;
             if (need)
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
                 const int s = s0 + i;
                 if (need & (1u << i)) {
                     ++ngath;
-                    const float lam = rc.sph_lambda[s];
+                    const float lam = ls[i].x;
                     const Cell c = locate_grid(g, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
                     float vv[8];
                     corners<GT>(g, c.base, vv);
@@ -157,7 +160,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         unsigned need = 0u;
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i)
-            need |= (i < e - s0 && !(mn[i] > rc.sph_skip[s0 + i])) ? (1u << i) : 0u;
+            need |= (i < e - s0 && !(mn[i] > rc.sph_ls[s0 + i].y)) ? (1u << i) : 0u;
         if (need)
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
