@@ -74,6 +74,56 @@ IterKernel lookup_kernel(int dtype, TileShape s, bool trace, bool self)
     }
 }
 
+IterKernel lookup_dense_kernel(int dtype, TileShape s)
+{
+    switch (dtype) {
+    case PM_F32: return iteration_kernel_f32_dense(s.C, s.L, s.P);
+    case PM_F16: return iteration_kernel_f16_dense(s.C, s.L, s.P);
+    case PM_BF16: return iteration_kernel_bf16_dense(s.C, s.L, s.P);
+    default: return nullptr;
+    }
+}
+
+// The iteration kernel of a call, its shared memory and resident blocks.
+// A one-step shape without tracing or the self term switches to its
+// kDenseBlocks instantiation when the extra units run the launch in fewer
+// rounds of tiles, and in at most two: a short launch is dominated by its
+// partly filled last round (K = 4096, H = 64: 3 rounds of 1776 units or 2
+// of 2072, replan 290 -> 280 us), a long one by the throughput per round,
+// where the fitted registers of the 6-block kernel win (K = 16384: 866
+// against 941 us per replan).
+struct KernelPick {
+    IterKernel fn = nullptr;
+    size_t smem = 0;
+    long long resident = 0;
+};
+
+pm_status pick_kernel(pm_ctx *c, long long K, TileShape sh, bool trace, KernelPick &out)
+{
+    const bool self = c->rc.n_self_groups > 0;
+    out.fn = lookup_kernel(c->gd.dtype, sh, trace, self);
+    if (!out.fn)
+        return set_err(c, trace ? PM_EINVAL : PM_EINTERNAL, "no %s kernel for C=%d L=%d P=%d",
+                       trace ? "trace" : "iteration", sh.C, sh.L, sh.P);
+    out.smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
+    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(out.fn), kBlock, out.smem);
+    if (per_sm < 1)
+        return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, out.smem);
+    out.resident = static_cast<long long>(c->n_sm) * per_sm;
+    IterKernel dense = (trace || self) ? nullptr : lookup_dense_kernel(c->gd.dtype, sh);
+    if (dense) {
+        const int per_sm_d = resident_blocks_per_sm(reinterpret_cast<const void *>(dense), kBlock, out.smem);
+        const long long upb = kWarps / sh.P, tiles = (K + 32 / sh.L - 1) / (32 / sh.L);
+        const long long units = out.resident * upb, units_d = static_cast<long long>(c->n_sm) * per_sm_d * upb;
+        const long long rounds = (tiles + units - 1) / units, rounds_d = (tiles + units_d - 1) / units_d;
+        if (per_sm_d > per_sm && rounds_d < rounds && rounds_d <= 2) {
+            out.fn = dense;
+            out.resident = static_cast<long long>(c->n_sm) * per_sm_d;
+        }
+    }
+    return PM_OK;
+}
+
 bool shape_known(TileShape t)
 {
     for (const TileShape &s : kShapes)
@@ -506,17 +556,13 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
     TileShape sh;
     pm_status pst = pick_shape(c, H, sh);
     if (pst != PM_OK) return pst;
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, trace, c->rc.n_self_groups > 0);
-    if (!fn) return set_err(c, trace ? PM_EINVAL : PM_EINTERNAL, "no %s kernel for C=%d L=%d P=%d",
-                            trace ? "trace" : "iteration", sh.C, sh.L, sh.P);
-    const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
-    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
-    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
-    const long long resident = static_cast<long long>(c->n_sm) * per_sm;
-    const int nb = static_cast<int>(launch_blocks(K, sh, resident));
+    KernelPick kp;
+    pst = pick_kernel(c, K, sh, trace, kp);
+    if (pst != PM_OK) return pst;
+    const int nb = static_cast<int>(launch_blocks(K, sh, kp.resident));
     pm_status st = ensure_capacity(c, K, H, nb);
     if (st != PM_OK) return st;
-    return enqueue_iteration(c, s, fn, nb, smem, in, Ubar, Uout, costs, c->d_part, c->d_c0, K, H, dt,
+    return enqueue_iteration(c, s, kp.fn, nb, kp.smem, in, Ubar, Uout, costs, c->d_part, c->d_c0, K, H, dt,
                              lambda, seed, iter, trace, trace_out,
                              (c->count_gathers && !trace) ? c->d_gathers : nullptr);
 }
@@ -588,12 +634,12 @@ pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &i
     TileShape sh;
     pm_status st = pick_shape(c, H, sh);
     if (st != PM_OK) return st;
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false, c->rc.n_self_groups > 0);
-    if (!fn) return set_err(c, PM_EINTERNAL, "no iteration kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
-    const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
-    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
-    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
-    long long nb = launch_blocks(K, sh, static_cast<long long>(c->n_sm) * per_sm);
+    KernelPick kp;
+    st = pick_kernel(c, K, sh, false, kp);
+    if (st != PM_OK) return st;
+    const IterKernel fn = kp.fn;
+    const size_t smem = kp.smem;
+    long long nb = launch_blocks(K, sh, kp.resident);
     const size_t per_block = 2 + static_cast<size_t>(H) * kNJ;
     while (nb > 1 && static_cast<size_t>(nb) * per_block > part_floats) --nb;   // fewer, longer blocks
     if (static_cast<size_t>(nb) * per_block > part_floats)
@@ -1358,13 +1404,12 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
     TileShape sh;
     st = pick_shape(c, H, sh);
     if (st != PM_OK) return st;
-    IterKernel fn = lookup_kernel(c->gd.dtype, sh, false, c->rc.n_self_groups > 0);
-    if (!fn) return set_err(c, PM_EINTERNAL, "no kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
-    const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
-    const int per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
-    if (per_sm < 1) return set_err(c, PM_ECUDA, "cannot give the C=%d kernel %zu bytes of shared memory", sh.C, smem);
-    const long long resident = static_cast<long long>(c->n_sm) * per_sm;
-    long long nb = launch_blocks(K, sh, resident);
+    KernelPick kp;
+    st = pick_kernel(c, K, sh, false, kp);
+    if (st != PM_OK) return st;
+    const IterKernel fn = kp.fn;
+    const size_t smem = kp.smem;
+    long long nb = launch_blocks(K, sh, kp.resident);
     // fewer, longer-running blocks when the partials would not fit the array
     const size_t per_block = 2 + static_cast<size_t>(H) * kNJ;
     auto fits = [&](long long n) { return kStaticHeaderFloats + static_cast<size_t>(n) * per_block <= kStaticScratchFloats; };

@@ -38,6 +38,11 @@ IterKernel iteration_kernel_bf16(int C, int L, int P, bool trace);
 IterKernel iteration_kernel_f32_self(int C, int L, int P, bool trace);
 IterKernel iteration_kernel_f16_self(int C, int L, int P, bool trace);
 IterKernel iteration_kernel_bf16_self(int C, int L, int P, bool trace);
+// The kDenseBlocks instantiation of a one-step shape ((1,16,1), (1,32,1),
+// (1,32,2)) without tracing or the self term; nullptr for other shapes.
+IterKernel iteration_kernel_f32_dense(int C, int L, int P);
+IterKernel iteration_kernel_f16_dense(int C, int L, int P);
+IterKernel iteration_kernel_bf16_dense(int C, int L, int P);
 
 } // namespace pm
 
@@ -59,6 +64,17 @@ IterKernel iteration_kernel_bf16_self(int C, int L, int P, bool trace);
         PM_KERNEL_CASE(1, 32, 2, GT, WITH_TRACE, SELF)                                     \
         PM_KERNEL_CASE(2, 32, 2, GT, WITH_TRACE, SELF)                                     \
         PM_KERNEL_CASE(4, 32, 2, GT, WITH_TRACE, SELF)                                     \
+        return nullptr;                                                                \
+    }                                                                                  \
+    }
+
+#define PM_INSTANTIATE_DENSE_TABLE(NAME, GT)                                                \
+    namespace pm {                                                                     \
+    IterKernel NAME(int C, int L, int P)                                               \
+    {                                                                                  \
+        if (C == 1 && L == 16 && P == 1) return smpc_iteration_kernel<1, 16, 1, GT, false, false, kDenseBlocks>; \
+        if (C == 1 && L == 32 && P == 1) return smpc_iteration_kernel<1, 32, 1, GT, false, false, kDenseBlocks>; \
+        if (C == 1 && L == 32 && P == 2) return smpc_iteration_kernel<1, 32, 2, GT, false, false, kDenseBlocks>; \
         return nullptr;                                                                \
     }                                                                                  \
     }

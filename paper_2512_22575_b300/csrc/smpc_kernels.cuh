@@ -37,6 +37,7 @@ namespace pm {
 constexpr int kBlock = 128;
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxBlocks = 4096;
+constexpr int kDenseBlocks = 7;   // blocks per SM of the dense one-step instantiations
 constexpr int kTraceCols = 8;   // pose, env, self, lim_q, lim_qd, lim_qdd, smooth, ns
 constexpr int kSphereBatch = 4;
 static_assert(kSphereBatch - 1 <= kSpherePad, "a batch reads past a frame's spheres into the zero padding");
@@ -645,8 +646,13 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 // P = 2 (L = 32): two warps of a block share one roll-out, warp 2p taking
 // steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
 // totals of the first half and their partial costs through shared memory.
-template <int C, int L, int P, typename GT, bool TRACE, bool SELF>
-__global__ void __launch_bounds__(kBlock, C == 1 ? 6 : 5)
+// MINB is the residency the registers are fitted to: 6 blocks per SM for
+// the one-step shapes (80 registers, no spills), 5 for the others; the
+// one-step shapes also have a kDenseBlocks instantiation (72 registers, a
+// few spilled bytes), which the host picks when its extra units save a
+// round of tiles on a short launch.
+template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 ? 6 : 5)>
+__global__ void __launch_bounds__(kBlock, MINB)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
                       const __grid_constant__ IterArgs a)
 {

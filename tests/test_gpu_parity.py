@@ -100,6 +100,19 @@ def test_tiles_and_ragged_shapes(cfg1, K, H):
     assert np.abs(Ug - Uo).max() <= U_ABS
 
 
+@pytest.mark.parametrize("K,H", [(2048, 64), (4096, 32), (8000, 16)])
+def test_dense_residency_launches(cfg1, K, H):
+    """Launches that run in at most two rounds of tiles with the 7-block
+    instantiation of their one-step shape, which takes them (one round
+    fewer than with 6 blocks per SM on a 148-SM GPU): same parity bars."""
+    sc = cfg1[4]
+    rng = np.random.default_rng(K + H)
+    U = (rng.normal(size=(H, 7)) * 0.3).astype(np.float32)
+    Ug, Sg, Uo, So, wo = run_both(sc, K, H, 91, 2, U=U)
+    assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL
+    assert np.abs(Ug - Uo).max() <= U_ABS
+
+
 @pytest.mark.parametrize("mult", [1, 2])
 def test_k0_pass_placements_on_a_full_grid(cfg1, mult):
     """The k = 0 state terms run once per launch: on a unit of their own when
