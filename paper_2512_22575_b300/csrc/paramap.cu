@@ -90,8 +90,8 @@ IterKernel lookup_dense_kernel(int dtype, TileShape s)
 // rounds of tiles, and in at most two: a short launch is dominated by its
 // partly filled last round (K = 4096, H = 64: 3 rounds of 1776 units or 2
 // of 2072, replan 290 -> 280 us), a long one by the throughput per round,
-// where the fitted registers of the 6-block kernel win (K = 16384: 866
-// against 941 us per replan).
+// where the 6-block kernel wins (K = 16384: 862 against 927 us per
+// replan).
 struct KernelPick {
     IterKernel fn = nullptr;
     size_t smem = 0;
@@ -932,6 +932,19 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     }
     if (!ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy"))
         return fail(PM_ECUDA);
+    // Load every iteration kernel this context may launch now (modules load
+    // lazily by default), so that the first call of a new tile shape or
+    // residency does not stall on it; the occupancy of each is cached.
+    {
+        const bool self = c->rc.n_self_groups > 0;
+        for (const TileShape &sh : kShapes) {
+            const size_t smem = iteration_smem_bytes(sh.C) + self_smem_bytes(c->rc);
+            const IterKernel fns[2] = {lookup_kernel(c->gd.dtype, sh, false, self),
+                                       self ? nullptr : lookup_dense_kernel(c->gd.dtype, sh)};
+            for (IterKernel fn : fns)
+                if (fn) resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, smem);
+        }
+    }
     *out = c;
     return PM_OK;
 }

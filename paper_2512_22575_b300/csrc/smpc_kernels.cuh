@@ -254,11 +254,12 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
 // State terms at a step (Eqs. 16, 19-20, 22, 24), or the terminal cost (Eq. 25).
 // Forward kinematics runs frame by frame; the spheres of each frame are
 // looked up as soon as it is known.
-template <typename GT, bool TRACE, bool SELF>
+template <typename GT, bool TRACE, bool SELF, bool QMEM = false>
 __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
                                             const InstanceState &st, const float *q,
                                             const float *qd, bool terminal, float *tr,
-                                            unsigned &ngath, float *sp)
+                                            unsigned &ngath, float *sp, const float *qa = nullptr,
+                                            int qstride = 1)
 {
     if (!SELF || terminal) sp = nullptr;
     float lq = 0.f, lqd = 0.f, ns = 0.f;
@@ -276,16 +277,22 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     Frame F = base_frame();
     float env = 0.f;
     // Not unrolled: the kernel's code then fits the instruction cache, which
-    // outweighs the indexed constant loads this costs.  The joint angles
-    // rotate through qr so that the loop indexes no register array.
+    // outweighs the indexed constant loads this costs.  With QMEM the joint
+    // angles are read where the step staged them (qa, stride qstride), so
+    // they hold no registers across the loop; otherwise they rotate through
+    // qr so that the loop indexes no register array.
     float qr[kNJ];
+    if (!QMEM) {
 #pragma unroll
-    for (int j = 0; j < kNJ; ++j) qr[j] = q[j];
+        for (int j = 0; j < kNJ; ++j) qr[j] = q[j];
+    }
 #pragma unroll 1
     for (int j = 0; j < kNJ; ++j) {
-        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], qr[0] + rc.th0[j]);
+        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], (QMEM ? qa[j * qstride] : qr[0]) + rc.th0[j]);
+        if (!QMEM) {
 #pragma unroll
-        for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
+            for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
+        }
         if (!terminal) env += link_env<GT, SELF>(rc, g, F, j, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
         if (SELF && sp) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
@@ -514,6 +521,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 continue;
             }
             float q[kNJ], qd[kNJ], cc = 0.f;
+            const float *qa = st.q0;
+            int qstride = 1;
             float *tr_x = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k + 1) * kTraceCols : nullptr;
             if (extra) {
 #pragma unroll
@@ -523,6 +532,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) { q[j] = qs[j * 32]; qd[j] = qs[(kNJ + j) * 32]; }
                 cc = qs[(2 * kNJ) * 32];
+                qa = qs;
+                qstride = 32;
             } else {
                 float u[kNJ];
                 const float kp_dt = static_cast<float>(k + 1) * dt;
@@ -539,7 +550,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 cc = control_cost<TRACE>(rc, u, tr_u);
             }
             const unsigned ng0 = ngath;
-            const float sc = state_cost<GT, TRACE, SELF>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp);
+            const float sc = state_cost<GT, TRACE, SELF, STAGE>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp,
+                                                                qa, qstride);
             if (extra) {
                 ngath = ng0;        // lookups of the roll-outs only
                 *job.c0 = sc;
@@ -647,10 +659,10 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 // steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
 // totals of the first half and their partial costs through shared memory.
 // MINB is the residency the registers are fitted to: 6 blocks per SM for
-// the one-step shapes (80 registers, no spills), 5 for the others; the
-// one-step shapes also have a kDenseBlocks instantiation (72 registers, a
-// few spilled bytes), which the host picks when its extra units save a
-// round of tiles on a short launch.
+// the one-step shapes (80 registers), 5 for the others; the one-step
+// shapes also have a kDenseBlocks instantiation (72 registers, neither
+// spills), which the host picks when its extra units save a round of
+// tiles on a short launch.
 template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 ? 6 : 5)>
 __global__ void __launch_bounds__(kBlock, MINB)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
