@@ -113,18 +113,20 @@ def test_dense_residency_launches(cfg1, K, H):
     assert np.abs(Ug - Uo).max() <= U_ABS
 
 
-@pytest.mark.parametrize("mult", [1, 2])
-def test_k0_pass_placements_on_a_full_grid(cfg1, mult):
+@pytest.mark.parametrize("per_sm", [12, 24, 14])
+def test_k0_pass_placements_on_a_full_grid(cfg1, per_sm):
     """The k = 0 state terms run once per launch: on a unit of their own when
     the tiles do not fill the units evenly (the ragged cases above), in an
     extra block when they do and the grid has room (K = 256, H = 32), and
     after the last tile when they fill a full resident grid.  H = 64 runs
-    pair tiles on 5 blocks of 4 warps per SM, i.e. 10 x SMs units; K = mult
-    times that fills them exactly."""
+    pair tiles, two units per block of 4 warps: 12 x SMs units at 6 blocks
+    per SM, filled exactly in one and two rounds by K = 12 and 24 x SMs
+    roll-outs; and 14 x SMs units at 7 blocks per SM, the instantiation the
+    launch takes for K = 14 x SMs, which it fills in one round."""
     sc = cfg1[4]
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    K, H = mult * 10 * n_sm, 64
-    rng = np.random.default_rng(40 + mult)
+    K, H = per_sm * n_sm, 64
+    rng = np.random.default_rng(40 + per_sm)
     U = (rng.normal(size=(H, 7)) * 0.3).astype(np.float32)
     Ug, Sg, Uo, So, wo = run_both(sc, K, H, 91, 5, U=U)
     assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL
