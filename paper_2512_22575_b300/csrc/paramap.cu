@@ -866,6 +866,10 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
                 dense = ps[p0 + i].a == a_lo + i / nb && ps[p0 + i].b == b_lo + i % nb;
             r.grp_dense[k] = dense ? 1 : 0;
         }
+        bool frames = true;
+        for (int k = 0; k <= g; ++k)
+            frames = frames && r.grp_dense[k] && r.link_line[r.grp_fa[k]] && r.link_line[r.grp_fb[k]];
+        r.self_frames = frames ? 1 : 0;
     }
     for (int i = 0; i < 6; ++i) { r.Q[i] = cp->Q[i]; r.QH[i] = cp->QH[i]; }
     r.w_env = cp->w_env; r.d_act = cp->d_act; r.w_self = cp->w_self;

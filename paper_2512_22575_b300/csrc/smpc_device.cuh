@@ -69,6 +69,7 @@ struct RobotConst {
     // 1: group g holds every pair of its two frames' spheres (at most
     // kSelfDense each), in (a, b) order, so it is evaluated as a dense block
     unsigned char grp_dense[kMaxSelfGroups];
+    unsigned char self_frames;    // 1: the self slots use the frame layout (see self_slots)
     float grp_thr2[kMaxSelfGroups];
     float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
     // device [n], grouped and ordered by (a, b) within a group: x = bits of
@@ -77,9 +78,17 @@ struct RobotConst {
     const float4 *self_pairs;
 };
 
-// Per-lane shared-memory slots of the self-collision term: the world
-// centres of the step's spheres, then of the frames' bounding spheres.
-__host__ __device__ constexpr int self_slots(int n_spheres) { return 3 * n_spheres + 3 * kNJ; }
+// Per-lane shared-memory slots of the self-collision term.  Sphere layout:
+// the world centres of the step's spheres, then of the frames' bounding
+// spheres.  Frame layout (self_frames, every group dense and every frame
+// in a group on a line): per frame j, its origin t, its rotated direction
+// v = R w and its bounding-sphere centre, 9 floats, from which the pair
+// test forms each centre as t + lambda_s v, as the lookups do.
+constexpr int kSelfFrameSlots = 9;
+__host__ __device__ constexpr int self_slots(int n_spheres, bool frames)
+{
+    return frames ? kSelfFrameSlots * kNJ : 3 * n_spheres + 3 * kNJ;
+}
 
 struct GridConst {
     const void *phi;              // [nz][ny][nx], x fastest; float, half or bf16

@@ -52,7 +52,9 @@ constexpr size_t iteration_smem_bytes(int C)
 // Extra dynamic shared memory of the self-collision term (0 when off).
 inline size_t self_smem_bytes(const RobotConst &rc)
 {
-    return rc.n_self_groups > 0 ? static_cast<size_t>(kWarps) * 32 * self_slots(rc.n_spheres) * sizeof(float) : 0;
+    return rc.n_self_groups > 0
+               ? static_cast<size_t>(kWarps) * 32 * self_slots(rc.n_spheres, rc.self_frames) * sizeof(float)
+               : 0;
 }
 
 struct IterArgs {
@@ -104,7 +106,14 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         const f3 gv = axpy(rc.link_wg[j][2], F.c3, axpy(rc.link_wg[j][1], F.c2, scale(rc.link_wg[j][0], F.c1)));
         const f3 gt = mk(fmaf(F.t.x, g.inv_res, g.bx), fmaf(F.t.y, g.inv_res, g.by), fmaf(F.t.z, g.inv_res, g.bz));
         f3 v{};
-        if (SELF && sp) v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
+        if (SELF && sp) {
+            v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
+            if (rc.self_frames) {
+                float *fs = sp + kSelfFrameSlots * j * 32;
+                fs[0] = F.t.x; fs[32] = F.t.y; fs[64] = F.t.z;
+                fs[96] = v.x; fs[128] = v.y; fs[160] = v.z;
+            }
+        }
         for (int s0 = b; s0 < e; s0 += kSphereBatch) {
             float mn[kSphereBatch];
             float2 ls[kSphereBatch];
@@ -113,7 +122,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                 const int s = s0 + i;               // past e: zero padding, masked below
                 ls[i] = rc.sph_ls[s];
                 const float lam = ls[i].x;
-                if (SELF && sp && i < e - s0) {     // kept for the self-collision term
+                if (SELF && sp && !rc.self_frames && i < e - s0) {   // kept for the self-collision term
                     const f3 p = axpy(lam, v, F.t);
                     sp[(3 * s) * 32] = p.x;
                     sp[(3 * s + 1) * 32] = p.y;
@@ -150,7 +159,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = s0 + i;               // past e: zero padding, masked below
             const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-            if (SELF && sp && i < e - s0) {     // kept for the self-collision term
+            if (SELF && sp && !rc.self_frames && i < e - s0) {   // kept for the self-collision term
                 sp[(3 * s) * 32] = p.x;
                 sp[(3 * s + 1) * 32] = p.y;
                 sp[(3 * s + 2) * 32] = p.z;
@@ -186,8 +195,51 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
 // centres the step stored in its lane's slots sp (stride 32 floats).
 __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp)
 {
-    const int lb0 = 3 * rc.n_spheres;
     float acc = 0.f;
+    if (rc.self_frames) {
+        // frame layout: every group dense, every centre t + lambda_s v of its
+        // frame, formed as the lookups form it (the same pairs and order as
+        // the dense blocks below)
+        for (int gi = 0; gi < rc.n_self_groups; ++gi) {
+            const int fa = rc.grp_fa[gi], fb = rc.grp_fb[gi];
+            const float *pa = sp + kSelfFrameSlots * fa * 32, *pb = sp + kSelfFrameSlots * fb * 32;
+            const float gx = pa[6 * 32] - pb[6 * 32];
+            const float gy = pa[7 * 32] - pb[7 * 32];
+            const float gz = pa[8 * 32] - pb[8 * 32];
+            if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > rc.grp_thr2[gi]) continue;   // exact zero
+            const int a_lo = rc.link_begin[fa + 1], a_hi = rc.link_begin[fa + 2];
+            const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
+            const f3 tb = mk(pb[0], pb[32], pb[64]), vb = mk(pb[96], pb[128], pb[160]);
+            const f3 ta = mk(pa[0], pa[32], pa[64]), va = mk(pa[96], pa[128], pa[160]);
+            float bx[kSelfDense], by[kSelfDense], bz[kSelfDense], br[kSelfDense];
+#pragma unroll
+            for (int i = 0; i < kSelfDense; ++i) {
+                const int sb = b_lo + min(i, nb - 1);
+                const f3 c = axpy(rc.sph_ls[sb].x, vb, tb);
+                bx[i] = c.x;
+                by[i] = c.y;
+                bz[i] = c.z;
+                br[i] = rc.sph_r[sb];
+            }
+            for (int a = a_lo; a < a_hi; ++a) {
+                const f3 ca = axpy(rc.sph_ls[a].x, va, ta);
+                const float ra = rc.sph_r[a];
+#pragma unroll
+                for (int i = 0; i < kSelfDense; ++i) {
+                    const float ex = ca.x - bx[i], ey = ca.y - by[i], ez = ca.z - bz[i];
+                    const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const float rs = ra + br[i];
+                    const float t = __fadd_ru(rs, 1e-5f);
+                    if (i < nb && d2 <= __fmul_ru(t, t)) {
+                        const float del = fmaxf(rs - sqrtf(d2), 0.f);
+                        acc = fmaf(del, del, acc);
+                    }
+                }
+            }
+        }
+        return rc.w_self * acc;
+    }
+    const int lb0 = 3 * rc.n_spheres;
     for (int gi = 0; gi < rc.n_self_groups; ++gi) {
         const int fa = lb0 + 3 * rc.grp_fa[gi], fb = lb0 + 3 * rc.grp_fb[gi];
         const float gx = sp[fa * 32] - sp[fb * 32];
@@ -296,7 +348,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         if (!terminal) env += link_env<GT, SELF>(rc, g, F, j, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
         if (SELF && sp) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
-            const int t = 3 * rc.n_spheres + 3 * j;
+            const int t = rc.self_frames ? kSelfFrameSlots * j + 6 : 3 * rc.n_spheres + 3 * j;
             sp[t * 32] = c.x;
             sp[(t + 1) * 32] = c.y;
             sp[(t + 2) * 32] = c.z;
@@ -403,7 +455,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     float run_m = CUDART_INF_F, run_z = 0.f;
     const float dt = job.dt, dt2 = job.dt * job.dt;
     float *sp = (SELF && rc.n_self_groups > 0 && sm.self)
-                    ? sm.self + warp * self_slots(rc.n_spheres) * 32 + lane : nullptr;
+                    ? sm.self + warp * self_slots(rc.n_spheres, rc.self_frames) * 32 + lane : nullptr;
     const int half = (P == 2) ? (warp & 1) : 0;
     const int pr = warp >> 1;
     const int kbase = half * 32 * C;
