@@ -345,7 +345,9 @@ __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 
     if (th < 1e-4f) {
         w = scale(0.5f + th * th * (1.0f / 12.0f), vee);
     } else if (th < CUDART_PI_F - 0.05f) {
-        w = scale(th / nv, vee);
+        // nv = 2 sin th lies in [2e-4, 2] here: __fdividef (2 ulp) needs no
+        // special cases, and so does the quotient of c(th) below
+        w = scale(__fdividef(th, nv), vee);
     } else {
         // Near pi: (R + R^T)/2 = cos(th) I + (1 - cos(th)) a a^T; take the axis
         // from the column with the largest diagonal, the sign from vee.
@@ -383,7 +385,7 @@ __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 
     if (th < 1e-2f) {
         cc = (1.0f / 12.0f) + th * th * (1.0f / 720.0f);
     } else if (th < CUDART_PI_F - 0.05f) {
-        cc = (1.0f - th * (1.0f + cth) / nv) / (th * th);
+        cc = __fdividef(1.0f - __fdividef(th * (1.0f + cth), nv), th * th);
     } else {
         const float h = 0.5f * th;
         float sh, ch;
