@@ -198,7 +198,9 @@ pm_status pm_replan(pm_ctx *ctx, float *q, float *qd, const float *T_goal, float
  * array that every GPU loading the library holds until exit.  The array's
  * device address is resolved with cudaGetSymbolAddress on the first call on
  * each device, with that device current; make that first call before any
- * stream capture.  Every call shares the array and keeps what the previous
+ * stream capture.  The address is cached for the life of the process: it
+ * does not survive cudaDeviceReset or a re-created primary context, after
+ * which this entry point must not be called.  Every call shares the array and keeps what the previous
  * call left there; each call writes every word it reads before reading it,
  * so nothing needs clearing, but calls must not overlap on the GPU (calls on
  * different streams, or from different contexts, that run concurrently race
@@ -211,6 +213,17 @@ pm_status pm_smpc_iterate_noalloc(pm_ctx *ctx, const float *q0, const float *qd0
                                   const float *T_goal, float *U, int K, int H, float dt,
                                   float lambda, const float *sigma, uint64_t seed,
                                   uint32_t iter_index, float *costs_out, void *cuda_stream);
+
+/*
+ * pm_launch_plan: the launch an iteration of K roll-outs over horizon H
+ * would use on this context (no counterpart in the paper; for tests and
+ * tuning): out[0..2] = the tile shape (C steps per lane, L lanes per
+ * roll-out, P warps per roll-out), out[3] = thread blocks of the iteration
+ * kernel.  With noalloc != 0 the block count is the one
+ * pm_smpc_iterate_noalloc launches (reduced so that the partials fit its
+ * static array; 0 if they cannot).  Launches nothing.  Errors: PM_EINVAL.
+ */
+pm_status pm_launch_plan(pm_ctx *ctx, int K, int H, int noalloc, int out[4]);
 
 /*
  * Batched iterations: many arms, each with its own context (robot, costs,
@@ -446,6 +459,13 @@ pm_status pm_map_update(pm_ctx *ctx, const uint8_t *occ, int occ_is_device, cons
  *   smooth, ns); row H holds the terminal cost in the pose column.  State
  *   terms of row 0 are the same for every roll-out and are left at 0.
  *   U is read, not updated.  Waits for the stream.
+ * pm_pose_error: xi[i] = log(T_goal[i]^{-1} T[i]) = [v; w] (Eqs. 11-15), the
+ *   pose error of the pose cost (Eqs. 16, 25) as the iteration evaluates it,
+ *   in its three regimes of the rotation angle theta (series below 1e-4,
+ *   the quotient form, the symmetric-part axis above pi - 0.05).  T_goal,
+ *   T: device float[n][16], row-major homogeneous transforms; xi: device
+ *   float[n][6].  Enqueued on cuda_stream.  Errors: PM_EINVAL (NULL or host
+ *   pointers), PM_ECUDA.
  */
 pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, size_t n,
                            void *cuda_stream);
@@ -460,6 +480,8 @@ pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, siz
 pm_status pm_fp32_fma_peak(int device, double *tflops);
 pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed,
                           uint32_t iter_index, float *eps, void *cuda_stream);
+pm_status pm_pose_error(const float *T_goal, const float *T, float *xi, size_t n,
+                        void *cuda_stream);
 pm_status pm_rollout_trace(pm_ctx *ctx, const float *q0, const float *qd0,
                            const float *T_goal, const float *U, int K, int H, float dt,
                            const float *sigma, uint64_t seed, uint32_t iter_index,

@@ -25,7 +25,7 @@ __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
     "create", "set_distance_field", "smpc_iterate", "smpc_iterate_noalloc", "replan",
     "philox4x32_10",
-    "sample_noise", "rollout_trace", "profile_enable", "profile_read", "profile_gathers",
+    "sample_noise", "rollout_trace", "pose_error", "profile_enable", "profile_read", "profile_gathers", "launch_plan",
     "set_tile_shape", "set_noise_dtype", "PM_PROFILE_TIME", "PM_PROFILE_GATHERS", "destroy",
     "last_error", "Planner", "Batch", "Server", "PM_BATCH_REPLAN", "PM_BATCH_GRAPH", "PM_BATCH_AUTOTUNE",
 ]
@@ -282,6 +282,14 @@ def sample_noise(K, H, sigma, seed, iter_index, eps, stream=None):
                                  _stream(stream)))
 
 
+def pose_error(T_goal, T, xi, stream=None):
+    """pm_pose_error on CUDA float32 tensors T_goal, T [n][16] (row-major 4x4)
+    into xi [n][6] = log(T_goal^-1 T) as [v; w]."""
+    n = T.numel() // 16
+    _check(lib().pm_pose_error(_ptr(T_goal, n=16 * n), _ptr(T, n=16 * n), _ptr(xi, n=6 * n, writable=True),
+                               C.c_size_t(n), _stream(stream)))
+
+
 PM_PROFILE_TIME, PM_PROFILE_GATHERS = 1, 2
 
 
@@ -305,6 +313,14 @@ def set_noise_dtype(ctx, dtype="f32"):
 def set_tile_shape(ctx, C_steps=0, L=0, P=0):
     """pm_set_tile_shape: force (C, L, P) for later calls; (0, 0, 0) = default."""
     _check(lib().pm_set_tile_shape(ctx, int(C_steps), int(L), int(P)), ctx)
+
+
+def launch_plan(ctx, K, H, noalloc=False):
+    """pm_launch_plan: ((C, L, P), thread blocks) of an iteration of K
+    roll-outs over horizon H (of pm_smpc_iterate_noalloc with noalloc)."""
+    out = (C.c_int * 4)()
+    _check(lib().pm_launch_plan(ctx, int(K), int(H), int(bool(noalloc)), out), ctx)
+    return (out[0], out[1], out[2]), out[3]
 
 
 def profile_read(ctx, reset=True):
@@ -542,6 +558,9 @@ class Planner:
 
     def profile_read(self, reset=True):
         return profile_read(self.ctx, reset)
+
+    def launch_plan(self, K, H, noalloc=False):
+        return launch_plan(self.ctx, K, H, noalloc)
 
     def close(self):
         if self.ctx is not None:

@@ -92,6 +92,8 @@ SIGNATURES = {
                             _V, C.c_uint64, C.c_uint32, _V, _V, _V]),
     "pm_philox4x32_10": (C.c_int, [_V, C.c_uint64, _V, C.c_size_t, _V]),
     "pm_sample_noise": (C.c_int, [C.c_int, C.c_int, _V, C.c_uint64, C.c_uint32, _V, _V]),
+    "pm_pose_error": (C.c_int, [_V, _V, _V, C.c_size_t, _V]),
+    "pm_launch_plan": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "pm_rollout_trace": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_float, _V,
                                    C.c_uint64, C.c_uint32, _V]),
     "pm_profile_enable": (C.c_int, [_V, C.c_int]),

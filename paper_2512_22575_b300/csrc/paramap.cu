@@ -282,6 +282,22 @@ __global__ void philox_words_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k
     }
 }
 
+// xi = log(T_g^{-1} T) of each pose pair with the iteration's pose_error
+// (Eqs. 11-15): Tg, T row-major 4x4, xi = [v; w].
+__global__ void pose_error_kernel(const float *Tg, const float *T, float *xi, size_t n)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float *g = Tg + 16 * i, *e = T + 16 * i;
+        const float Rg[9] = {g[0], g[1], g[2], g[4], g[5], g[6], g[8], g[9], g[10]};
+        const float tg[3] = {g[3], g[7], g[11]};
+        float x[6];
+        pose_error(Rg, tg, mk(e[0], e[4], e[8]), mk(e[1], e[5], e[9]), mk(e[2], e[6], e[10]),
+                   mk(e[3], e[7], e[11]), x);
+        for (int j = 0; j < 6; ++j) xi[6 * i + j] = x[j];
+    }
+}
+
 struct Sigma { float s[8]; };
 
 __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint32_t s_hi,
@@ -1244,6 +1260,18 @@ pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, siz
     return PM_OK;
 }
 
+pm_status pm_pose_error(const float *T_goal, const float *T, float *xi, size_t n, void *cuda_stream)
+{
+    if (!T_goal || !T || !xi) return set_err(nullptr, PM_EINVAL, "NULL argument");
+    if (n == 0) return PM_OK;
+    if (!is_device_ptr(T_goal) || !is_device_ptr(T) || !is_device_ptr(xi))
+        return set_err(nullptr, PM_EINVAL, "T_goal/T/xi must be device memory");
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((n + 127) / 128, 65535));
+    pose_error_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(cuda_stream)>>>(T_goal, T, xi, n);
+    PM_CUDA(nullptr, cudaGetLastError());
+    return PM_OK;
+}
+
 pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed, uint32_t iter_index,
                           float *eps, void *cuda_stream)
 {
@@ -1399,6 +1427,16 @@ pm_status static_scratch(pm_ctx *c, int device, float **out)
     return PM_OK;
 }
 
+// Blocks of a launch whose partials live in the static array: fewer, longer
+// running blocks when nb blocks' partials would not fit; 0 if none fits.
+long long static_blocks(long long nb, int H)
+{
+    const size_t per_block = 2 + static_cast<size_t>(H) * kNJ;
+    auto fits = [&](long long n) { return kStaticHeaderFloats + static_cast<size_t>(n) * per_block <= kStaticScratchFloats; };
+    while (nb > 1 && !fits(nb)) --nb;
+    return fits(nb) ? nb : 0;
+}
+
 } // namespace
 
 extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const float *qd0,
@@ -1426,12 +1464,8 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
     if (st != PM_OK) return st;
     const IterKernel fn = kp.fn;
     const size_t smem = kp.smem;
-    long long nb = launch_blocks(K, sh, kp.resident);
-    // fewer, longer-running blocks when the partials would not fit the array
-    const size_t per_block = 2 + static_cast<size_t>(H) * kNJ;
-    auto fits = [&](long long n) { return kStaticHeaderFloats + static_cast<size_t>(n) * per_block <= kStaticScratchFloats; };
-    while (nb > 1 && !fits(nb)) --nb;
-    if (!fits(nb))
+    const long long nb = static_blocks(launch_blocks(K, sh, kp.resident), H);
+    if (nb < 1)
         return set_err(c, PM_EINVAL, "H=%d needs more than the %zu-float static scratch", H, kStaticScratchFloats);
 
     cudaStream_t s = pick_stream(c, cuda_stream);
@@ -1448,3 +1482,24 @@ extern "C" pm_status pm_smpc_iterate_noalloc(pm_ctx *c, const float *q0, const f
                              iter_index, false, nullptr, nullptr);
 }
 
+extern "C" pm_status pm_launch_plan(pm_ctx *c, int K, int H, int noalloc, int out[4])
+{
+    if (!c || !out) return set_err(c, PM_EINVAL, "NULL argument");
+    if (K < 1 || H < 1 || K > PM_MAX_ROLLOUTS || H > PM_MAX_HORIZON)
+        return set_err(c, PM_EINVAL, "K=%d / H=%d out of range", K, H);
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    TileShape sh;
+    pm_status st = pick_shape(c, H, sh);
+    if (st != PM_OK) return st;
+    KernelPick kp;
+    st = pick_kernel(c, K, sh, false, kp);
+    if (st != PM_OK) return st;
+    long long nb = launch_blocks(K, sh, kp.resident);
+    if (noalloc) nb = static_blocks(nb, H);
+    out[0] = sh.C;
+    out[1] = sh.L;
+    out[2] = sh.P;
+    out[3] = static_cast<int>(nb);
+    return PM_OK;
+}

@@ -62,9 +62,14 @@ def reference_replans(arm, requests):
 
 
 def check(res, ref):
+    """A served result against the same replan alone: u0* within the U* bar
+    (1e-5; the two differ only in how the roll-outs are cut into blocks, so
+    in the merge order of the soft-min sums)."""
     qq, qqd, u0, best = ref
     assert res["status"] == "PM_OK"
-    assert np.abs(res["u0"] - u0).max() <= N_ITERS * U_ABS
+    err = np.abs(res["u0"] - u0).max()
+    print(f"served vs alone: |u0 - u0_alone| = {err:.1e}")
+    assert err <= U_ABS
     assert np.abs(res["qd_next"] - qqd).max() <= 1e-6
     assert np.abs(res["q_next"] - qq).max() <= 1e-6
     assert abs(res["best_cost"] - best) <= 1e-4 * abs(best)

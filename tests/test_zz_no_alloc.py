@@ -44,7 +44,11 @@ def _run(p, entry, sc, U0, K, seed, it):
 
 @pytest.mark.parametrize("K,H", [(256, 32), (4096, 64), (300, 200)])
 def test_noalloc_matches_iterate_on_two_calls_in_a_row(scene, K, H):
+    """Where the static array holds the usual grid's partials, both entry
+    points launch the same kernel with the same blocks on the same inputs:
+    the results must be bit-identical, on two calls in a row."""
     p = scene.planner()
+    assert p.launch_plan(K, H, noalloc=True) == p.launch_plan(K, H)
     rng = np.random.default_rng(K + H)
     U0 = (rng.normal(size=(H, 7)) * 0.2).astype(np.float32)
     # first call: same inputs on both entry points
@@ -55,8 +59,30 @@ def test_noalloc_matches_iterate_on_two_calls_in_a_row(scene, K, H):
     Un2, Sn2 = _run(p, p.smpc_iterate_noalloc, scene, Ur1, K, 31, 1)
     p.close()
     for Ur, Un, Sr, Sn in ((Ur1, Un1, Sr1, Sn1), (Ur2, Un2, Sr2, Sn2)):
-        assert np.abs(Un - Ur).max() <= U_ABS
-        assert (np.abs(Sn - Sr) / np.abs(Sr)).max() <= S_REL
+        assert np.array_equal(Un, Ur)
+        assert np.array_equal(Sn, Sr)
+
+
+@pytest.mark.parametrize("K,H", [(300, 200), (4096, 256)])
+def test_noalloc_against_the_oracle(scene, K, H):
+    """The no-allocation call against the FP64 oracle directly, on two calls
+    in a row.  At K = 4096, H = 256 the usual grid's partials exceed the
+    static array, so the call runs fewer, longer blocks (checked through the
+    launch plan)."""
+    p = scene.planner()
+    shape, nb = p.launch_plan(K, H)
+    _, nb_static = p.launch_plan(K, H, noalloc=True)
+    if H == 256:
+        assert 0 < nb_static < nb
+    rng = np.random.default_rng(5 * K + H)
+    U = (rng.normal(size=(H, 7)) * 0.2).astype(np.float32)
+    for it in range(2):
+        Ug, Sg = _run(p, p.smpc_iterate_noalloc, scene, U, K, 33, it)
+        Uo, So, _ = scene.oracle_iterate(U, K, 0.02, 0.05, SIGMA, 33, it, n_threads=0)
+        assert (np.abs(Sg - So) / np.abs(So)).max() <= S_REL, it
+        assert np.abs(Ug - Uo).max() <= U_ABS, it
+        U = Ug
+    p.close()
 
 
 def test_noalloc_rejects_host_buffers(scene):
