@@ -215,6 +215,42 @@ pm_status pm_smpc_iterate_noalloc(pm_ctx *ctx, const float *q0, const float *qd0
                                   uint32_t iter_index, float *costs_out, void *cuda_stream);
 
 /*
+ * Memory-safety checks (no counterpart in the paper).  The library built
+ * with PM_BOUNDS_CHECK (libparamap_checked.so, from the same sources)
+ * checks the index of every distance-field gather, shared-memory slot and
+ * cost / partial / trace write of the iteration kernels against the extent
+ * of its array; a violation skips the access (a read takes element 0) and
+ * sets a bit in the context's violation word: 1 field gather, 2 tile
+ * arrays, 4 staged states, 8 block accumulator, 16 nominal sequence read,
+ * 32 cost write, 64 block partial, 128 trace, 256 self-collision slots.
+ * Nothing traps.  pm_bounds_checked returns 1 in that build and 0 in the
+ * normal one.  pm_bounds_status waits for the device, stores the context's
+ * word in *word (always 0 in the normal build) and clears it if reset.
+ * Errors: PM_EINVAL, PM_ECUDA.
+ */
+int pm_bounds_checked(void);
+pm_status pm_bounds_status(pm_ctx *ctx, unsigned *word, int reset);
+
+/*
+ * pm_set_call_graphs: with enable != 0 (the default), a pm_smpc_iterate or
+ * pm_replan call whose q0/q, qd0/qd, T_goal, U and outputs are all host
+ * memory is replayed from a CUDA graph the context captures on the first
+ * call of each shape (K, H, n_iters, costs wanted; at most 32 kept, least
+ * recently used dropped): one graph launch per call instead of 2 n_iters + 1
+ * kernel launches.  The graph's kernels read the call's inputs and scalars
+ * (sigma, dt, lambda, seed, iteration index) from a fixed device block that
+ * the call fills with one copy from a pinned host block (one copy brings the
+ * outputs back), and compute exactly what the direct launches compute (same
+ * results, bit for bit).
+ * Applies to contexts with a float field and no self-collision term while
+ * profiling and gather counting are off; other calls launch directly.  The
+ * first call of a shape pays the capture (about a millisecond).  enable = 0
+ * drops the captured graphs and launches every call directly.  No
+ * counterpart in the paper.  Errors: PM_EINVAL.
+ */
+pm_status pm_set_call_graphs(pm_ctx *ctx, int enable);
+
+/*
  * pm_launch_plan: the launch an iteration of K roll-outs over horizon H
  * would use on this context (no counterpart in the paper; for tests and
  * tuning): out[0..2] = the tile shape (C steps per lane, L lanes per

@@ -25,7 +25,7 @@ __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
     "create", "set_distance_field", "smpc_iterate", "smpc_iterate_noalloc", "replan",
     "philox4x32_10",
-    "sample_noise", "rollout_trace", "pose_error", "profile_enable", "profile_read", "profile_gathers", "launch_plan",
+    "sample_noise", "rollout_trace", "pose_error", "profile_enable", "profile_read", "profile_gathers", "launch_plan", "set_call_graphs", "bounds_checked", "bounds_status",
     "set_tile_shape", "set_noise_dtype", "PM_PROFILE_TIME", "PM_PROFILE_GATHERS", "destroy",
     "last_error", "Planner", "Batch", "Server", "PM_BATCH_REPLAN", "PM_BATCH_GRAPH", "PM_BATCH_AUTOTUNE",
 ]
@@ -315,6 +315,24 @@ def set_tile_shape(ctx, C_steps=0, L=0, P=0):
     _check(lib().pm_set_tile_shape(ctx, int(C_steps), int(L), int(P)), ctx)
 
 
+def bounds_checked():
+    """pm_bounds_checked: True in the bounds-checked build."""
+    return bool(lib().pm_bounds_checked())
+
+
+def bounds_status(ctx, reset=True):
+    """pm_bounds_status: the context's violation word (0 = no violation)."""
+    w = C.c_uint()
+    _check(lib().pm_bounds_status(ctx, C.byref(w), int(bool(reset))), ctx)
+    return w.value
+
+
+def set_call_graphs(ctx, enable=True):
+    """pm_set_call_graphs: replay host-buffer calls from captured CUDA graphs
+    (default on) or launch every call directly."""
+    _check(lib().pm_set_call_graphs(ctx, int(bool(enable))), ctx)
+
+
 def launch_plan(ctx, K, H, noalloc=False):
     """pm_launch_plan: ((C, L, P), thread blocks) of an iteration of K
     roll-outs over horizon H (of pm_smpc_iterate_noalloc with noalloc)."""
@@ -561,6 +579,12 @@ class Planner:
 
     def launch_plan(self, K, H, noalloc=False):
         return launch_plan(self.ctx, K, H, noalloc)
+
+    def set_call_graphs(self, enable=True):
+        set_call_graphs(self.ctx, enable)
+
+    def bounds_status(self, reset=True):
+        return bounds_status(self.ctx, reset)
 
     def close(self):
         if self.ctx is not None:

@@ -94,6 +94,9 @@ SIGNATURES = {
     "pm_sample_noise": (C.c_int, [C.c_int, C.c_int, _V, C.c_uint64, C.c_uint32, _V, _V]),
     "pm_pose_error": (C.c_int, [_V, _V, _V, C.c_size_t, _V]),
     "pm_launch_plan": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "pm_set_call_graphs": (C.c_int, [_V, C.c_int]),
+    "pm_bounds_checked": (C.c_int, []),
+    "pm_bounds_status": (C.c_int, [_V, C.POINTER(C.c_uint), C.c_int]),
     "pm_rollout_trace": (C.c_int, [_V, _V, _V, _V, _V, C.c_int, C.c_int, C.c_float, _V,
                                    C.c_uint64, C.c_uint32, _V]),
     "pm_profile_enable": (C.c_int, [_V, C.c_int]),
@@ -129,8 +132,16 @@ SIGNATURES = {
 _lib = None
 
 
+LIB_NAMES = ("libparamap.so", "libparamap_checked.so")
+
+
 def lib_path():
-    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libparamap.so")
+    """The library this process loads: libparamap.so, or the bounds-checked
+    build when the environment sets PARAMAP_LIB=libparamap_checked.so."""
+    name = os.environ.get("PARAMAP_LIB", "libparamap.so")
+    if name not in LIB_NAMES:
+        raise ImportError(f"PARAMAP_LIB={name!r}: expected one of {LIB_NAMES}")
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
 
 
 def lib():

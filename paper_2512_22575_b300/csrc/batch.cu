@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     __shared__ float s_wm[kWarps], s_wz[kWarps];
     __shared__ int s_item;
     const int tid = threadIdx.x;
+    grid_dependency_prologue();
 
     for (;;) {
         __syncthreads();   // the previous item is done with shared memory
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
             int *dst = reinterpret_cast<int *>(&s_rc);
             for (int i = tid; i < static_cast<int>(sizeof(RobotConst) / 4); i += kBlock) dst[i] = __ldg(src + i);
         }
-        load_state(s_inst.in, s_state);
+        load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
         __syncthreads();
         const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
         TileJob job = s_inst.job;
@@ -96,6 +97,66 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     }
 }
 
+// The same work list when every item has a one-step shape ((1,16,1),
+// (1,32,1) or (1,32,2): H <= 64, the default shapes up to there): the item's
+// shape selects one of three compile-time instantiations of the block loop,
+// so, as in the single-instance kernel, the shape folds away and each step's
+// state is staged in shared memory, and the kernel is fitted to MINB blocks
+// per SM (the run-time-shape kernel above holds 4).
+constexpr int kBatchC1Steps = 64;   // C * L * P of the widest one-step shape
+
+template <typename GT, bool SELF, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __grid_constant__ BatchArgs ba)
+{
+    extern __shared__ float s_dyn[];
+    __shared__ RobotConst s_rc;
+    __shared__ BatchInstance s_inst;
+    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
+    __shared__ float s_S[kWarps / 2 + 1][2][2];
+    __shared__ float s_state[kStateFloats];
+    __shared__ float s_blk[kBatchC1Steps * kNJ];
+    __shared__ float s_wm[kWarps], s_wz[kWarps];
+    __shared__ float s_qs[kWarps * kStageFloats * 32];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    grid_dependency_prologue();
+
+    for (;;) {
+        __syncthreads();   // the previous item is done with shared memory
+        if (tid == 0) s_item = static_cast<int>(atomicAdd(ba.queue, 1u));
+        __syncthreads();
+        const int item = s_item;
+        if (item >= ba.n_work) return;
+        const int2 w = ba.work[item];
+        {
+            const int *src = reinterpret_cast<const int *>(ba.inst + w.x);
+            int *dst = reinterpret_cast<int *>(&s_inst);
+            for (int i = tid; i < static_cast<int>(sizeof(BatchInstance) / 4); i += kBlock) dst[i] = src[i];
+        }
+        __syncthreads();
+        {
+            const int *src = reinterpret_cast<const int *>(s_inst.rc);
+            int *dst = reinterpret_cast<int *>(&s_rc);
+            for (int i = tid; i < static_cast<int>(sizeof(RobotConst) / 4); i += kBlock) dst[i] = __ldg(src + i);
+        }
+        load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
+        __syncthreads();
+        const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
+        TileJob job = s_inst.job;
+        job.iter += ba.it;
+        job.c0 = s_inst.c0;
+        BlockSmem sm{s_dyn, s_dyn + kWarps * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
+                     (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kNJ * 32 : nullptr, s_qs};
+        unsigned ngath = 0;
+        if (s_inst.L == 16)
+            run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 16, 1, w.y, sm, ngath);
+        else if (s_inst.P == 1)
+            run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 32, 1, w.y, sm, ngath);
+        else
+            run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 32, 2, w.y, sm, ngath);
+    }
+}
+
 // Merge items: (instance, first output); one block per kMergeRows outputs
 // of an instance's U*, as the single-instance merge (merge_rows).  The
 // instance's first item also writes min S and adds the k = 0 terms to its
@@ -103,6 +164,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
 __global__ void __launch_bounds__(kMergeThreads)
 batch_merge_kernel(const BatchInstance *inst, const int2 *rows)
 {
+    grid_dependency_prologue();
     const int2 row = rows[blockIdx.x];
     const BatchInstance &I = inst[row.x];
     const float M = merge_rows(I.job.part, I.job.nb, I.job.H * kNJ, row.y, I.job.inv_lambda, I.job.Ubar, I.Uout);
@@ -119,6 +181,7 @@ batch_merge_kernel(const BatchInstance *inst, const int2 *rows)
 // step repeating the last row.
 __global__ void batch_finish_kernel(const BatchInstance *inst, int replan)
 {
+    grid_dependency_prologue();
     const BatchInstance &I = inst[blockIdx.x];
     if (threadIdx.x == 0 && I.best_out) *I.best_out = I.c0[1];
     if (!replan) return;
@@ -146,9 +209,12 @@ namespace {
 struct Plan {
     std::vector<TileShape> shape;
     std::vector<int> nb;
+    bool c1 = false;            // every shape one-step: smpc_batch_kernel_c1
     double us = 0.0;            // measured time of the autotuned candidate (0 = default)
     std::string how;
 };
+
+constexpr int kBatchC1MinBlocks = 6;   // residency the one-step batch kernel is fitted to
 
 constexpr size_t kMaxPlans = 1024;   // cached plans per engine
 constexpr size_t kMaxGraphs = 64;    // cached executable graphs per engine
@@ -167,6 +233,10 @@ struct pm_batch {
     int blocks_per_sm = 1;      // resident batch blocks per SM without the self-collision region
     int bps_call = 1;           // ... for the current call's shared memory
     size_t smem_call = 0;       // dynamic shared memory of the current call
+    int bps_c1 = 1;             // resident one-step batch blocks per SM without the self-collision region
+    int bps_c1_call = 1;        // resident one-step batch blocks per SM for the current call
+    size_t smem_c1_call = 0;    // dynamic shared memory of the one-step kernel for the current call
+    bool self_call = false;     // an item of the current call has the self-collision term
     std::mutex mu;
     std::string err;
     // workspace
@@ -238,6 +308,15 @@ pm_status grow_host(pm_batch *b, T **p, size_t *cap, size_t n)
 }
 
 size_t batch_smem() { return 2u * kWarps * kBatchCMax * kNJ * 32 * sizeof(float); }
+size_t batch_c1_smem() { return 2u * kWarps * kNJ * 32 * sizeof(float); }
+
+using BatchKernel = void (*)(BatchArgs);
+
+BatchKernel c1_kernel(bool self)
+{
+    return self ? smpc_batch_kernel_c1<float, true, kBatchC1MinBlocks>
+                : smpc_batch_kernel_c1<float, false, kBatchC1MinBlocks>;
+}
 
 int blocks_needed(int K, int H, TileShape s)
 {
@@ -255,19 +334,24 @@ Plan make_plan(pm_batch *b, const pm_batch_item *it, int n, double scale, bool w
 {
     Plan p;
     double total = 0.0;
-    for (int i = 0; i < n; ++i) total += static_cast<double>(it[i].K) * it[i].H;
-    const double B = scale * b->n_sm * b->bps_call;
+    p.c1 = true;
     for (int i = 0; i < n; ++i) {
+        total += static_cast<double>(it[i].K) * it[i].H;
         TileShape s = default_shape(it[i].H);
         if (wide && it[i].H > 32 && it[i].H <= 64) s = TileShape{2, 32, 1};
         if (wide && it[i].H > 16 && it[i].H <= 32) s = TileShape{1, 32, 1};
+        p.shape.push_back(s);
+        p.c1 = p.c1 && s.C == 1;
+    }
+    const double B = scale * b->n_sm * (p.c1 ? b->bps_c1_call : b->bps_call);
+    for (int i = 0; i < n; ++i) {
+        const TileShape s = p.shape[i];
         const int need = blocks_needed(it[i].K, it[i].H, s);
         const int share = static_cast<int>(std::lround(B * it[i].K * it[i].H / total));
-        p.shape.push_back(s);
         p.nb.push_back(std::max(1, std::min(need, share)));
     }
     std::ostringstream os;
-    os << "scale=" << scale << (wide ? " wide" : " default");
+    os << "scale=" << scale << (wide ? " wide" : " default") << (p.c1 ? " one-step" : "");
     p.how = os.str();
     return p;
 }
@@ -332,6 +416,7 @@ pm_status stage_batch(pm_batch *b, const pm_batch_item *it, int n, const Plan &p
         I.in.qd0 = x.qd;
         I.in.Tg = x.T_goal;
         for (int j = 0; j < 8; ++j) I.in.sigma[j] = j < kNJ ? x.sigma[j] : 0.f;
+        I.in.dyn = nullptr;
         const size_t na = static_cast<size_t>(x.H) * kNJ;
         I.job.Ubar = x.U;
         I.Uout = x.U;
@@ -346,6 +431,7 @@ pm_status stage_batch(pm_batch *b, const pm_batch_item *it, int n, const Plan &p
         I.job.dt = x.dt;
         I.job.inv_lambda = 1.0f / x.lambda;
         I.job.noise_dtype = c->noise_dtype;
+        I.job.dyn = nullptr;
         I.c0 = b->d_c0 + 2 * i;
         if (flags & PM_BATCH_REPLAN) {
             I.q_out = x.q;
@@ -376,25 +462,27 @@ pm_status stage_batch(pm_batch *b, const pm_batch_item *it, int n, const Plan &p
 // Enqueue (or capture) the whole call: descriptor copies, then per
 // iteration the batch kernel and the merge, then the replan step.
 pm_status enqueue_batch(pm_batch *b, int n, int n_work, int n_rows, int n_iters, int flags,
-                        bool tune, cudaStream_t s)
+                        bool tune, bool c1, cudaStream_t s)
 {
     PM_BCUDA(b, cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, s));
     PM_BCUDA(b, cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int2) * n_work, cudaMemcpyHostToDevice, s));
     PM_BCUDA(b, cudaMemcpyAsync(b->d_rows, b->h_rows, sizeof(int2) * n_rows, cudaMemcpyHostToDevice, s));
     PM_BCUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned) * n_iters, s));
-    const int grid = std::max(1, std::min(n_work, b->n_sm * b->bps_call));
+    const int grid = std::max(1, std::min(n_work, b->n_sm * (c1 ? b->bps_c1_call : b->bps_call)));
+    const BatchKernel kern = c1 ? c1_kernel(b->self_call)
+                                : (b->self_call ? smpc_batch_kernel<float, true> : smpc_batch_kernel<float, false>);
+    const size_t smem = c1 ? b->smem_c1_call : b->smem_call;
     for (int itn = 0; itn < n_iters; ++itn) {
         BatchArgs a{b->d_inst, b->d_work, n_work, b->d_queue + itn, static_cast<uint32_t>(itn)};
-        if (b->smem_call > batch_smem()) smpc_batch_kernel<float, true><<<grid, kBlock, b->smem_call, s>>>(a);
-        else smpc_batch_kernel<float, false><<<grid, kBlock, b->smem_call, s>>>(a);
-        PM_BCUDA(b, cudaGetLastError());
-        batch_merge_kernel<<<n_rows, kMergeThreads, 0, s>>>(b->d_inst, b->d_rows);
-        PM_BCUDA(b, cudaGetLastError());
+        PM_BCUDA(b, launch_dependent(kern, dim3(grid), dim3(kBlock), smem, s, a));
+        PM_BCUDA(b, launch_dependent(batch_merge_kernel, dim3(n_rows), dim3(kMergeThreads), 0, s,
+                                     static_cast<const BatchInstance *>(b->d_inst),
+                                     static_cast<const int2 *>(b->d_rows)));
     }
-    if (!tune) {
-        batch_finish_kernel<<<n, 256, 0, s>>>(b->d_inst, (flags & PM_BATCH_REPLAN) ? 1 : 0);
-        PM_BCUDA(b, cudaGetLastError());
-    }
+    if (!tune)
+        PM_BCUDA(b, launch_dependent(batch_finish_kernel, dim3(n), dim3(256), 0, s,
+                                     static_cast<const BatchInstance *>(b->d_inst),
+                                     (flags & PM_BATCH_REPLAN) ? 1 : 0));
     return PM_OK;
 }
 
@@ -432,7 +520,7 @@ pm_status time_candidate(pm_batch *b, const pm_batch_item *it, int n, int n_iter
     double best = 1e30;
     for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, s);
-        st = enqueue_batch(b, n, nw, nr, n_iters, flags, true, s);
+        st = enqueue_batch(b, n, nw, nr, n_iters, flags, true, p.c1, s);
         cudaEventRecord(e1, s);
         if (st != PM_OK) break;
         cudaEventSynchronize(e1);
@@ -464,7 +552,7 @@ pm_status pm::batch_reserve(pm_batch *b, int max_items, int flags)
     // rounding to at most scale * resident + n/2 in all
     const size_t n = static_cast<size_t>(max_items);
     const double scale = (flags & PM_BATCH_AUTOTUNE) ? 4.0 : 1.0;
-    const size_t work = static_cast<size_t>(scale * b->n_sm * b->blocks_per_sm) + 2 * n;
+    const size_t work = static_cast<size_t>(scale * b->n_sm * std::max(b->blocks_per_sm, b->bps_c1)) + 2 * n;
     const size_t rows = n * ((kBatchMaxSteps * kNJ + kMergeRows - 1) / kMergeRows);
     pm_status st;
     if ((st = grow_dev(b, &b->d_inst, &b->cap_inst, n)) != PM_OK) return st;
@@ -506,6 +594,10 @@ pm_status pm_batch_create(int device, pm_batch **out)
     b->blocks_per_sm = resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float, false>),
                                               kBlock, batch_smem());
     if (b->blocks_per_sm < 1) return fail(PM_ECUDA);
+    b->bps_c1 = resident_blocks_per_sm(reinterpret_cast<const void *>(c1_kernel(false)), kBlock, batch_c1_smem());
+    if (b->bps_c1 < 1) return fail(PM_ECUDA);
+    b->bps_c1_call = b->bps_c1;
+    b->smem_c1_call = batch_c1_smem();
     b->bps_call = b->blocks_per_sm;
     b->smem_call = batch_smem();
     if (prev >= 0) cudaSetDevice(prev);
@@ -530,11 +622,17 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
         b->pending = false;
     }
     b->smem_call = call_smem(items, n);
-    b->bps_call = b->smem_call > batch_smem()
+    b->self_call = b->smem_call > batch_smem();
+    b->bps_call = b->self_call
                       ? resident_blocks_per_sm(reinterpret_cast<const void *>(smpc_batch_kernel<float, true>), kBlock,
                                                b->smem_call)
                       : b->blocks_per_sm;
     if (b->bps_call < 1) return berr(b, PM_ECUDA, "cannot give the batch kernel %zu bytes of shared memory", b->smem_call);
+    b->smem_c1_call = batch_c1_smem() + (b->smem_call - batch_smem());
+    b->bps_c1_call = resident_blocks_per_sm(reinterpret_cast<const void *>(c1_kernel(b->self_call)), kBlock,
+                                            b->smem_c1_call);
+    if (b->bps_c1_call < 1)
+        return berr(b, PM_ECUDA, "cannot give the one-step batch kernel %zu bytes of shared memory", b->smem_c1_call);
     const std::string key = structure_key(items, n, n_iters, flags);
     auto pit = b->plans.find(key);
     if (pit == b->plans.end()) {
@@ -575,7 +673,7 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
             cudaStream_t cap = b->cap;
             cudaGraph_t graph;
             PM_BCUDA(b, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-            pm_status cst = enqueue_batch(b, n, nw, nr, n_iters, flags, false, cap);
+            pm_status cst = enqueue_batch(b, n, nw, nr, n_iters, flags, false, p.c1, cap);
             cudaError_t ce = cudaStreamEndCapture(cap, &graph);
             if (cst != PM_OK) return cst;
             PM_BCUDA(b, ce);
@@ -587,7 +685,7 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
         }
         PM_BCUDA(b, cudaGraphLaunch(g.exec, s));
     } else {
-        if ((st = enqueue_batch(b, n, nw, nr, n_iters, flags, false, s)) != PM_OK) return st;
+        if ((st = enqueue_batch(b, n, nw, nr, n_iters, flags, false, p.c1, s)) != PM_OK) return st;
     }
     PM_BCUDA(b, cudaEventRecord(b->done, s));
     b->pending = true;

@@ -6,6 +6,7 @@
 
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 struct pm_ctx {
@@ -47,6 +48,7 @@ struct pm_ctx {
     float *d_part = nullptr;            // block partials
     size_t cap_part = 0;
 
+    unsigned *d_err = nullptr;          // bounds-checked builds: violation word of the kernels
     float *d_c0 = nullptr;              // small scratch: [0] c0, [1] best, [8, 32) replan q, qd, u0,
                                         // [32, 40) the robot mask's configuration,
                                         // [48, 84) an episode's q, qd, goal and metrics
@@ -58,6 +60,22 @@ struct pm_ctx {
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, end)
     size_t prof_used = 0;               // events recorded since the last reset
     cudaStream_t prof_stream = nullptr;
+    // Host-buffer calls replayed as CUDA graphs (one per call shape): the
+    // call's inputs and scalars go through one fixed pinned block and its
+    // device mirror, so a call is one graph launch instead of 2-17 launches.
+    struct Graph {
+        int kind, K, H, n_iters;
+        bool costs;
+        unsigned gen;
+        const void *part, *costs_d, *costs_h, *c0;   // scratch captured into the graph
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;          // most recently used last
+    unsigned graph_gen = 0;             // bumped when a setting captured in a graph changes
+    bool graphs_on = true;
+    float *d_gslot = nullptr;           // [kGraphSlotFloats] device
+    float *h_gslot = nullptr;           // its pinned mirror
+    cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
     std::string err;
     std::mutex mu;
 };
@@ -99,7 +117,29 @@ inline GridConst grid_const(const pm_ctx *c)
     g.mx = static_cast<float>(c->gd.nx - 1);
     g.my = static_cast<float>(c->gd.ny - 1);
     g.mz = static_cast<float>(c->gd.nz - 1);
+    g.err = c->d_err;
     return g;
+}
+
+// Launch a kernel that may start while its predecessor in the stream is
+// still running (programmatic dependent launch): the kernel's
+// grid_dependency_prologue() waits for the predecessor's completion and
+// memory before anything else, so only the launch latency overlaps.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Resident blocks per SM of an iteration kernel (raises its dynamic shared

@@ -159,27 +159,6 @@ long long launch_blocks(long long K, TileShape sh, long long resident)
 
 size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : 2; }
 
-// Launch a kernel that may start while its predecessor in the stream is
-// still running (programmatic dependent launch): the kernel's
-// grid_dependency_prologue() waits for the predecessor's completion and
-// memory before anything else, so only the launch latency overlaps.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                             Args &&...args)
-{
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
 // ------------------------------------------------------------ small kernels
 __global__ void convert_grid_kernel(const float *src, void *dst, size_t n, int dtype)
 {
@@ -318,9 +297,10 @@ __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint3
 // writes min S = M + c0, and the k = 0 terms c0 are added to the costs.
 __global__ void __launch_bounds__(kMergeThreads)
 softmin_merge_kernel(const float *part, int nb, int na, const float *Ubar, float *Uout,
-                     float inv_lambda, float *c0, float *costs, int K)
+                     float inv_lambda, const float *dyn, float *c0, float *costs, int K)
 {
     grid_dependency_prologue();
+    if (dyn) inv_lambda = __ldg(dyn + kDynInvLambda);
     const float M = merge_rows(part, nb, na, blockIdx.x * kMergeRows, inv_lambda, Ubar, Uout);
     const float k0 = __ldg(c0);
     if (blockIdx.x == 0 && threadIdx.x == 0) c0[1] = M + k0;
@@ -332,10 +312,11 @@ softmin_merge_kernel(const float *part, int nb, int na, const float *Ubar, float
 // Receding-horizon step (Sec. IV-C): execute u0* for one integrator step and
 // shift U one step left, repeating the last row.  One block.
 __global__ void replan_advance_kernel(const float *q0, const float *qd0, float *U, int H, float dt,
-                                      float *q_out, float *qd_out, float *u0_out, const float *c0,
-                                      float *best_out)
+                                      const float *dyn, float *q_out, float *qd_out, float *u0_out,
+                                      const float *c0, float *best_out)
 {
     grid_dependency_prologue();
+    if (dyn) dt = __ldg(dyn + kDynDt);
     __shared__ float sU[kMaxHorizon * kNJ];
     const int n = H * kNJ;
     for (int i = threadIdx.x; i < n; i += blockDim.x) sU[i] = U[i];
@@ -534,11 +515,11 @@ pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, si
     a.noise_dtype = c->noise_dtype;
     a.K = K;
     a.H = H;
-    a.seed_lo = static_cast<uint32_t>(seed & 0xffffffffu);
-    a.seed_hi = static_cast<uint32_t>(seed >> 32);
-    a.iter = iter;
-    a.dt = dt;
-    a.inv_lambda = trace ? 1.0f : 1.0f / lambda;
+    a.cs.seed_lo = static_cast<uint32_t>(seed & 0xffffffffu);
+    a.cs.seed_hi = static_cast<uint32_t>(seed >> 32);
+    a.cs.iter = iter;
+    a.cs.dt = dt;
+    a.cs.inv_lambda = trace ? 1.0f : 1.0f / lambda;
     const bool prof = c->prof && !trace;
     if (prof) {
         while (c->prof_ev.size() < c->prof_used + 2) {
@@ -559,7 +540,7 @@ pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, si
         const int na = H * kNJ;
         PM_CUDA(c, launch_dependent(softmin_merge_kernel, dim3((na + kMergeRows - 1) / kMergeRows),
                                     dim3(kMergeThreads), 0, s, static_cast<const float *>(part), nb, na,
-                                    Ubar, Uout, a.inv_lambda, c0, costs, K));
+                                    Ubar, Uout, a.cs.inv_lambda, in.dyn, c0, costs, K));
         PM_CUDA(c, cudaGetLastError());
     }
     return PM_OK;
@@ -584,6 +565,151 @@ pm_status launch_iteration(pm_ctx *c, cudaStream_t s, const CallInputs &in, cons
 }
 
 cudaStream_t pick_stream(pm_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+// ------------------------------------------------------------ call graphs
+// A call whose inputs and outputs are all host memory (the usual form for a
+// controller) is replayed from a CUDA graph captured once per call shape
+// (kind, K, H, n_iters, costs wanted): its launches read the inputs and the
+// per-call scalars from one fixed device block (g-slot), which the call
+// fills by one copy from its pinned mirror before the graph launch; one
+// copy after it brings the outputs back.  A call then costs one graph
+// launch and two copies on the host instead of 2 (iterate) or
+// 2 n_iters + 1 (replan) kernel launches and two copies, which keeps the
+// GPU fed when the host is slow.  The kernels are the
+// float-field instantiations that read the scalars from that block (DYN),
+// with the same arithmetic, tile shape and blocks as a direct launch, so the
+// results are bit-identical.
+constexpr int kGraphIterate = 1, kGraphReplan = 2;
+constexpr int kGOut = 64;   // replan outputs [q 8][qd 8][u0 8][best]
+constexpr int kGU = 96;     // U [H][7]
+constexpr size_t kGraphSlotFloats = kGU + static_cast<size_t>(kMaxHorizon) * kNJ;
+constexpr size_t kMaxGraphs = 32;
+static_assert(kDynFloats <= kGOut, "call scalars overlap the outputs");
+
+bool graph_ok(const pm_ctx *c)
+{
+    return c->graphs_on && !c->prof && !c->count_gathers && c->gd.dtype == PM_F32 && c->rc.n_self_groups == 0;
+}
+
+void graphs_clear(pm_ctx *c)
+{
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+pm_status graph_capture(pm_ctx *c, int kind, int K, int H, int n_iters, bool costs, cudaGraphExec_t &exec)
+{
+    TileShape sh;
+    pm_status st = pick_shape(c, H, sh);
+    if (st != PM_OK) return st;
+    KernelPick kp;
+    st = pick_kernel(c, K, sh, false, kp);
+    if (st != PM_OK) return st;
+    const bool dense = kp.fn == lookup_dense_kernel(c->gd.dtype, sh);
+    const IterKernel fn = iteration_kernel_f32_dyn(sh.C, sh.L, sh.P, dense);
+    if (!fn) return set_err(c, PM_EINTERNAL, "no graph kernel for C=%d L=%d P=%d", sh.C, sh.L, sh.P);
+    if (resident_blocks_per_sm(reinterpret_cast<const void *>(fn), kBlock, kp.smem) < 1)
+        return set_err(c, PM_ECUDA, "cannot give the graph kernel %zu bytes of shared memory", kp.smem);
+    const int nb = static_cast<int>(launch_blocks(K, sh, kp.resident));
+    st = ensure_capacity(c, K, H, nb);
+    if (st != PM_OK) return st;
+    if (!c->d_gslot) PM_CUDA(c, cudaMalloc(&c->d_gslot, kGraphSlotFloats * sizeof(float)));
+    if (!c->h_gslot) PM_CUDA(c, cudaMallocHost(&c->h_gslot, kGraphSlotFloats * sizeof(float)));
+    if (!c->cap_stream) PM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+
+    float *d = c->d_gslot;
+    CallInputs in{};
+    in.q0 = d;
+    in.qd0 = d + 8;
+    in.Tg = d + 16;
+    in.dyn = d;
+    float *U = d + kGU;
+    const size_t nU = static_cast<size_t>(H) * kNJ;
+    cudaStream_t s = c->cap_stream;
+    PM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    // nothing may return between here and the end of the capture
+    pm_status cst = PM_OK;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < n_iters && e == cudaSuccess && cst == PM_OK; ++it)
+        cst = enqueue_iteration(c, s, fn, nb, kp.smem, in, U, U, costs ? c->d_costs : nullptr, c->d_part, c->d_c0,
+                                K, H, 0.f, 1.f, 0, static_cast<uint32_t>(it), false, nullptr, nullptr);
+    if (e == cudaSuccess && cst == PM_OK) {
+        if (kind == kGraphReplan) {
+            e = launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, U, H, 0.f,
+                                 in.dyn, d + kGOut, d + kGOut + 8, d + kGOut + 16,
+                                 static_cast<const float *>(c->d_c0), d + kGOut + 24);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (cst != PM_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (cst != PM_OK) return cst;
+        return set_err(c, PM_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, PM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return PM_OK;
+}
+
+// The graph of a call shape, captured on first use (the least recently used
+// graph is dropped beyond kMaxGraphs).  A graph is reused only while the
+// scratch it captured is still the context's.
+pm_status graph_get(pm_ctx *c, int kind, int K, int H, int n_iters, bool costs, cudaGraphExec_t &exec)
+{
+    for (size_t i = 0; i < c->graphs.size(); ++i) {
+        const pm_ctx::Graph &g = c->graphs[i];
+        if (g.kind == kind && g.K == K && g.H == H && g.n_iters == n_iters && g.costs == costs &&
+            g.gen == c->graph_gen && g.part == c->d_part && g.costs_d == c->d_costs && g.costs_h == c->h_out &&
+            g.c0 == c->d_c0) {
+            const pm_ctx::Graph hit = g;
+            c->graphs.erase(c->graphs.begin() + static_cast<long>(i));
+            c->graphs.push_back(hit);
+            exec = hit.exec;
+            return PM_OK;
+        }
+    }
+    pm_status st = graph_capture(c, kind, K, H, n_iters, costs, exec);
+    if (st != PM_OK) return st;
+    // scratch growth inside the capture may have moved buffers that older
+    // graphs captured: drop those now
+    for (size_t i = 0; i < c->graphs.size();) {
+        const pm_ctx::Graph &g = c->graphs[i];
+        if (g.gen != c->graph_gen || g.part != c->d_part || g.costs_d != c->d_costs || g.costs_h != c->h_out) {
+            cudaGraphExecDestroy(g.exec);
+            c->graphs.erase(c->graphs.begin() + static_cast<long>(i));
+        } else {
+            ++i;
+        }
+    }
+    if (c->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({kind, K, H, n_iters, costs, c->graph_gen, c->d_part, c->d_costs, c->h_out, c->d_c0, exec});
+    return PM_OK;
+}
+
+// Inputs and scalars of a host-buffer call into the pinned g-slot.
+void graph_fill(pm_ctx *c, const float *q0, const float *qd0, const float *T_goal, const float *sigma, float dt,
+                float lambda, uint64_t seed, uint32_t iter0, const float *U, int H)
+{
+    float *h = c->h_gslot;
+    std::memcpy(h, q0, kNJ * sizeof(float));
+    std::memcpy(h + 8, qd0, kNJ * sizeof(float));
+    std::memcpy(h + 16, T_goal, 16 * sizeof(float));
+    for (int j = 0; j < 8; ++j) h[kDynSigma + j] = j < kNJ ? sigma[j] : 0.f;
+    h[kDynDt] = dt;
+    h[kDynInvLambda] = 1.0f / lambda;
+    const uint32_t w[3] = {static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), iter0};
+    std::memcpy(h + kDynSeedLo, w, sizeof(w));
+    std::memcpy(h + kGU, U, static_cast<size_t>(H) * kNJ * sizeof(float));
+}
 
 } // namespace
 
@@ -665,8 +791,8 @@ pm_status pm::replan_with_scratch(pm_ctx *c, cudaStream_t s, const CallInputs &i
                                lambda, seed, iter0 + static_cast<uint32_t>(it), false, nullptr, nullptr);
         if (st != PM_OK) return st;
     }
-    PM_CUDA(c, launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, U, H, dt, q_out,
-                                qd_out, u0_out, static_cast<const float *>(c0), best_out));
+    PM_CUDA(c, launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, U, H, dt, in.dyn,
+                                q_out, qd_out, u0_out, static_cast<const float *>(c0), best_out));
     PM_CUDA(c, cudaGetLastError());
     return PM_OK;
 }
@@ -952,6 +1078,11 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     }
     if (!ck(cudaMemcpy(c->d_rc, &c->rc, sizeof(RobotConst), cudaMemcpyHostToDevice), "robot constants copy"))
         return fail(PM_ECUDA);
+#ifdef PM_BOUNDS_CHECK
+    if (!ck(cudaMalloc(&c->d_err, sizeof(unsigned)), "bounds word") ||
+        !ck(cudaMemset(c->d_err, 0, sizeof(unsigned)), "bounds word"))
+        return fail(PM_ECUDA);
+#endif
     // Load every iteration kernel this context may launch now (modules load
     // lazily by default), so that the first call of a new tile shape or
     // residency does not stall on it; the occupancy of each is cached.
@@ -1013,6 +1144,23 @@ pm_status pm_smpc_iterate(pm_ctx *c, const float *q0, const float *qd0, const fl
     if (!dU && !finite_all(U, H * kNJ)) return set_err(c, PM_EINVAL, "U has a non-finite entry");
     const bool dC = costs_out && is_device_ptr(costs_out);
     cudaStream_t s = pick_stream(c, cuda_stream);
+    if (graph_ok(c) && !dU && !dC && !is_device_ptr(q0) && !is_device_ptr(qd0) && !is_device_ptr(T_goal)) {
+        cudaGraphExec_t ex = nullptr;
+        st = graph_get(c, kGraphIterate, K, H, 1, costs_out != nullptr, ex);
+        if (st != PM_OK) return st;
+        graph_fill(c, q0, qd0, T_goal, sigma, dt, lambda, seed, iter_index, U, H);
+        const size_t nU = static_cast<size_t>(H) * kNJ;
+        PM_CUDA(c, cudaMemcpyAsync(c->d_gslot, c->h_gslot, (kGU + nU) * sizeof(float), cudaMemcpyHostToDevice, s));
+        PM_CUDA(c, cudaGraphLaunch(ex, s));
+        PM_CUDA(c, cudaMemcpyAsync(c->h_gslot + kGU, c->d_gslot + kGU, nU * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (costs_out)
+            PM_CUDA(c, cudaMemcpyAsync(c->h_out, c->d_costs, static_cast<size_t>(K) * sizeof(float),
+                                       cudaMemcpyDeviceToHost, s));
+        PM_CUDA(c, cudaStreamSynchronize(s));
+        std::memcpy(U, c->h_gslot + kGU, sizeof(float) * nU);
+        if (costs_out) std::memcpy(costs_out, c->h_out, sizeof(float) * K);
+        return PM_OK;
+    }
     st = ensure_capacity(c, K, H, 1);
     if (st != PM_OK) return st;
     // a host U travels with the inputs through the staging slot
@@ -1051,6 +1199,25 @@ pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *
     const bool dq = is_device_ptr(q), dqd = is_device_ptr(qd);
     const bool du0 = u0_out && is_device_ptr(u0_out), dbest = best_cost && is_device_ptr(best_cost);
     cudaStream_t s = pick_stream(c, cuda_stream);
+    if (graph_ok(c) && !dU && !dq && !dqd && !du0 && !dbest && !is_device_ptr(T_goal)) {
+        cudaGraphExec_t ex = nullptr;
+        st = graph_get(c, kGraphReplan, K, H, n_iters, false, ex);
+        if (st != PM_OK) return st;
+        graph_fill(c, q, qd, T_goal, sigma, dt, lambda, seed, replan_index * static_cast<uint32_t>(n_iters), U, H);
+        const size_t nU = static_cast<size_t>(H) * kNJ;
+        PM_CUDA(c, cudaMemcpyAsync(c->d_gslot, c->h_gslot, (kGU + nU) * sizeof(float), cudaMemcpyHostToDevice, s));
+        PM_CUDA(c, cudaGraphLaunch(ex, s));
+        PM_CUDA(c, cudaMemcpyAsync(c->h_gslot + kGOut, c->d_gslot + kGOut, (kGU - kGOut + nU) * sizeof(float),
+                                   cudaMemcpyDeviceToHost, s));
+        PM_CUDA(c, cudaStreamSynchronize(s));
+        const float *h = c->h_gslot + kGOut;
+        std::memcpy(q, h, kNJ * sizeof(float));
+        std::memcpy(qd, h + 8, kNJ * sizeof(float));
+        if (u0_out) std::memcpy(u0_out, h + 16, kNJ * sizeof(float));
+        if (best_cost) *best_cost = h[24];
+        std::memcpy(U, c->h_gslot + kGU, sizeof(float) * H * kNJ);
+        return PM_OK;
+    }
     st = ensure_capacity(c, K, H, 1);
     if (st != PM_OK) return st;
     CallInputs in{};
@@ -1066,7 +1233,7 @@ pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *
     }
     float *small = io.d;  // [q 8][qd 8][u0 8][min S] for host outputs, then U when staged
     PM_CUDA(c, launch_dependent(replan_advance_kernel, dim3(1), dim3(256), 0, s, in.q0, in.qd0, Ud, H, dt,
-                                dq ? q : small, dqd ? qd : small + 8,
+                                static_cast<const float *>(nullptr), dq ? q : small, dqd ? qd : small + 8,
                                 u0_out ? (du0 ? u0_out : small + 16) : static_cast<float *>(nullptr),
                                 static_cast<const float *>(c->d_c0),
                                 best_cost ? (dbest ? best_cost : small + 24) : static_cast<float *>(nullptr)));
@@ -1318,6 +1485,39 @@ pm_status pm_set_noise_dtype(pm_ctx *c, int dtype)
         return set_err(c, PM_EINVAL, "noise dtype %d unknown", dtype);
     std::lock_guard<std::mutex> lk(c->mu);
     c->noise_dtype = dtype;
+    ++c->graph_gen;
+    return PM_OK;
+}
+
+int pm_bounds_checked(void)
+{
+#ifdef PM_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+pm_status pm_bounds_status(pm_ctx *c, unsigned *word, int reset)
+{
+    if (!c || !word) return set_err(c, PM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    *word = 0;
+    if (!c->d_err) return PM_OK;
+    PM_CUDA(c, cudaDeviceSynchronize());
+    PM_CUDA(c, cudaMemcpy(word, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (reset) PM_CUDA(c, cudaMemset(c->d_err, 0, sizeof(unsigned)));
+    return PM_OK;
+}
+
+pm_status pm_set_call_graphs(pm_ctx *c, int enable)
+{
+    if (!c) return set_err(nullptr, PM_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    c->graphs_on = enable != 0;
+    if (!c->graphs_on) graphs_clear(c);
     return PM_OK;
 }
 
@@ -1328,10 +1528,12 @@ pm_status pm_set_tile_shape(pm_ctx *c, int C, int L, int P)
     const TileShape t{C, L, P};
     if (C == 0 && L == 0 && P == 0) {
         c->forced = t;
+        ++c->graph_gen;
         return PM_OK;
     }
     if (!shape_known(t)) return set_err(c, PM_EINVAL, "no kernel for tile shape C=%d L=%d P=%d", C, L, P);
     c->forced = t;
+    ++c->graph_gen;
     return PM_OK;
 }
 
@@ -1380,7 +1582,12 @@ void pm_destroy(pm_ctx *c)
         cudaFree(c->d_part);
 
         cudaFree(c->d_c0);
+        cudaFree(c->d_err);
         cudaFree(c->d_gathers);
+        graphs_clear(c);
+        cudaFree(c->d_gslot);
+        cudaFreeHost(c->h_gslot);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
         for (cudaEvent_t e : c->slot_ev)
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);

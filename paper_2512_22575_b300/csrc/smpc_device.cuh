@@ -104,6 +104,44 @@ struct GridConst {
     float inv_res;
     float bx, by, bz;             // -origin / res - 1/2: grid coordinate g = p / res + b
     float mx, my, mz;             // n - 1 (clamp bound)
+    unsigned *err;                // bounds-checked builds: the context's violation word (else null)
+};
+
+// ------------------------------------------------------------ bounds checks
+// A library built with PM_BOUNDS_CHECK checks the index of every field
+// gather, shared-memory slot and partial / cost / trace write of the
+// iteration kernels against its extent.  A violation sets its bit in the
+// context's word (GridConst::err) and the access is skipped (a read takes
+// element 0 instead); nothing traps.  In the normal build the checks
+// compile away.
+constexpr unsigned kErrField = 1u, kErrTile = 2u, kErrStage = 4u, kErrBlock = 8u, kErrUbar = 16u,
+                   kErrCosts = 32u, kErrPartial = 64u, kErrTrace = 128u, kErrSelf = 256u;
+
+__device__ __forceinline__ bool pm_ok(bool in_bounds, unsigned code, const GridConst &g)
+{
+#ifdef PM_BOUNDS_CHECK
+    if (!in_bounds) {
+        if (g.err) atomicOr(g.err, code);
+        return false;
+    }
+    return true;
+#else
+    (void)in_bounds; (void)code; (void)g;
+    return true;
+#endif
+}
+
+// index i of an array of n elements, or 0 (flagged) when out of range
+__device__ __forceinline__ long long pm_idx(long long i, long long n, unsigned code, const GridConst &g)
+{
+    return pm_ok(i >= 0 && i < n, code, g) ? i : 0;
+}
+
+// The scalars of one launch: Philox key words, iteration index (the
+// counter's last word), dt and 1/lambda.
+struct CallScalars {
+    uint32_t seed_lo, seed_hi, iter;
+    float dt, inv_lambda;
 };
 
 // Per-call state as each block holds it in shared memory.
@@ -112,28 +150,46 @@ struct InstanceState {
     float Rg[9];                  // row-major R_g
     float tg[3];
     float sigma[8];
+    CallScalars cs;               // filled only from a call's device block (CallInputs::dyn)
 };
 
+// Per-call scalars in device memory (a replayed graph's launches read them
+// there, so one graph serves every call of its shape): floats
+// [kDynSigma, +7) sigma, then dt, 1/lambda and the words seed_lo, seed_hi and
+// iter0 (the iteration index of the call's first iteration).
+constexpr int kDynSigma = 32, kDynDt = 40, kDynInvLambda = 41, kDynSeedLo = 42, kDynSeedHi = 43,
+              kDynIter0 = 44, kDynFloats = 48;
+
 // Per-call inputs: device pointers to q_0, qdot_0 [7] and the row-major goal
-// pose [16]; sigma by value.
+// pose [16]; sigma by value.  dyn: null, or the call's device block (sigma
+// and the scalars are then read from it; see kDyn*).
 struct CallInputs {
     const float *q0, *qd0, *Tg;
     float sigma[8];
+    const float *dyn;
 };
 
 // Fill the shared-memory state from the call inputs (threads of one block).
-__device__ __forceinline__ void load_state(const CallInputs &in, float *s_state)
+// With in.dyn the call's scalars come from its device block, the iteration
+// index as iter0 + cs.iter (cs: the launch's arguments).
+__device__ __forceinline__ void load_state(const CallInputs &in, const CallScalars &cs, float *s_state)
 {
     InstanceState &st = *reinterpret_cast<InstanceState *>(s_state);
     const int t = threadIdx.x;
     if (t < kNJ) {
         st.q0[t] = in.q0[t];
         st.qd0[t] = in.qd0[t];
-        st.sigma[t] = in.sigma[t];
+        st.sigma[t] = in.dyn ? in.dyn[kDynSigma + t] : in.sigma[t];
     } else if (t >= 32 && t < 44) {
         const int i = t - 32, r = i >> 2, c = i & 3;   // rows 0-2 of T_goal
         if (c < 3) st.Rg[3 * r + c] = in.Tg[4 * r + c];
         else st.tg[r] = in.Tg[4 * r + 3];
+    } else if (t == 64 && in.dyn) {
+        st.cs.seed_lo = __float_as_uint(in.dyn[kDynSeedLo]);
+        st.cs.seed_hi = __float_as_uint(in.dyn[kDynSeedHi]);
+        st.cs.iter = __float_as_uint(in.dyn[kDynIter0]) + cs.iter;
+        st.cs.dt = in.dyn[kDynDt];
+        st.cs.inv_lambda = in.dyn[kDynInvLambda];
     }
 }
 constexpr int kStateFloats = sizeof(InstanceState) / sizeof(float);
@@ -294,6 +350,7 @@ template <typename T>
 __device__ __forceinline__ void corners(const GridConst &g, int base, float v[8])
 {
     const int sy = g.nx, sz = g.nx * g.ny;
+    base = static_cast<int>(pm_idx(base, static_cast<long long>(sz) * g.nz - sz - sy - 1, kErrField, g));
     const T *b = static_cast<const T *>(g.phi) + base;
     v[0] = grid_load(b);          v[1] = grid_load(b + 1);
     v[2] = grid_load(b + sy);     v[3] = grid_load(b + sy + 1);

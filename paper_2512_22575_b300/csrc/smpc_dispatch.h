@@ -41,6 +41,11 @@ IterKernel iteration_kernel_bf16_self(int C, int L, int P, bool trace);
 // The kDenseBlocks instantiation of a one-step shape ((1,16,1), (1,32,1),
 // (1,32,2)) without tracing or the self term; nullptr for other shapes.
 IterKernel iteration_kernel_f32_dense(int C, int L, int P);
+// Float-field kernels that read the call's scalars from its device block
+// (CallInputs::dyn), for launches captured once in a graph and replayed:
+// the default-residency instantiation of a shape, or with dense its
+// kDenseBlocks one (one-step shapes only); nullptr if not instantiated.
+IterKernel iteration_kernel_f32_dyn(int C, int L, int P, bool dense);
 IterKernel iteration_kernel_f16_dense(int C, int L, int P);
 IterKernel iteration_kernel_bf16_dense(int C, int L, int P);
 
@@ -75,6 +80,33 @@ IterKernel iteration_kernel_bf16_dense(int C, int L, int P);
         if (C == 1 && L == 16 && P == 1) return smpc_iteration_kernel<1, 16, 1, GT, false, false, kDenseBlocks>; \
         if (C == 1 && L == 32 && P == 1) return smpc_iteration_kernel<1, 32, 1, GT, false, false, kDenseBlocks>; \
         if (C == 1 && L == 32 && P == 2) return smpc_iteration_kernel<1, 32, 2, GT, false, false, kDenseBlocks>; \
+        return nullptr;                                                                \
+    }                                                                                  \
+    }
+
+#define PM_DYN_CASE(C_, L_, P_)                                                             \
+    if (C == C_ && L == L_ && P == P_)                                                   \
+        return smpc_iteration_kernel<C_, L_, P_, float, false, false, (C_ == 1 ? 6 : 5), true>;
+
+#define PM_INSTANTIATE_DYN_TABLE(NAME)                                                      \
+    namespace pm {                                                                     \
+    IterKernel NAME(int C, int L, int P, bool dense)                                   \
+    {                                                                                  \
+        if (dense) {                                                                   \
+            if (C == 1 && L == 16 && P == 1) return smpc_iteration_kernel<1, 16, 1, float, false, false, kDenseBlocks, true>; \
+            if (C == 1 && L == 32 && P == 1) return smpc_iteration_kernel<1, 32, 1, float, false, false, kDenseBlocks, true>; \
+            if (C == 1 && L == 32 && P == 2) return smpc_iteration_kernel<1, 32, 2, float, false, false, kDenseBlocks, true>; \
+            return nullptr;                                                            \
+        }                                                                              \
+        PM_DYN_CASE(1, 16, 1)                                                          \
+        PM_DYN_CASE(1, 32, 1)                                                          \
+        PM_DYN_CASE(3, 16, 1)                                                          \
+        PM_DYN_CASE(2, 32, 1)                                                          \
+        PM_DYN_CASE(4, 32, 1)                                                          \
+        PM_DYN_CASE(8, 32, 1)                                                          \
+        PM_DYN_CASE(1, 32, 2)                                                          \
+        PM_DYN_CASE(2, 32, 2)                                                          \
+        PM_DYN_CASE(4, 32, 2)                                                          \
         return nullptr;                                                                \
     }                                                                                  \
     }

@@ -67,8 +67,7 @@ struct IterArgs {
     unsigned long long *gathers;  // if not null: += number of 8-corner lookups performed
     int noise_dtype;            // PM_F32 (0), PM_F16 (1) or PM_BF16 (2): rounding of eps
     int K, H;
-    uint32_t seed_lo, seed_hi, iter;
-    float dt, inv_lambda;
+    CallScalars cs;             // seed, iteration index, dt, 1/lambda (see CallInputs::dyn)
 };
 
 // ------------------------------------------------------------ cost terms
@@ -108,7 +107,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         f3 v{};
         if (SELF && sp) {
             v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
-            if (rc.self_frames) {
+            if (rc.self_frames && pm_ok(kSelfFrameSlots * j + 5 < self_slots(rc.n_spheres, true), kErrSelf, g)) {
                 float *fs = sp + kSelfFrameSlots * j * 32;
                 fs[0] = F.t.x; fs[32] = F.t.y; fs[64] = F.t.z;
                 fs[96] = v.x; fs[128] = v.y; fs[160] = v.z;
@@ -122,7 +121,8 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                 const int s = s0 + i;               // past e: zero padding, masked below
                 ls[i] = rc.sph_ls[s];
                 const float lam = ls[i].x;
-                if (SELF && sp && !rc.self_frames && i < e - s0) {   // kept for the self-collision term
+                if (SELF && sp && !rc.self_frames && i < e - s0 &&
+                    pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {   // kept for the self term
                     const f3 p = axpy(lam, v, F.t);
                     sp[(3 * s) * 32] = p.x;
                     sp[(3 * s + 1) * 32] = p.y;
@@ -159,7 +159,8 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = s0 + i;               // past e: zero padding, masked below
             const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
-            if (SELF && sp && !rc.self_frames && i < e - s0) {   // kept for the self-collision term
+            if (SELF && sp && !rc.self_frames && i < e - s0 &&
+                pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {   // kept for the self term
                 sp[(3 * s) * 32] = p.x;
                 sp[(3 * s + 1) * 32] = p.y;
                 sp[(3 * s + 2) * 32] = p.z;
@@ -346,7 +347,8 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
             for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
         }
         if (!terminal) env += link_env<GT, SELF>(rc, g, F, j, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
-        if (SELF && sp) {
+        if (SELF && sp && pm_ok((rc.self_frames ? kSelfFrameSlots * j + 8 : 3 * rc.n_spheres + 3 * j + 2) <
+                                    self_slots(rc.n_spheres, rc.self_frames), kErrSelf, g)) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
             const int t = rc.self_frames ? kSelfFrameSlots * j + 6 : 3 * rc.n_spheres + 3 * j;
             sp[t * 32] = c.x;
@@ -415,7 +417,33 @@ struct TileJob {
     uint32_t seed_lo, seed_hi, iter;
     float dt, inv_lambda;
     int noise_dtype;
+    // DYN kernels: the call's scalars in shared memory (they replace the five
+    // above), read where they are used so that they hold no registers
+    const CallScalars *dyn;
 };
+
+// A call scalar of a tile job: the field, or with DYN its copy in shared
+// memory, loaded at the point of use.
+template <bool DYN> __device__ __forceinline__ uint32_t job_seed_lo(const TileJob &j)
+{
+    return DYN ? *reinterpret_cast<const volatile uint32_t *>(&j.dyn->seed_lo) : j.seed_lo;
+}
+template <bool DYN> __device__ __forceinline__ uint32_t job_seed_hi(const TileJob &j)
+{
+    return DYN ? *reinterpret_cast<const volatile uint32_t *>(&j.dyn->seed_hi) : j.seed_hi;
+}
+template <bool DYN> __device__ __forceinline__ uint32_t job_iter(const TileJob &j)
+{
+    return DYN ? *reinterpret_cast<const volatile uint32_t *>(&j.dyn->iter) : j.iter;
+}
+template <bool DYN> __device__ __forceinline__ float job_dt(const TileJob &j)
+{
+    return DYN ? *reinterpret_cast<const volatile float *>(&j.dyn->dt) : j.dt;
+}
+template <bool DYN> __device__ __forceinline__ float job_inv_lambda(const TileJob &j)
+{
+    return DYN ? *reinterpret_cast<const volatile float *>(&j.dyn->inv_lambda) : j.inv_lambda;
+}
 
 // Shared-memory arrays a block needs for run_block.
 struct BlockSmem {
@@ -435,7 +463,7 @@ constexpr int kStageFloats = 2 * kNJ + 1;
 // block partial (m_b, z_b, acc_b) into job.part.  Tile shape (C, L, P) as
 // described at the top of this file; called by every thread of the block.
 // With constant arguments (the single-instance kernel) the shape folds away.
-template <typename GT, bool TRACE, bool SELF, bool STAGE>
+template <typename GT, bool TRACE, bool SELF, bool STAGE, bool DYN = false>
 __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst &g,
                                           const InstanceState &st, const TileJob &job,
                                           float *trace, const int C, const int L, const int P,
@@ -445,15 +473,18 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     const int R = 32 / L;
     const int seg = lane / L, sl = lane % L;
     const int H = job.H;
-    auto E = [&](int w, int s, int j) { return ((w * C + s) * kNJ + j) * 32; };
-    for (int i = tid; i < C * L * P * kNJ; i += kBlock) sm.blk[i] = 0.f;
+    // slot (w, s, j) of the [kWarps][C][7][32] tile arrays (lane added by the caller)
+    auto E = [&](int w, int s, int j) {
+        return static_cast<int>(pm_idx(((w * C + s) * kNJ + j) * 32, kWarps * C * kNJ * 32 - 31, kErrTile, g));
+    };
+    for (int i = tid; i < C * L * P * kNJ; i += kBlock) sm.blk[i] = 0.f;   // s_blk holds C L P 7 floats
     for (int s = 0; s < C; ++s)
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) sm.acc[E(warp, s, j) + lane] = 0.f;
     __syncthreads();
 
     float run_m = CUDART_INF_F, run_z = 0.f;
-    const float dt = job.dt, dt2 = job.dt * job.dt;
+    const float dt = job_dt<DYN>(job), dt2 = dt * dt;
     float *sp = (SELF && rc.n_self_groups > 0 && sm.self)
                     ? sm.self + warp * self_slots(rc.n_spheres, rc.self_frames) * 32 + lane : nullptr;
     const int half = (P == 2) ? (warp & 1) : 0;
@@ -487,7 +518,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             float z[8];
             const bool live = active && k < H;
             if (live) {
-                step_normals(job.seed_lo, job.seed_hi, job.iter, static_cast<uint32_t>(m),
+                step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
                              static_cast<uint32_t>(k), z);
             }
 #pragma unroll
@@ -496,7 +527,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 // precision variant: eps rounded as if stored in FP16 / BF16
                 if (job.noise_dtype == 1) e = __half2float(__float2half_rn(e));
                 else if (job.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
-                const float u = live ? __ldg(job.Ubar + k * kNJ + j) + e : 0.f;
+                const float u = live ? __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + e : 0.f;
                 sm.eps[E(warp, s, j) + lane] = e;
                 T[j] += u;
                 TB[j] += T[j];
@@ -546,18 +577,21 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 const int k = kbase + sl * C + s;
                 if (!(active && k < H)) break;
                 float u[kNJ];
-                float *qs = sm.qs + ((warp * C + s) * kStageFloats) * 32 + lane;
+                float *qs = sm.qs + pm_idx(((warp * C + s) * kStageFloats) * 32, kWarps * kStageFloats * 32 -
+                                           (kStageFloats - 1) * 32 - 31, kErrStage, g) + lane;
                 const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
-                    u[j] = __ldg(job.Ubar + k * kNJ + j) + sm.eps[E(warp, s, j) + lane];
+                    u[j] = __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + sm.eps[E(warp, s, j) + lane];
                     runU[j] += u[j];
                     const float A = A0[j] + runU[j];           // A_{k+1}
                     runB[j] += A;                               // B_{k+1}
                     qs[j * 32] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
                     qs[(kNJ + j) * 32] = fmaf(dt, A, st.qd0[j]);
                 }
-                float *tr_u = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols : nullptr;
+                float *tr_u = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k,
+                                                    static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
+                                   : nullptr;
                 qs[(2 * kNJ) * 32] = control_cost<TRACE>(rc, u, tr_u);
             }
         }
@@ -575,12 +609,15 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             float q[kNJ], qd[kNJ], cc = 0.f;
             const float *qa = st.q0;
             int qstride = 1;
-            float *tr_x = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k + 1) * kTraceCols : nullptr;
+            float *tr_x = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k + 1,
+                                                static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
+                               : nullptr;
             if (extra) {
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) { q[j] = st.q0[j]; qd[j] = st.qd0[j]; }
             } else if (STAGE) {
-                const float *qs = sm.qs + ((warp * C + s) * kStageFloats) * 32 + lane;
+                const float *qs = sm.qs + pm_idx(((warp * C + s) * kStageFloats) * 32, kWarps * kStageFloats * 32 -
+                                                 (kStageFloats - 1) * 32 - 31, kErrStage, g) + lane;
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) { q[j] = qs[j * 32]; qd[j] = qs[(kNJ + j) * 32]; }
                 cc = qs[(2 * kNJ) * 32];
@@ -591,14 +628,16 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
-                    u[j] = __ldg(job.Ubar + k * kNJ + j) + sm.eps[E(warp, s, j) + lane];
+                    u[j] = __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + sm.eps[E(warp, s, j) + lane];
                     runU[j] += u[j];
                     const float A = A0[j] + runU[j];           // A_{k+1}
                     runB[j] += A;                               // B_{k+1}
                     qd[j] = fmaf(dt, A, st.qd0[j]);
                     q[j] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
                 }
-                float *tr_u = TRACE ? trace + (static_cast<size_t>(m) * (H + 1) + k) * kTraceCols : nullptr;
+                float *tr_u = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k,
+                                                    static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
+                                   : nullptr;
                 cc = control_cost<TRACE>(rc, u, tr_u);
             }
             const unsigned ng0 = ngath;
@@ -631,13 +670,13 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             S = ns + ((sm.S[pr][0][1] + sm.S[pr][1][1]) + e);
         }
         if (TRACE) continue;
-        if (active && sl == 0 && half == 0 && job.costs) job.costs[m] = S;
+        if (active && sl == 0 && half == 0 && job.costs && pm_ok(m < job.K, kErrCosts, g)) job.costs[m] = S;
 
         // online soft-min accumulation (Eqs. 29-30)
         if (active) {
             const float nm = fminf(run_m, S);
-            const float f_old = weight_factor(run_m, nm, job.inv_lambda);
-            const float f_new = expf((nm - S) * job.inv_lambda);
+            const float f_old = weight_factor(run_m, nm, job_inv_lambda<DYN>(job));
+            const float f_new = expf((nm - S) * job_inv_lambda<DYN>(job));
             run_z = fmaf(run_z, f_old, f_new);
 #pragma unroll 1
             for (int s = 0; s < C; ++s)
@@ -656,8 +695,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         const float om = __shfl_xor_sync(0xffffffffu, run_m, off);
         const float oz = __shfl_xor_sync(0xffffffffu, run_z, off);
         const float nm = fminf(run_m, om);
-        const float fa = weight_factor(run_m, nm, job.inv_lambda);
-        const float fb = weight_factor(om, nm, job.inv_lambda);
+        const float fa = weight_factor(run_m, nm, job_inv_lambda<DYN>(job));
+        const float fb = weight_factor(om, nm, job_inv_lambda<DYN>(job));
         run_z = run_z * fa + oz * fb;
 #pragma unroll 1
         for (int s = 0; s < C; ++s)
@@ -676,12 +715,12 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     float Mb = CUDART_INF_F;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) Mb = fminf(Mb, sm.wm[w]);
-    const float fw = weight_factor(run_m, Mb, job.inv_lambda);
+    const float fw = weight_factor(run_m, Mb, job_inv_lambda<DYN>(job));
     for (int w = 0; w < kWarps; ++w) {
         if (warp == w && seg == 0) {
             for (int s = 0; s < C; ++s) {
                 const int k = kbase + sl * C + s;
-                if (k < H) {
+                if (k < H && pm_ok(k < C * L * P, kErrBlock, g)) {
 #pragma unroll
                     for (int j = 0; j < kNJ; ++j)
                         sm.blk[k * kNJ + j] = fmaf(fw, sm.acc[E(warp, s, j) + lane], sm.blk[k * kNJ + j]);
@@ -692,15 +731,16 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     }
     const int na = H * kNJ;
     const int nb = job.nb;
-    if (tid == 0) {
+    if (tid == 0 && pm_ok(lb < nb, kErrPartial, g)) {
         float zb = 0.f;
         // a pair's two warps carry the same (m, z): count it once
-        for (int w = 0; w < kWarps; w += P) zb += sm.wz[w] * weight_factor(sm.wm[w], Mb, job.inv_lambda);
+        for (int w = 0; w < kWarps; w += P) zb += sm.wz[w] * weight_factor(sm.wm[w], Mb, job_inv_lambda<DYN>(job));
         job.part[lb] = Mb;
         job.part[nb + lb] = zb;
     }
     float *acc_b = job.part + 2 * static_cast<size_t>(nb) + lb;
-    for (int i = tid; i < na; i += kBlock) acc_b[static_cast<size_t>(i) * nb] = sm.blk[i];
+    if (pm_ok(lb < nb && na <= C * L * P * kNJ, kErrPartial, g))
+        for (int i = tid; i < na; i += kBlock) acc_b[static_cast<size_t>(i) * nb] = sm.blk[i];
 }
 
 // ------------------------------------------------------------------ kernel
@@ -715,7 +755,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 // shapes also have a kDenseBlocks instantiation (72 registers, neither
 // spills), which the host picks when its extra units save a round of
 // tiles on a short launch.
-template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 ? 6 : 5)>
+template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 ? 6 : 5), bool DYN = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
                       const __grid_constant__ IterArgs a)
@@ -734,7 +774,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     __shared__ float s_qs[kStage ? kWarps * kStageFloats * 32 : 1];
 
     grid_dependency_prologue();
-    load_state(a.in, s_state);
+    load_state(a.in, a.cs, s_state);
     __syncthreads();
     const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
     TileJob job;
@@ -745,16 +785,20 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     job.K = a.K;
     job.H = a.H;
     job.nb = gridDim.x;
-    job.seed_lo = a.seed_lo;
-    job.seed_hi = a.seed_hi;
-    job.iter = a.iter;
-    job.dt = a.dt;
-    job.inv_lambda = a.inv_lambda;
+    if (DYN) {
+        job.dyn = &st.cs;
+    } else {
+        job.seed_lo = a.cs.seed_lo;
+        job.seed_hi = a.cs.seed_hi;
+        job.iter = a.cs.iter;
+        job.dt = a.cs.dt;
+        job.inv_lambda = a.cs.inv_lambda;
+    }
     job.noise_dtype = a.noise_dtype;
     BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
                  (SELF && rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr, s_qs};
     unsigned ngath = 0;
-    run_block<GT, TRACE, SELF, kStage>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
+    run_block<GT, TRACE, SELF, kStage, DYN>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
     if (!TRACE && a.gathers) {
         const int lane = threadIdx.x & 31;
         unsigned n = ngath;

@@ -254,3 +254,4 @@ def test_iteration_sweeping_the_small_angle_branches(scene):
     sigma = np.full(7, 0.05, np.float32)
     iterate_and_compare(sc, Tg, sigma, 256, 32, 62,
                         lambda ths: (ths < 1e-4).any() and ((ths > 1e-4) & (ths < 1e-2)).mean() > 0.3)
+
