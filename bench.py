@@ -485,7 +485,7 @@ def bench_latency_cfg1(pm, torch, dev, stream, reps=200):
 
 
 def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, deadline_ms=10.0,
-                  seed=7, spin_us=5000, max_inflight=2):
+                  seed=7, spin_us=5000, max_inflight=2, admit_window_us=0):
     """Serving workload: Poisson replan requests from 256 arms (own field of
     96^3-128^3 at 1 cm each; per request K in {512, 1024, 2048, 4096}, H in
     {16, 32, 48, 64}, 8 iterations, warm start from the arm's resident
@@ -531,7 +531,8 @@ def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, 
                 "plans_s": ok / span_s if span_s > 0 else 0.0,
                 "completed": ok, "missed_deadline": n - ok}
 
-    srv = pm.Server(dev_i, max_batch=64, max_inflight=max_inflight, spin_us=spin_us)
+    srv = pm.Server(dev_i, max_batch=64, max_inflight=max_inflight, spin_us=spin_us,
+                    admit_window_us=admit_window_us)
     arm_ids = [srv.add_arm(p) for p in planners]
     stream = torch.cuda.Stream(device=dev)
     U_plain = [torch.zeros((256, 7), dtype=torch.float32, device=dev) for _ in range(n_arms)]

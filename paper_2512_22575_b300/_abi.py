@@ -47,7 +47,7 @@ class PmBatchItem(C.Structure):
 
 class PmServerConfig(C.Structure):
     _fields_ = [("max_batch", C.c_int), ("max_inflight", C.c_int), ("hbm_headroom", C.c_size_t),
-                ("batch_flags", C.c_int), ("spin_us", C.c_uint32)]
+                ("batch_flags", C.c_int), ("spin_us", C.c_uint32), ("admit_window_us", C.c_uint32)]
 
 
 class PmRequest(C.Structure):

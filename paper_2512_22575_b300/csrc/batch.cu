@@ -98,11 +98,13 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
 }
 
 // The same work list when every item has a one-step shape ((1,16,1),
-// (1,32,1) or (1,32,2): H <= 64, the default shapes up to there): the item's
-// shape selects one of three compile-time instantiations of the block loop,
-// so, as in the single-instance kernel, the shape folds away and each step's
-// state is staged in shared memory, and the kernel is fitted to MINB blocks
-// per SM (the run-time-shape kernel above holds 4).
+// (1,32,1) or (1,32,2): H <= 64, the default shapes up to there): with one
+// step per lane fixed at compile time, each step's state is staged in
+// shared memory as in the single-instance kernel, the kernel is fitted to
+// MINB blocks per SM (the run-time-shape kernel above holds 4), and L and P
+// stay run-time values, so the block loop exists once (three compile-time
+// copies of it, one per shape, missed the instruction cache: 3.8 stalls per
+// issue on an empty instruction buffer).
 constexpr int kBatchC1Steps = 64;   // C * L * P of the widest one-step shape
 
 template <typename GT, bool SELF, int MINB>
@@ -148,12 +150,7 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
         BlockSmem sm{s_dyn, s_dyn + kWarps * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
                      (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kNJ * 32 : nullptr, s_qs};
         unsigned ngath = 0;
-        if (s_inst.L == 16)
-            run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 16, 1, w.y, sm, ngath);
-        else if (s_inst.P == 1)
-            run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 32, 1, w.y, sm, ngath);
-        else
-            run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 32, 2, w.y, sm, ngath);
+        run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, s_inst.L, s_inst.P, w.y, sm, ngath);
     }
 }
 
@@ -640,7 +637,7 @@ pm_status pm_batch_run(pm_batch *b, const pm_batch_item *items, int n, int n_ite
         Plan best = make_plan(b, items, n, 1.0, false);
         if (flags & PM_BATCH_AUTOTUNE) {
             double best_us = 1e30;
-            for (double scale : {0.5, 1.0, 2.0, 4.0})
+            for (double scale : {1.0, 2.0, 4.0, 8.0, 16.0})
                 for (bool wide : {false, true}) {
                     Plan cand = make_plan(b, items, n, scale, wide);
                     double us = 0.0;

@@ -918,10 +918,13 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
             r.sph_ls[i].x = static_cast<float>(lam);
         }
         r.link_line[j] = line ? 1 : 0;
+        double w2 = 0.0;
         for (int k = 0; k < 3; ++k) {
             r.link_w[j][k] = static_cast<float>(w[k]);
             r.link_wg[j][k] = static_cast<float>(w[k] / static_cast<double>(gd->res));
+            w2 += static_cast<double>(r.link_w[j][k]) * r.link_w[j][k];
         }
+        r.link_w2[j] = static_cast<float>(w2);
     }
     for (int j = 0; j < n; ++j) {
         r.ca[j] = static_cast<float>(std::cos(static_cast<double>(rb->alpha[j])));
@@ -1008,9 +1011,27 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
                 dense = ps[p0 + i].a == a_lo + i / nb && ps[p0 + i].b == b_lo + i % nb;
             r.grp_dense[k] = dense ? 1 : 0;
         }
+        // bounding centres on their frame's line: link_c = link_lc link_w
+        bool lc_line[kNJ];
+        for (int j = 0; j < n; ++j) {
+            double ww = 0.0, lam = 0.0, d2 = 0.0;
+            for (int k = 0; k < 3; ++k) ww += static_cast<double>(r.link_w[j][k]) * r.link_w[j][k];
+            if (ww > 0.0) {
+                for (int k = 0; k < 3; ++k) lam += lc[j][k] * r.link_w[j][k];
+                lam /= ww;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double dk = lc[j][k] - lam * r.link_w[j][k];
+                d2 += dk * dk;
+            }
+            r.link_lc[j] = static_cast<float>(lam);
+            lc_line[j] = ww > 0.0 && d2 <= 1e-14 * ww + 1e-24;
+        }
         bool frames = true;
-        for (int k = 0; k <= g; ++k)
-            frames = frames && r.grp_dense[k] && r.link_line[r.grp_fa[k]] && r.link_line[r.grp_fb[k]];
+        for (int k = 0; k <= g; ++k) {
+            const int fa = r.grp_fa[k], fb = r.grp_fb[k];
+            frames = frames && r.grp_dense[k] && r.link_line[fa] && r.link_line[fb] && lc_line[fa] && lc_line[fb];
+        }
         r.self_frames = frames ? 1 : 0;
     }
     for (int i = 0; i < 6; ++i) { r.Q[i] = cp->Q[i]; r.QH[i] = cp->QH[i]; }

@@ -72,6 +72,8 @@ struct RobotConst {
     unsigned char self_frames;    // 1: the self slots use the frame layout (see self_slots)
     float grp_thr2[kMaxSelfGroups];
     float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
+    float link_w2[kNJ];           // |link_w|^2 (the rotated direction's squared length)
+    float link_lc[kNJ];           // frame layout: the bounding centre link_c = link_lc link_w
     // device [n], grouped and ordered by (a, b) within a group: x = bits of
     // the internal sphere indices a | b << 8, y = r_a + r_b, z = a squared
     // distance above which the pair is apart (its violation is exactly 0)
@@ -81,10 +83,10 @@ struct RobotConst {
 // Per-lane shared-memory slots of the self-collision term.  Sphere layout:
 // the world centres of the step's spheres, then of the frames' bounding
 // spheres.  Frame layout (self_frames, every group dense and every frame
-// in a group on a line): per frame j, its origin t, its rotated direction
-// v = R w and its bounding-sphere centre, 9 floats, from which the pair
-// test forms each centre as t + lambda_s v, as the lookups do.
-constexpr int kSelfFrameSlots = 9;
+// in a group on a line, its bounding-sphere centre too): per frame j, its
+// origin t and its rotated direction v = R w, 6 floats; every sphere and
+// bounding centre of the frame is t + lambda v.
+constexpr int kSelfFrameSlots = 6;
 __host__ __device__ constexpr int self_slots(int n_spheres, bool frames)
 {
     return frames ? kSelfFrameSlots * kNJ : 3 * n_spheres + 3 * kNJ;

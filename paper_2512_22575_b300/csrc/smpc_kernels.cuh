@@ -199,40 +199,53 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
     float acc = 0.f;
     if (rc.self_frames) {
         // frame layout: every group dense, every centre t + lambda_s v of its
-        // frame, formed as the lookups form it (the same pairs and order as
-        // the dense blocks below)
+        // frame (the same pairs and order as the dense blocks below)
         for (int gi = 0; gi < rc.n_self_groups; ++gi) {
             const int fa = rc.grp_fa[gi], fb = rc.grp_fb[gi];
             const float *pa = sp + kSelfFrameSlots * fa * 32, *pb = sp + kSelfFrameSlots * fb * 32;
-            const float gx = pa[6 * 32] - pb[6 * 32];
-            const float gy = pa[7 * 32] - pb[7 * 32];
-            const float gz = pa[8 * 32] - pb[8 * 32];
-            if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > rc.grp_thr2[gi]) continue;   // exact zero
-            const int a_lo = rc.link_begin[fa + 1], a_hi = rc.link_begin[fa + 2];
-            const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
             const f3 tb = mk(pb[0], pb[32], pb[64]), vb = mk(pb[96], pb[128], pb[160]);
             const f3 ta = mk(pa[0], pa[32], pa[64]), va = mk(pa[96], pa[128], pa[160]);
-            float bx[kSelfDense], by[kSelfDense], bz[kSelfDense], br[kSelfDense];
+            // c_a - c_b = dl + l_a va - l_b vb with dl = ta - tb, so
+            // |c_a - c_b|^2 = P_a + Q_b + m_a l_b with, per group, the dot
+            // products of dl, va, vb (|va|^2 = |w_a|^2: a rotation keeps lengths):
+            //   P_a = |dl|^2 + l_a (l_a |w_a|^2 + 2 dl.va),  m_a = -2 l_a va.vb,
+            //   Q_b = l_b (l_b |w_b|^2 - 2 dl.vb),
+            // two operations per pair instead of six.  The skip test is still
+            // exact: the rounding of this sum stays below 1e-7 m^2 for arm-sized
+            // frames, far inside the pair threshold's 1e-5 m margin (about
+            // 2e-6 m^2 at these radii).
+            const f3 dl = sub(ta, tb);
+            const float D = dot(dl, dl), Da2 = 2.0f * dot(dl, va), Db2 = 2.0f * dot(dl, vb);
+            const float Vab2 = -2.0f * dot(va, vb);
+            const float wa2 = rc.link_w2[fa], wb2 = rc.link_w2[fb];
+            // the frames' bounding spheres, centred at lambda-bar on each line,
+            // in the same form: apart beyond their radii + 0.1 mm, every pair of
+            // the group is apart (exact zero)
+            {
+                const float la = rc.link_lc[fa], lb0 = rc.link_lc[fb];
+                const float g2 = fmaf(la * Vab2, lb0, fmaf(la, fmaf(la, wa2, Da2), D) + lb0 * fmaf(lb0, wb2, -Db2));
+                if (g2 > rc.grp_thr2[gi]) continue;
+            }
+            const int a_lo = rc.link_begin[fa + 1], a_hi = rc.link_begin[fa + 2];
+            const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
+            float lb[kSelfDense], Qb[kSelfDense], br[kSelfDense];
 #pragma unroll
             for (int i = 0; i < kSelfDense; ++i) {
                 const int sb = b_lo + min(i, nb - 1);
-                const f3 c = axpy(rc.sph_ls[sb].x, vb, tb);
-                bx[i] = c.x;
-                by[i] = c.y;
-                bz[i] = c.z;
+                lb[i] = rc.sph_ls[sb].x;
+                Qb[i] = lb[i] * fmaf(lb[i], wb2, -Db2);
                 br[i] = rc.sph_r[sb];
             }
             for (int a = a_lo; a < a_hi; ++a) {
-                const f3 ca = axpy(rc.sph_ls[a].x, va, ta);
-                const float ra = rc.sph_r[a];
+                const float la = rc.sph_ls[a].x, ra = rc.sph_r[a];
+                const float Pa = fmaf(la, fmaf(la, wa2, Da2), D), ma = la * Vab2;
 #pragma unroll
                 for (int i = 0; i < kSelfDense; ++i) {
-                    const float ex = ca.x - bx[i], ey = ca.y - by[i], ez = ca.z - bz[i];
-                    const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const float d2 = fmaf(ma, lb[i], Pa + Qb[i]);
                     const float rs = ra + br[i];
                     const float t = __fadd_ru(rs, 1e-5f);
                     if (i < nb && d2 <= __fmul_ru(t, t)) {
-                        const float del = fmaxf(rs - sqrtf(d2), 0.f);
+                        const float del = fmaxf(rs - sqrtf(fmaxf(d2, 0.f)), 0.f);
                         acc = fmaf(del, del, acc);
                     }
                 }
@@ -347,10 +360,10 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
             for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
         }
         if (!terminal) env += link_env<GT, SELF>(rc, g, F, j, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
-        if (SELF && sp && pm_ok((rc.self_frames ? kSelfFrameSlots * j + 8 : 3 * rc.n_spheres + 3 * j + 2) <
-                                    self_slots(rc.n_spheres, rc.self_frames), kErrSelf, g)) {
+        if (SELF && sp && !rc.self_frames &&
+            pm_ok(3 * rc.n_spheres + 3 * j + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
-            const int t = rc.self_frames ? kSelfFrameSlots * j + 6 : 3 * rc.n_spheres + 3 * j;
+            const int t = 3 * rc.n_spheres + 3 * j;
             sp[t * 32] = c.x;
             sp[(t + 1) * 32] = c.y;
             sp[(t + 2) * 32] = c.z;

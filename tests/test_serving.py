@@ -180,3 +180,20 @@ def test_abandoned_tickets_are_cleaned_up(arms):
     t = srv.submit(aid, a.q, a.qd, a.T, 512, 16, 2, seed=99)
     assert srv.wait(t)["status"] == "PM_OK"
     srv.close()
+
+
+def test_admission_window_groups_close_arrivals(arms):
+    """With an admission window, requests submitted one by one within it
+    share a batch (instead of the first running alone), and each result is
+    still the replan alone."""
+    srv = pm.Server(admit_window_us=20000)
+    sel = arms[10:14]
+    ids = [srv.add_arm(a.planner) for a in sel]
+    reqs = [(1024, 32, 60 + i, 0, True) for i in range(len(sel))]
+    tickets = [srv.submit(aid, a.q, a.qd, a.T, K, H, N_ITERS, seed=seed, iter_index=it0)
+               for aid, a, (K, H, seed, it0, _) in zip(ids, sel, reqs)]
+    results = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert max(r["batch_size"] for r in results) >= 2
+    for a, r, req in zip(sel, results, reqs):
+        check(r, reference_replans(a, [req])[0])
