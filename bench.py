@@ -254,15 +254,16 @@ def bench_batched(pm, torch, dev, stream, reps=20):
     b = pm.Batch(dev.index or 0)
 
     def timed(fn):
+        # reps back-to-back rounds between two events on the stream: the
+        # host's preparation of a round (marshalling 64 items, descriptors)
+        # overlaps the GPU work of the previous one, as in a serving loop
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ts = []
+        e0.record(stream)
         for _ in range(reps):
-            e0.record(stream)
             fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
 
     with torch.cuda.stream(stream):
         for _ in range(3):
@@ -284,6 +285,7 @@ def bench_batched(pm, torch, dev, stream, reps=20):
         p.close()
     return {"workload": "64 uneven instances (K 256-4096, H 16-64, fields 64^3-128^3), one replan "
                         "(8 iterations) each",
+            "timing": f"{reps} back-to-back rounds between CUDA events on the stream, per round",
             "value": units / (t_batch / 1e3), "unit": UNIT, "ms_per_batch_replan": t_batch,
             "sequential_ms": t_seq, "sequential_value": units / (t_seq / 1e3),
             "speedup_vs_sequential": t_seq / t_batch,
@@ -485,7 +487,7 @@ def bench_latency_cfg1(pm, torch, dev, stream, reps=200):
 
 
 def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, deadline_ms=10.0,
-                  seed=7, spin_us=5000, max_inflight=2, admit_window_us=0):
+                  seed=7, spin_us=5000, max_inflight=2, admit_window_us=100):
     """Serving workload: Poisson replan requests from 256 arms (own field of
     96^3-128^3 at 1 cm each; per request K in {512, 1024, 2048, 4096}, H in
     {16, 32, 48, 64}, 8 iterations, warm start from the arm's resident
@@ -612,6 +614,8 @@ def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, 
                         "{512,1024,2048,4096}, H in {16,32,48,64}, 8 iterations, warm start, "
                         f"{deadline_ms:g} ms admission deadline, {duration_s:g} s per rate",
             "latency": "scheduled arrival to result on the host", "rates": results,
+            "server": {"max_batch": 64, "max_inflight": max_inflight, "admit_window_us": admit_window_us,
+                       "spin_us": spin_us},
             "server_stats": stats}
 
 
@@ -814,7 +818,9 @@ def run_ours(args, rank, world, local):
     # reduced-precision variants (field and noise in FP16 / BF16) on the same
     # workload: device time of the replan and of the iteration kernel
     variants = {}
-    for dt_name in ("f16", "bf16"):
+    legs = set(args.legs.split(",")) if args.legs else None
+    want = (lambda name: legs is None or name in legs)
+    for dt_name in (("f16", "bf16") if want("precision") else ()):
         pv = pm.Planner(w["robot"], sc["grid"], w["cp"], device=local, dtype=dt_name)
         pv.set_distance_field(w["phi"])
         pv.set_noise_dtype(dt_name)
@@ -849,15 +855,20 @@ def run_ours(args, rank, world, local):
         variants[dt_name] = {"value": K * H * iters * n_v / (vms / 1e3), "unit": UNIT,
                              "ms_per_step": vms / n_v, "kernel_ms_per_launch": kms / max(kn, 1),
                              "replans": n_v}
-    line["precision_variants"] = variants
-    line["latency_cfg1"] = bench_latency_cfg1(pm, torch, dev, stream)
-    line["self_collision"] = bench_self_collision(pm, torch, dev, stream, w, Ts)
-    line["self_collision_gap3"] = bench_self_collision(pm, torch, dev, stream, w, Ts, min_link_gap=3)
-    line["episodes"] = bench_episodes(pm, torch, dev, stream)
-    line["mapping"] = bench_mapping(pm, torch, dev, stream, w)
-    if not args.no_batched:
+    if variants:
+        line["precision_variants"] = variants
+    if want("latency"):
+        line["latency_cfg1"] = bench_latency_cfg1(pm, torch, dev, stream)
+    if want("self"):
+        line["self_collision"] = bench_self_collision(pm, torch, dev, stream, w, Ts)
+        line["self_collision_gap3"] = bench_self_collision(pm, torch, dev, stream, w, Ts, min_link_gap=3)
+    if want("episodes"):
+        line["episodes"] = bench_episodes(pm, torch, dev, stream)
+    if want("mapping"):
+        line["mapping"] = bench_mapping(pm, torch, dev, stream, w)
+    if not args.no_batched and want("batched"):
         line["batched"] = bench_batched(pm, torch, dev, stream)
-    if not args.no_serving:
+    if not args.no_serving and want("serving"):
         line["serving"] = bench_serving(pm, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -882,6 +893,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--flush-mb", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--legs", default="",
+                    help="comma list of the extra legs to run (precision, latency, self, episodes, mapping, "
+                         "batched, serving); empty = all")
     ap.add_argument("--warm-s", type=float, default=0.5,
                     help="seconds of untimed calls (scratch state) before each timed region")
     ap.add_argument("--cpu-budget", type=float, default=12.0)

@@ -360,10 +360,12 @@ typedef struct {
     uint32_t spin_us;       /* the scheduler busy-polls (one host core) for
                                this long after its last activity before it
                                sleeps; 0 = always sleep (default 5000)     */
-    uint32_t admit_window_us; /* a free slot launches once the oldest waiting
-                               request is this old, or max_batch are waiting,
-                               so that requests arriving close together
-                               share a batch; 0 = launch at once (default) */
+    uint32_t admit_window_us; /* while a batch is on the GPU, a free slot
+                               launches only once the oldest waiting request
+                               is this old or max_batch are waiting, so that
+                               requests arriving during a batch share the
+                               next one (an idle GPU launches at once);
+                               0 = launch at once; default 100             */
 } pm_server_config;
 
 typedef struct {

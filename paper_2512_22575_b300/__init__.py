@@ -444,7 +444,7 @@ class Server:
     q_next, qd_next, best_cost, latency_us, queue_us and batch_size."""
 
     def __init__(self, device=0, max_batch=64, max_inflight=2, hbm_headroom=256 << 20,
-                 batch_flags=0, spin_us=5000, admit_window_us=0):
+                 batch_flags=0, spin_us=5000, admit_window_us=100):
         cfg = PmServerConfig(int(max_batch), int(max_inflight), int(hbm_headroom), int(batch_flags),
                              int(spin_us), int(admit_window_us))
         out = C.c_void_p()

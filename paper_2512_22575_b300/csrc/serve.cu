@@ -328,10 +328,13 @@ void scheduler(pm_server *s)
             std::lock_guard<std::mutex> lk(s->mu);
             if (s->stop) break;
             retire(s);
-            // with an admission window, a free slot waits until the oldest
-            // waiting request is that old or a full batch is waiting
+            // with an admission window, a free slot waits, while another
+            // batch is on the GPU, until the oldest waiting request is that
+            // old or a full batch is waiting (an idle GPU launches at once)
+            bool other_busy = false;
+            for (auto &slp : s->slots) other_busy |= slp->busy;
             const bool ripe = !s->pending.empty() &&
-                              (s->cfg.admit_window_us == 0 ||
+                              (s->cfg.admit_window_us == 0 || !other_busy ||
                                static_cast<int>(s->pending.size()) >= s->cfg.max_batch ||
                                now_us() - s->pending.front().t_submit >= s->cfg.admit_window_us);
             for (auto &slp : s->slots) {
@@ -400,7 +403,7 @@ pm_status pm_server_create(int device, const pm_server_config *cfg, pm_server **
     c.hbm_headroom = static_cast<size_t>(256) << 20;
     c.batch_flags = 0;   // batch mixes rarely repeat, so graphs seldom pay off
     c.spin_us = 5000;
-    c.admit_window_us = 0;
+    c.admit_window_us = 100;
     if (cfg) c = *cfg;
     if (c.max_batch < 1 || c.max_batch > 4096 || c.max_inflight < 1 || c.max_inflight > 8) return PM_EINVAL;
     pm_server *s = new pm_server();

@@ -183,12 +183,15 @@ def test_abandoned_tickets_are_cleaned_up(arms):
 
 
 def test_admission_window_groups_close_arrivals(arms):
-    """With an admission window, requests submitted one by one within it
-    share a batch (instead of the first running alone), and each result is
-    still the replan alone."""
+    """With an admission window, requests submitted one by one while a batch
+    is on the GPU share the next batch (instead of each running alone), and
+    each result is still the replan alone."""
     srv = pm.Server(admit_window_us=20000)
     sel = arms[10:14]
     ids = [srv.add_arm(a.planner) for a in sel]
+    busy = srv.add_arm(arms[15].planner)
+    a15 = arms[15]
+    srv.submit(busy, a15.q, a15.qd, a15.T, 4096, 256, 64)    # about 10 ms on the GPU meanwhile
     reqs = [(1024, 32, 60 + i, 0, True) for i in range(len(sel))]
     tickets = [srv.submit(aid, a.q, a.qd, a.T, K, H, N_ITERS, seed=seed, iter_index=it0)
                for aid, a, (K, H, seed, it0, _) in zip(ids, sel, reqs)]
