@@ -49,6 +49,10 @@ constexpr size_t iteration_smem_bytes(int C)
     return 2u * kWarps * C * kNJ * 32 * sizeof(float);
 }
 
+// the block accumulator of a self-collision kernel lives in the slots (see
+// smpc_iteration_kernel): the slots of any sphere count hold the longest one
+static_assert(kWarps * 32 * 3 * kNJ >= kMaxHorizon * kNJ, "self slots hold the block accumulator");
+
 // Extra dynamic shared memory of the self-collision term (0 when off).
 inline size_t self_smem_bytes(const RobotConst &rc)
 {
@@ -490,7 +494,6 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     auto E = [&](int w, int s, int j) {
         return static_cast<int>(pm_idx(((w * C + s) * kNJ + j) * 32, kWarps * C * kNJ * 32 - 31, kErrTile, g));
     };
-    for (int i = tid; i < C * L * P * kNJ; i += kBlock) sm.blk[i] = 0.f;   // s_blk holds C L P 7 floats
     for (int s = 0; s < C; ++s)
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) sm.acc[E(warp, s, j) + lane] = 0.f;
@@ -725,6 +728,10 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     // block partial, warps merged in warp order
     if (lane == 0) { sm.wm[warp] = run_m; sm.wz[warp] = run_z; }
     __syncthreads();
+    // the block accumulator (C L P 7 floats) is cleared only now: with the
+    // self term it shares its memory with the tiles' self-collision slots
+    for (int i = tid; i < C * L * P * kNJ; i += kBlock) sm.blk[i] = 0.f;
+    __syncthreads();
     float Mb = CUDART_INF_F;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) Mb = fminf(Mb, sm.wm[w]);
@@ -780,7 +787,9 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
     __shared__ float s_S[kWarps / 2 + 1][2][2];
     __shared__ float s_state[kStateFloats];
-    __shared__ float s_blk[C * L * P * kNJ];   // block accumulator [k][j], k < C*L*P (>= H, host-checked)
+    // block accumulator [k][j], k < C*L*P (>= H, host-checked); with the
+    // self term it takes the start of the self-collision slots instead
+    __shared__ float s_blk[SELF ? 1 : C * L * P * kNJ];
     __shared__ float s_wm[kWarps], s_wz[kWarps];
     // one-step shapes stage their steps' states (run_block, STAGE)
     constexpr bool kStage = (C == 1);
@@ -808,8 +817,9 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
         job.inv_lambda = a.cs.inv_lambda;
     }
     job.noise_dtype = a.noise_dtype;
-    BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
-                 (SELF && rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * C * kNJ * 32 : nullptr, s_qs};
+    float *self_slots_base = s_dyn + 2 * kWarps * C * kNJ * 32;
+    BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, SELF ? self_slots_base : s_blk, s_wm, s_wz,
+                 (SELF && rc.n_self_groups > 0) ? self_slots_base : nullptr, s_qs};
     unsigned ngath = 0;
     run_block<GT, TRACE, SELF, kStage, DYN>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
     if (!TRACE && a.gathers) {
