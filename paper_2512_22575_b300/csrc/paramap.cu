@@ -811,7 +811,7 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
     *out = nullptr;
     if (!rb || !gd || !cp) return set_err(nullptr, PM_EINVAL, "NULL robot, grid or costs");
     if (rb->n_joints != kNJ)
-        return set_err(nullptr, PM_EINVAL, "n_joints=%d: this build compiles a %d-joint chain", rb->n_joints, kNJ);
+        return set_err(nullptr, PM_EINVAL, "n_joints=%d: the library is compiled for a %d-joint chain", rb->n_joints, kNJ);
     const int n = rb->n_joints;
     if (!rb->a || !rb->d || !rb->alpha || !rb->theta_offset || !rb->q_min || !rb->q_max ||
         !rb->qd_max || !rb->qdd_max)

@@ -1,7 +1,7 @@
 """The bounds-checked build (libparamap_checked.so, PM_BOUNDS_CHECK).
 
 compute-sanitizer is not available here, so memory safety is checked by the
-library itself: in this build every distance-field gather, shared-memory
+library itself: in the checked library every distance-field gather, shared-memory
 slot and cost / partial / trace write of the iteration kernels is checked
 against its extent, and a violation sets a bit in the context's word and
 skips the access (no trap).  A child process loads that build (the
