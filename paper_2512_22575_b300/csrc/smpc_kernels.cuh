@@ -218,18 +218,17 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
             // exact: the rounding of this sum stays below 1e-7 m^2 for arm-sized
             // frames, far inside the pair threshold's 1e-5 m margin (about
             // 2e-6 m^2 at these radii).
+            // the frames' bounding spheres, centred at lambda-bar on each line:
+            // apart beyond their radii + 0.1 mm, every pair of the group is
+            // apart (exact zero); tested before the group's dot products
+            {
+                const f3 g = sub(axpy(rc.link_lc[fa], va, ta), axpy(rc.link_lc[fb], vb, tb));
+                if (dot(g, g) > rc.grp_thr2[gi]) continue;
+            }
             const f3 dl = sub(ta, tb);
             const float D = dot(dl, dl), Da2 = 2.0f * dot(dl, va), Db2 = 2.0f * dot(dl, vb);
             const float Vab2 = -2.0f * dot(va, vb);
             const float wa2 = rc.link_w2[fa], wb2 = rc.link_w2[fb];
-            // the frames' bounding spheres, centred at lambda-bar on each line,
-            // in the same form: apart beyond their radii + 0.1 mm, every pair of
-            // the group is apart (exact zero)
-            {
-                const float la = rc.link_lc[fa], lb0 = rc.link_lc[fb];
-                const float g2 = fmaf(la * Vab2, lb0, fmaf(la, fmaf(la, wa2, Da2), D) + lb0 * fmaf(lb0, wb2, -Db2));
-                if (g2 > rc.grp_thr2[gi]) continue;
-            }
             const int a_lo = rc.link_begin[fa + 1], a_hi = rc.link_begin[fa + 2];
             const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
             float lb[kSelfDense], Qb[kSelfDense], br[kSelfDense];
