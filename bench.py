@@ -40,6 +40,7 @@ EPISODE = 200
 # its trilinear interpolation and cost, 26.  The terminal step (no spheres or
 # state limits) is 729.
 FLOPS_STEP = 856 + 28 * 37
+FLOPS_STEP_ESTIMATE = 2300   # planning estimate: full trilinear evaluation of all 28 spheres
 FLOPS_GATHER = 26
 FLOPS_TERMINAL = 729
 FP32_LANES_PER_SM = 128
@@ -792,6 +793,9 @@ def run_ours(args, rank, world, local):
                 # FMUL, ncu), against the fixed algorithmic count `achieved` uses
                 "executed_fp32_flops_per_step_ncu": (kernel_counters() or {}).get("fp32_flop_equiv_per_step"),
                 "algorithmic_flops_per_step": flops_launch / (K * H),
+                # the same rate with the planning estimate of 2300 FP32 flops per
+                # roll-out step (every sphere interpolated, no skip)
+                "frac_at_2300_flops_per_step": K * H * FLOPS_STEP_ESTIMATE / avg_kernel_s / 1e12 / peak,
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes "
                               f"x 2 x {SM_MAX_MHZ_NOMINAL:.0f} MHz (unit counts and max clock)"}
 
