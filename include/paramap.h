@@ -160,6 +160,11 @@ pm_status pm_set_distance_field(pm_ctx *ctx, const float *grid, int grid_is_devi
  *                     mapped by Box-Muller (b = 0: joints 0-3, b = 1: 4-6)
  *   costs_out [K]     S^(m) of Eq. 28, or NULL (host or device)
  *   cuda_stream       cudaStream_t to run on, or NULL for the context's own
+ * When U or costs_out is host memory the call returns once they are
+ * written; otherwise it only enqueues (host inputs are staged first).
+ * Calls on one context
+ * share its scratch (partials, staging): calls on different streams must
+ * not overlap on the GPU.
  * Errors: PM_EINVAL (range, NaN in q0/qd0/T_goal/sigma, no field set; U is
  * left untouched), PM_ENOMEM, PM_ECUDA.
  */
@@ -246,7 +251,9 @@ pm_status pm_bounds_status(pm_ctx *ctx, unsigned *word, int reset);
  * profiling and gather counting are off; other calls launch directly.  The
  * first call of a shape pays the capture (about a millisecond).  enable = 0
  * drops the captured graphs and launches every call directly.  No
- * counterpart in the paper.  Errors: PM_EINVAL.
+ * counterpart in the paper.  If a capture fails (a driver without graph
+ * support for these launches), the context turns the replay off and the
+ * call, like every later one, launches directly.  Errors: PM_EINVAL.
  */
 pm_status pm_set_call_graphs(pm_ctx *ctx, int enable);
 

@@ -1165,10 +1165,15 @@ pm_status pm_smpc_iterate(pm_ctx *c, const float *q0, const float *qd0, const fl
     if (!dU && !finite_all(U, H * kNJ)) return set_err(c, PM_EINVAL, "U has a non-finite entry");
     const bool dC = costs_out && is_device_ptr(costs_out);
     cudaStream_t s = pick_stream(c, cuda_stream);
-    if (graph_ok(c) && !dU && !dC && !is_device_ptr(q0) && !is_device_ptr(qd0) && !is_device_ptr(T_goal)) {
-        cudaGraphExec_t ex = nullptr;
-        st = graph_get(c, kGraphIterate, K, H, 1, costs_out != nullptr, ex);
-        if (st != PM_OK) return st;
+    cudaGraphExec_t ex = nullptr;
+    if (graph_ok(c) && !dU && !dC && !is_device_ptr(q0) && !is_device_ptr(qd0) && !is_device_ptr(T_goal) &&
+        graph_get(c, kGraphIterate, K, H, 1, costs_out != nullptr, ex) != PM_OK) {
+        c->graphs_on = false;      // capture not possible here: launch directly from now on
+        graphs_clear(c);
+        cudaGetLastError();
+        ex = nullptr;
+    }
+    if (ex) {
         graph_fill(c, q0, qd0, T_goal, sigma, dt, lambda, seed, iter_index, U, H);
         const size_t nU = static_cast<size_t>(H) * kNJ;
         PM_CUDA(c, cudaMemcpyAsync(c->d_gslot, c->h_gslot, (kGU + nU) * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -1220,10 +1225,15 @@ pm_status pm_replan(pm_ctx *c, float *q, float *qd, const float *T_goal, float *
     const bool dq = is_device_ptr(q), dqd = is_device_ptr(qd);
     const bool du0 = u0_out && is_device_ptr(u0_out), dbest = best_cost && is_device_ptr(best_cost);
     cudaStream_t s = pick_stream(c, cuda_stream);
-    if (graph_ok(c) && !dU && !dq && !dqd && !du0 && !dbest && !is_device_ptr(T_goal)) {
-        cudaGraphExec_t ex = nullptr;
-        st = graph_get(c, kGraphReplan, K, H, n_iters, false, ex);
-        if (st != PM_OK) return st;
+    cudaGraphExec_t ex = nullptr;
+    if (graph_ok(c) && !dU && !dq && !dqd && !du0 && !dbest && !is_device_ptr(T_goal) &&
+        graph_get(c, kGraphReplan, K, H, n_iters, false, ex) != PM_OK) {
+        c->graphs_on = false;      // capture not possible here: launch directly from now on
+        graphs_clear(c);
+        cudaGetLastError();
+        ex = nullptr;
+    }
+    if (ex) {
         graph_fill(c, q, qd, T_goal, sigma, dt, lambda, seed, replan_index * static_cast<uint32_t>(n_iters), U, H);
         const size_t nU = static_cast<size_t>(H) * kNJ;
         PM_CUDA(c, cudaMemcpyAsync(c->d_gslot, c->h_gslot, (kGU + nU) * sizeof(float), cudaMemcpyHostToDevice, s));
