@@ -597,6 +597,11 @@ def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, 
                 lat.append(t_end - arrive)
         return summary(lat, len(t_arr), t_end - t0)
 
+    # the request loops run with Python's garbage collector paused, so that a
+    # collection in the submitting thread does not delay submissions
+    import gc
+    gc.collect()
+    gc.disable()
     # warm up both paths (kernel loading, plan caches, pinned staging)
     w = arrivals(2000)
     served(*[x[:200] for x in w])
@@ -607,6 +612,7 @@ def bench_serving(pm, torch, dev, rates=SERVE_RATES, duration_s=0.5, n_iters=8, 
         a = arrivals(rate)
         results.append({"offered_per_s": rate, "requests": len(a[0]),
                         "served": served(*a), "plain": plain(*a)})
+    gc.enable()
     stats = srv.stats()
     srv.close()
     for p in planners:
@@ -764,9 +770,12 @@ def run_ours(args, rank, world, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_call_ms = np.diff(t_call) * 1e3
     e2e_value = whole_job_value(K * H * iters * n_e2e, world, e2e_s)
-    state_bytes = 36 * 4                    # q0, qd0, R_g, t_g, sigma as staged
-    h2d = state_bytes + H * 7 * 4           # + U
-    d2h = 25 * 4 + H * 7 * 4                # q, qd, u0, best + U
+    # the host-buffer replan runs from its graph: one copy in of the call's
+    # block (q0, qd0, T_goal, sigma, dt, lambda, seed, iteration: 96 floats
+    # with padding) and U, one copy out of the outputs (q, qd, u0, best: 32
+    # floats with padding) and U
+    h2d = (96 + H * 7) * 4
+    d2h = (32 + H * 7) * 4
 
     # roofline of the iteration kernel (algorithmic FP32 flops / event-timed duration)
     flops_launch = K * ((H - 1) * FLOPS_STEP + FLOPS_TERMINAL) + FLOPS_GATHER * gathers_per_launch

@@ -316,9 +316,11 @@ size_t batch_c1_smem() { return 2u * kWarps * kNJ * 32 * sizeof(float); }
 
 using BatchKernel = void (*)(BatchArgs);
 
+// with the self term the slots' shared memory allows 5 blocks per SM, so
+// that variant is fitted to 5 (96 registers instead of spilling at 80)
 BatchKernel c1_kernel(bool self)
 {
-    return self ? smpc_batch_kernel_c1<float, true, kBatchC1MinBlocks>
+    return self ? smpc_batch_kernel_c1<float, true, kBatchC1MinBlocks - 1>
                 : smpc_batch_kernel_c1<float, false, kBatchC1MinBlocks>;
 }
 
