@@ -515,6 +515,14 @@ pm_status pm_map_update(pm_ctx *ctx, const uint8_t *occ, int occ_is_device, cons
  *   T: device float[n][16], row-major homogeneous transforms; xi: device
  *   float[n][6].  Enqueued on cuda_stream.  Errors: PM_EINVAL (NULL or host
  *   pointers), PM_ECUDA.
+ * pm_joint_sincos: sc[i] = (sin x[i], cos x[i]) as the forward kinematics
+ *   evaluates the joint rotations (Eq. 6): a Cody-Waite reduction by pi/2
+ *   and polynomials on [-pi/4, pi/4] fitted for this library (within 2
+ *   float32 ulps for |x| <= 64, within 2^-23 absolute up to 1e4 and 2^-21
+ *   up to 2^22; NaN for non-finite x).  If
+ *   sc_ref is not NULL it receives CUDA's sincosf of the same arguments.
+ *   x: device float[n]; sc, sc_ref: device float[n][2].  Enqueued on
+ *   cuda_stream.  Errors: PM_EINVAL (NULL x/sc or host pointers), PM_ECUDA.
  */
 pm_status pm_philox4x32_10(const uint32_t *ctr, uint64_t key, uint32_t *out, size_t n,
                            void *cuda_stream);
@@ -531,6 +539,7 @@ pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed,
                           uint32_t iter_index, float *eps, void *cuda_stream);
 pm_status pm_pose_error(const float *T_goal, const float *T, float *xi, size_t n,
                         void *cuda_stream);
+pm_status pm_joint_sincos(const float *x, float *sc, float *sc_ref, size_t n, void *cuda_stream);
 pm_status pm_rollout_trace(pm_ctx *ctx, const float *q0, const float *qd0,
                            const float *T_goal, const float *U, int K, int H, float dt,
                            const float *sigma, uint64_t seed, uint32_t iter_index,

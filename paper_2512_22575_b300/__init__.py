@@ -25,7 +25,7 @@ __all__ = [
     "PM_F32", "PM_F16", "PM_BF16", "PmError", "lib_path", "version",
     "create", "set_distance_field", "smpc_iterate", "smpc_iterate_noalloc", "replan",
     "philox4x32_10",
-    "sample_noise", "rollout_trace", "pose_error", "profile_enable", "profile_read", "profile_gathers", "launch_plan", "set_call_graphs", "bounds_checked", "bounds_status",
+    "sample_noise", "rollout_trace", "pose_error", "joint_sincos", "profile_enable", "profile_read", "profile_gathers", "launch_plan", "set_call_graphs", "bounds_checked", "bounds_status",
     "set_tile_shape", "set_noise_dtype", "PM_PROFILE_TIME", "PM_PROFILE_GATHERS", "destroy",
     "last_error", "Planner", "Batch", "Server", "PM_BATCH_REPLAN", "PM_BATCH_GRAPH", "PM_BATCH_AUTOTUNE",
 ]
@@ -288,6 +288,15 @@ def pose_error(T_goal, T, xi, stream=None):
     n = T.numel() // 16
     _check(lib().pm_pose_error(_ptr(T_goal, n=16 * n), _ptr(T, n=16 * n), _ptr(xi, n=6 * n, writable=True),
                                C.c_size_t(n), _stream(stream)))
+
+
+def joint_sincos(x, sc, sc_ref=None, stream=None):
+    """pm_joint_sincos on CUDA float32 tensors: x [n] into sc [n][2] = (sin, cos)
+    as the forward kinematics computes them; sc_ref, if given, gets CUDA's sincosf."""
+    n = x.numel()
+    _check(lib().pm_joint_sincos(_ptr(x, n=n), _ptr(sc, n=2 * n, writable=True),
+                                 None if sc_ref is None else _ptr(sc_ref, n=2 * n, writable=True),
+                                 C.c_size_t(n), _stream(stream)))
 
 
 PM_PROFILE_TIME, PM_PROFILE_GATHERS = 1, 2

@@ -93,6 +93,7 @@ SIGNATURES = {
     "pm_philox4x32_10": (C.c_int, [_V, C.c_uint64, _V, C.c_size_t, _V]),
     "pm_sample_noise": (C.c_int, [C.c_int, C.c_int, _V, C.c_uint64, C.c_uint32, _V, _V]),
     "pm_pose_error": (C.c_int, [_V, _V, _V, C.c_size_t, _V]),
+    "pm_joint_sincos": (C.c_int, [_V, _V, _V, C.c_size_t, _V]),
     "pm_launch_plan": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "pm_set_call_graphs": (C.c_int, [_V, C.c_int]),
     "pm_bounds_checked": (C.c_int, []),

@@ -117,6 +117,8 @@ inline GridConst grid_const(const pm_ctx *c)
     g.mx = static_cast<float>(c->gd.nx - 1);
     g.my = static_cast<float>(c->gd.ny - 1);
     g.mz = static_cast<float>(c->gd.nz - 1);
+    g.inv_res_pk = make_float2(g.inv_res, g.inv_res);
+    g.bxy = make_float2(g.bx, g.by);
     g.err = c->d_err;
     return g;
 }

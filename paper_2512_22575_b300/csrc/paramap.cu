@@ -277,6 +277,26 @@ __global__ void pose_error_kernel(const float *Tg, const float *T, float *xi, si
     }
 }
 
+// joint_sincos with the coefficients as the kernels hold them (parameter
+// bank), beside CUDA's sincosf of the same argument for comparison
+struct SinCosPoly { float2 kc[4]; };
+
+__global__ void joint_sincos_kernel(const float *x, float *sc, float *sc_ref, size_t n, const __grid_constant__ SinCosPoly kp)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float s, c;
+        joint_sincos(x[i], s, c, kp.kc);
+        sc[2 * i] = s;
+        sc[2 * i + 1] = c;
+        if (sc_ref) {
+            sincosf(x[i], &s, &c);
+            sc_ref[2 * i] = s;
+            sc_ref[2 * i + 1] = c;
+        }
+    }
+}
+
 struct Sigma { float s[8]; };
 
 __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint32_t s_hi,
@@ -361,7 +381,7 @@ __global__ void episode_step_kernel(const RobotConst rc, const float *Tg, float 
     __syncthreads();
     if (threadIdx.x == 0) {
         Frame F = base_frame();
-        for (int j = 0; j < kNJ; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], s_q[j] + rc.th0[j]);
+        for (int j = 0; j < kNJ; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], s_q[j] + rc.th0[j], rc.sincos_pk);
         const f3 t = axpy(rc.flange_d, F.c3, F.t);
         const f3 e = sub(t, mk(Tg[3], Tg[7], Tg[11]));
         // R_d = R_g^T R: entries from the goal's columns and the frame's columns
@@ -943,6 +963,16 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         r.qdd_hi[j] = static_cast<float>(acc - mf * 2.0 * acc);
         r.q_ref[j] = cp->q_ref[j];
     }
+    for (int i = 0; i < 4; ++i) r.sincos_pk[i] = kSinCosPoly[i];
+    for (int p = 0; p < kNJ / 2; ++p) {
+        r.q_lo_pk[p] = make_float2(r.q_lo[2 * p], r.q_lo[2 * p + 1]);
+        r.q_hi_pk[p] = make_float2(r.q_hi[2 * p], r.q_hi[2 * p + 1]);
+        r.qd_lo_pk[p] = make_float2(r.qd_lo[2 * p], r.qd_lo[2 * p + 1]);
+        r.qd_hi_pk[p] = make_float2(r.qd_hi[2 * p], r.qd_hi[2 * p + 1]);
+        r.qdd_lo_pk[p] = make_float2(r.qdd_lo[2 * p], r.qdd_lo[2 * p + 1]);
+        r.qdd_hi_pk[p] = make_float2(r.qdd_hi[2 * p], r.qdd_hi[2 * p + 1]);
+        r.q_ref_pk[p] = make_float2(r.q_ref[2 * p], r.q_ref[2 * p + 1]);
+    }
     r.flange_d = rb->flange_d;
     // self-collision set: pairs in internal sphere order, grouped by their
     // frames (fa <= fb); each frame's bounding sphere around its spheres
@@ -1466,6 +1496,20 @@ pm_status pm_pose_error(const float *T_goal, const float *T, float *xi, size_t n
         return set_err(nullptr, PM_EINVAL, "T_goal/T/xi must be device memory");
     const unsigned blocks = static_cast<unsigned>(std::min<size_t>((n + 127) / 128, 65535));
     pose_error_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(cuda_stream)>>>(T_goal, T, xi, n);
+    PM_CUDA(nullptr, cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_joint_sincos(const float *x, float *sc, float *sc_ref, size_t n, void *cuda_stream)
+{
+    if (!x || !sc) return set_err(nullptr, PM_EINVAL, "NULL argument");
+    if (n == 0) return PM_OK;
+    if (!is_device_ptr(x) || !is_device_ptr(sc) || (sc_ref && !is_device_ptr(sc_ref)))
+        return set_err(nullptr, PM_EINVAL, "x/sc/sc_ref must be device memory");
+    SinCosPoly kp;
+    for (int i = 0; i < 4; ++i) kp.kc[i] = kSinCosPoly[i];
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>((n + 127) / 128, 65535));
+    joint_sincos_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, sc, sc_ref, n, kp);
     PM_CUDA(nullptr, cudaGetLastError());
     return PM_OK;
 }

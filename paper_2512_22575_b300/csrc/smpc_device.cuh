@@ -73,6 +73,11 @@ struct RobotConst {
     float grp_thr2[kMaxSelfGroups];
     float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
     float link_w2[kNJ];           // |link_w|^2 (the rotated direction's squared length)
+    // coefficient pairs (sin, cos) of joint_sincos's Horner steps, highest
+    // degree first (operands of packed FP32 FMAs, read from the parameter bank)
+    float2 sincos_pk[4];
+    // joints (2p, 2p+1), p < 3, of the boxes of Eq. 21 and of q_ref
+    float2 q_lo_pk[3], q_hi_pk[3], qd_lo_pk[3], qd_hi_pk[3], qdd_lo_pk[3], qdd_hi_pk[3], q_ref_pk[3];
     float link_lc[kNJ];           // frame layout: the bounding centre link_c = link_lc link_w
     // device [n], grouped and ordered by (a, b) within a group: x = bits of
     // the internal sphere indices a | b << 8, y = r_a + r_b, z = a squared
@@ -106,6 +111,7 @@ struct GridConst {
     float inv_res;
     float bx, by, bz;             // -origin / res - 1/2: grid coordinate g = p / res + b
     float mx, my, mz;             // n - 1 (clamp bound)
+    float2 inv_res_pk, bxy;       // (inv_res, inv_res) and (bx, by), for packed operations
     unsigned *err;                // bounds-checked builds: the context's violation word (else null)
 };
 
@@ -228,7 +234,8 @@ __device__ __forceinline__ void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32
 // significand, so u is exact in FP32 and strictly inside (0, 1).
 __device__ __forceinline__ float word_to_uniform(uint32_t x)
 {
-    return (static_cast<float>(x >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    // (i + 1/2) 2^-23 = i 2^-23 + 2^-24, exact either way
+    return fmaf(static_cast<float>(x >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
 }
 
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1)
@@ -260,14 +267,26 @@ __device__ __forceinline__ void step_normals(uint32_t seed_lo, uint32_t seed_hi,
 // ------------------------------------------------------------------ vectors
 struct f3 { float x, y, z; };
 
+// The x and y components go through the packed FP32 units (__fmul2_rn,
+// __ffma2_rn, __fadd2_rn: two IEEE operations in one instruction), z through
+// the scalar ones; the results are those of three scalar operations.
 __device__ __forceinline__ f3 mk(float x, float y, float z) { return f3{x, y, z}; }
-__device__ __forceinline__ f3 scale(float a, f3 x) { return f3{a * x.x, a * x.y, a * x.z}; }
+__device__ __forceinline__ f3 scale(float a, f3 x)
+{
+    const float2 xy = __fmul2_rn(make_float2(a, a), make_float2(x.x, x.y));
+    return f3{xy.x, xy.y, a * x.z};
+}
 // a*x + y
 __device__ __forceinline__ f3 axpy(float a, f3 x, f3 y)
 {
-    return f3{fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z)};
+    const float2 xy = __ffma2_rn(make_float2(a, a), make_float2(x.x, x.y), make_float2(y.x, y.y));
+    return f3{xy.x, xy.y, fmaf(a, x.z, y.z)};
 }
-__device__ __forceinline__ f3 sub(f3 a, f3 b) { return f3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 sub(f3 a, f3 b)
+{
+    const float2 xy = __fadd2_rn(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
+    return f3{xy.x, xy.y, a.z - b.z};
+}
 __device__ __forceinline__ float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 __device__ __forceinline__ f3 cross(f3 a, f3 b)
 {
@@ -282,15 +301,58 @@ __device__ __forceinline__ Frame base_frame()
     return Frame{mk(1.f, 0.f, 0.f), mk(0.f, 1.f, 0.f), mk(0.f, 0.f, 1.f), mk(0.f, 0.f, 0.f)};
 }
 
+// sin and cos of a joint angle x (Eq. 6).  Cody-Waite reduction by pi/2:
+// n = rint(x 2/pi), taken from the low bits of x 2/pi + 1.5 2^23 (valid for
+// |x| < 2^22 pi/2), r = x - n p1 - n p2 - n p3 with p1 + p2 + p3 = pi/2 in
+// three float32 parts; with FMA the first step is exact (x - n p1 is a
+// multiple of 2^-24 below 1 in magnitude).  Then sin r and cos r on [-1.01 pi/4, 1.01 pi/4]
+// by the odd and even polynomials of gen_sincos_poly.py (least-squares fits
+// on Chebyshev nodes, within 0.9 ulp in float32 evaluation), their Horner
+// steps paired in packed FP32 FMAs, and the quadrant n mod 4 applied by a
+// swap and two sign flips.  Within 2 ulps for |x| <= 64 and 2^-23 absolute
+// up to 1e4; NaN for non-finite x.
+__device__ __forceinline__ void joint_sincos(float x, float &s, float &c, const float2 (&kc)[4])
+{
+    constexpr float kTwoOverPi = 0.636619772367581343f;
+    constexpr float kRound = 12582912.0f;                  // 1.5 2^23
+    constexpr float kPio2Hi = 1.57079637050628662f;        // float32(pi/2)
+    constexpr float kPio2Mid = -4.371138828673793e-8f;    // float32(pi/2 - kPio2Hi)
+    constexpr float kPio2Lo = -1.7763568394002505e-15f;   // float32(pi/2 - kPio2Hi - kPio2Mid)
+    const float t = fmaf(x, kTwoOverPi, kRound);
+    const float n = t - kRound;
+    const unsigned qb = __float_as_uint(t);                // n mod 4 in the low bits
+    float r = fmaf(-n, kPio2Hi, x);
+    r = fmaf(-n, kPio2Mid, r);
+    r = fmaf(-n, kPio2Lo, r);
+    const float z = r * r;
+    const float2 zz = make_float2(z, z);
+    float2 p = __ffma2_rn(zz, kc[0], kc[1]);
+    p = __ffma2_rn(zz, p, kc[2]);
+    p = __ffma2_rn(zz, p, kc[3]);
+    const float sr = fmaf(r * z, p.x, r);
+    const float cr = fmaf(z, p.y, 1.0f);
+    const bool odd = (qb & 1u) != 0u;
+    const float sv = odd ? cr : sr, cv = odd ? sr : cr;
+    s = __uint_as_float(__float_as_uint(sv) ^ ((qb << 30) & 0x80000000u));          // n mod 4 in {2, 3}
+    c = __uint_as_float(__float_as_uint(cv) ^ (((qb + 1u) << 30) & 0x80000000u));   // n mod 4 in {1, 2}
+}
+
+// joint_sincos's coefficients (sin, cos), highest degree first (host copy,
+// loaded into RobotConst::sincos_pk)
+constexpr float2 kSinCosPoly[4] = {{2.724328624e-06f, 2.445699101e-05f}, {-1.984003320e-04f, -1.388753648e-03f},
+                                   {8.333331905e-03f, 4.166664928e-02f}, {-1.666666716e-01f, -5.0e-01f}};
+
 // T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d)  (modified DH, Eq. 6).
-__device__ __forceinline__ void dh_step(Frame &F, float ca, float sa, float a, float d,
-                                        float theta)
+// kc: joint_sincos's coefficients as the kernel holds them (RobotConst::
+// sincos_pk, in the parameter bank, so the packed FMAs read them in place).
+__device__ __forceinline__ void dh_step(Frame &F, float ca, float sa, float a, float d, float theta,
+                                        const float2 (&kc)[4])
 {
     F.t = axpy(a, F.c1, F.t);                       // TransX(a); RotX keeps the x axis
     const f3 x2 = axpy(sa, F.c3, scale(ca, F.c2));  // RotX(alpha): y' = ca y + sa z
     const f3 x3 = axpy(-sa, F.c2, scale(ca, F.c3)); //              z' = -sa y + ca z
     float s, c;
-    sincosf(theta, &s, &c);
+    joint_sincos(theta, s, c, kc);
     const f3 y1 = axpy(s, x2, scale(c, F.c1));      // RotZ(theta): x'' = c x + s y'
     const f3 y2 = axpy(-s, F.c1, scale(c, x2));     //              y'' = -s x + c y'
     F.c1 = y1;
@@ -471,6 +533,15 @@ __device__ __forceinline__ float quad_cost(const float xi[6], const float *Q)
 __device__ __forceinline__ float limit_violation(float x, float lo, float hi)
 {
     return fmaxf(x - hi, 0.0f) + fminf(x - lo, 0.0f);
+}
+
+// limit_violation of two joints at once
+__device__ __forceinline__ float2 limit_violation_pk(float2 x, float2 lo, float2 hi)
+{
+    const float2 dh = __fadd2_rn(x, make_float2(-hi.x, -hi.y));
+    const float2 dl = __fadd2_rn(x, make_float2(-lo.x, -lo.y));
+    return __fadd2_rn(make_float2(fmaxf(dh.x, 0.0f), fmaxf(dh.y, 0.0f)),
+                      make_float2(fminf(dl.x, 0.0f), fminf(dl.y, 0.0f)));
 }
 
 // ------------------------------------------------------ compensated sums

@@ -79,17 +79,37 @@ struct IterArgs {
 template <bool TRACE>
 __device__ __forceinline__ float control_cost(const RobotConst &rc, const float *u, float *tr)
 {
-    float lim = 0.f, sm = 0.f;
+    // joints in pairs through the packed FP32 units, the last one alone
+    float2 lim2 = make_float2(0.f, 0.f), sm2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < kNJ; ++j) {
-        const float dl = limit_violation(u[j], rc.qdd_lo[j], rc.qdd_hi[j]);
-        lim = fmaf(dl, dl, lim);
-        sm = fmaf(u[j], u[j], sm);
+    for (int p = 0; p < kNJ / 2; ++p) {
+        const float2 uu = make_float2(u[2 * p], u[2 * p + 1]);
+        const float2 dl = limit_violation_pk(uu, rc.qdd_lo_pk[p], rc.qdd_hi_pk[p]);
+        lim2 = __ffma2_rn(dl, dl, lim2);
+        sm2 = __ffma2_rn(uu, uu, sm2);
     }
+    const float d6 = limit_violation(u[kNJ - 1], rc.qdd_lo[kNJ - 1], rc.qdd_hi[kNJ - 1]);
+    float lim = fmaf(d6, d6, lim2.x + lim2.y);
+    float sm = fmaf(u[kNJ - 1], u[kNJ - 1], sm2.x + sm2.y);
     lim *= rc.w_qdd;
     sm *= rc.w_s;
     if (TRACE) { tr[5] = lim; tr[6] = sm; }
     return lim + sm;
+}
+
+// Whether a batch of spheres may hold one to gather: max_i (thr_i - mn_i) >= 0,
+// i.e. some skip bound mn_i is not above its threshold (for finite values
+// thr - mn >= 0 exactly when mn <= thr).  The batch's entries past its
+// frame's last sphere (the next frame's spheres, or the zero padding) take
+// part too: they can only cause a needless pass, whose per-sphere tests
+// exclude them.
+static_assert(kSphereBatch == 4, "batch_may_gather takes four spheres");
+__device__ __forceinline__ bool batch_may_gather(const float (&mn)[kSphereBatch], float t0, float t1, float t2,
+                                                 float t3)
+{
+    const float2 d01 = __fadd2_rn(make_float2(t0, t1), make_float2(-mn[0], -mn[1]));
+    const float2 d23 = __fadd2_rn(make_float2(t2, t3), make_float2(-mn[2], -mn[3]));
+    return fmaxf(fmaxf(d01.x, d01.y), fmaxf(d23.x, d23.y)) >= 0.0f;
 }
 
 // sum over spheres s in [b, e) of frame F of max(0, d_act - (phi(p_s) - r_s))^2
@@ -107,7 +127,8 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         // spheres on a line through the frame origin: grid coordinates
         // gt + lambda_s gv, gt of the origin and gv of the rotated direction
         const f3 gv = axpy(rc.link_wg[j][2], F.c3, axpy(rc.link_wg[j][1], F.c2, scale(rc.link_wg[j][0], F.c1)));
-        const f3 gt = mk(fmaf(F.t.x, g.inv_res, g.bx), fmaf(F.t.y, g.inv_res, g.by), fmaf(F.t.z, g.inv_res, g.bz));
+        const float2 gtxy = __ffma2_rn(make_float2(F.t.x, F.t.y), g.inv_res_pk, g.bxy);
+        const f3 gt = mk(gtxy.x, gtxy.y, fmaf(F.t.z, g.inv_res, g.bz));
         f3 v{};
         if (SELF && sp) {
             v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
@@ -132,21 +153,19 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                     sp[(3 * s + 1) * 32] = p.y;
                     sp[(3 * s + 2) * 32] = p.z;
                 }
-                mn[i] = tex3D<float>(g.cmin_tex, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
+                const float2 gxy = __ffma2_rn(make_float2(lam, lam), make_float2(gv.x, gv.y), make_float2(gt.x, gt.y));
+                mn[i] = tex3D<float>(g.cmin_tex, gxy.x, gxy.y, fmaf(lam, gv.z, gt.z));
             }
-            // one branch for the batch: spheres to gather, as bits
-            unsigned need = 0u;
-#pragma unroll
-            for (int i = 0; i < kSphereBatch; ++i)
-                need |= (i < e - s0 && !(mn[i] > ls[i].y)) ? (1u << i) : 0u;
-            if (need)
+            // one branch for the batch (see batch_may_gather), then each sphere's own test
+            if (batch_may_gather(mn, ls[0].y, ls[1].y, ls[2].y, ls[3].y))
 #pragma unroll
             for (int i = 0; i < kSphereBatch; ++i) {
                 const int s = s0 + i;
-                if (need & (1u << i)) {
+                if (i < e - s0 && !(mn[i] > ls[i].y)) {
                     ++ngath;
                     const float lam = ls[i].x;
-                    const Cell c = locate_grid(g, fmaf(lam, gv.x, gt.x), fmaf(lam, gv.y, gt.y), fmaf(lam, gv.z, gt.z));
+                    const float2 gxy = __ffma2_rn(make_float2(lam, lam), make_float2(gv.x, gv.y), make_float2(gt.x, gt.y));
+                    const Cell c = locate_grid(g, gxy.x, gxy.y, fmaf(lam, gv.z, gt.z));
                     float vv[8];
                     corners<GT>(g, c.base, vv);
                     const float phi = interpolate(vv, c.fx, c.fy, c.fz);
@@ -172,15 +191,11 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             mn[i] = tex3D<float>(g.cmin_tex, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by),
                                  fmaf(p.z, g.inv_res, g.bz));
         }
-        unsigned need = 0u;
-#pragma unroll
-        for (int i = 0; i < kSphereBatch; ++i)
-            need |= (i < e - s0 && !(mn[i] > rc.sph_ls[s0 + i].y)) ? (1u << i) : 0u;
-        if (need)
+        if (batch_may_gather(mn, rc.sph_ls[s0].y, rc.sph_ls[s0 + 1].y, rc.sph_ls[s0 + 2].y, rc.sph_ls[s0 + 3].y))
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = s0 + i;
-            if (need & (1u << i)) {
+            if (i < e - s0 && !(mn[i] > rc.sph_ls[s].y)) {
                 // the few spheres near an obstacle: locate again with fractions
                 ++ngath;
                 const Cell c = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
@@ -333,15 +348,25 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     if (!SELF || terminal) sp = nullptr;
     float lq = 0.f, lqd = 0.f, ns = 0.f;
     if (!terminal) {
+        // joints in pairs through the packed FP32 units, the last one alone
+        float2 lq2 = make_float2(0.f, 0.f), lqd2 = make_float2(0.f, 0.f), ns2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < kNJ; ++j) {
-            const float a = limit_violation(q[j], rc.q_lo[j], rc.q_hi[j]);
-            const float b = limit_violation(qd[j], rc.qd_lo[j], rc.qd_hi[j]);
-            const float e = q[j] - rc.q_ref[j];
-            lq = fmaf(a, a, lq);
-            lqd = fmaf(b, b, lqd);
-            ns = fmaf(e, e, ns);
+        for (int p = 0; p < kNJ / 2; ++p) {
+            const float2 qq = make_float2(q[2 * p], q[2 * p + 1]), vv = make_float2(qd[2 * p], qd[2 * p + 1]);
+            const float2 a = limit_violation_pk(qq, rc.q_lo_pk[p], rc.q_hi_pk[p]);
+            const float2 b = limit_violation_pk(vv, rc.qd_lo_pk[p], rc.qd_hi_pk[p]);
+            const float2 e = __fadd2_rn(qq, make_float2(-rc.q_ref_pk[p].x, -rc.q_ref_pk[p].y));
+            lq2 = __ffma2_rn(a, a, lq2);
+            lqd2 = __ffma2_rn(b, b, lqd2);
+            ns2 = __ffma2_rn(e, e, ns2);
         }
+        constexpr int j = kNJ - 1;
+        const float a = limit_violation(q[j], rc.q_lo[j], rc.q_hi[j]);
+        const float b = limit_violation(qd[j], rc.qd_lo[j], rc.qd_hi[j]);
+        const float e = q[j] - rc.q_ref[j];
+        lq = fmaf(a, a, lq2.x + lq2.y);
+        lqd = fmaf(b, b, lqd2.x + lqd2.y);
+        ns = fmaf(e, e, ns2.x + ns2.y);
     }
     Frame F = base_frame();
     float env = 0.f;
@@ -357,7 +382,8 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     }
 #pragma unroll 1
     for (int j = 0; j < kNJ; ++j) {
-        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], (QMEM ? qa[j * qstride] : qr[0]) + rc.th0[j]);
+        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], (QMEM ? qa[j * qstride] : qr[0]) + rc.th0[j],
+                rc.sincos_pk);
         if (!QMEM) {
 #pragma unroll
             for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
@@ -391,6 +417,20 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
 }
 
 // ---------------------------------------------------------- warp scans
+// Inclusive prefix sum over the L lanes of each segment, for 7 values.
+__device__ __forceinline__ void seg_inclusive_scan(const float *x, float *in, int sl, int L)
+{
+#pragma unroll
+    for (int j = 0; j < kNJ; ++j) {
+        float v = x[j];
+        for (int d = 1; d < L; d <<= 1) {
+            const float t = __shfl_up_sync(0xffffffffu, v, d, L);
+            if (sl >= d) v += t;
+        }
+        in[j] = v;
+    }
+}
+
 // Exclusive prefix sum over the L lanes of each segment, for 7 values.
 __device__ __forceinline__ void seg_exclusive_scan(const float *x, float *ex, int sl, int L)
 {
@@ -524,9 +564,11 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 
         // sample and perturb (Algorithm 1, Eq. 27): eps ~ D, u = ubar + eps;
         // chunk sums T = sum_s u_s and TB = sum_s sum_{s'<=s} u_s' for the scans
+        // (sums start at -0, the identity of IEEE addition, so the first
+        // add folds away)
         float T[kNJ], TB[kNJ];
 #pragma unroll
-        for (int j = 0; j < kNJ; ++j) { T[j] = 0.f; TB[j] = 0.f; }
+        for (int j = 0; j < kNJ; ++j) { T[j] = -0.f; TB[j] = -0.f; }
 #pragma unroll 1
         for (int s = 0; s < C; ++s) {
             const int k = kbase + sl * C + s;
@@ -549,8 +591,33 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             }
         }
 
-        // roll-out (Eq. 7) by two segmented prefix scans
+        // roll-out (Eq. 7) by two segmented prefix scans.  One step per lane
+        // (STAGE, C = 1): T = u_k, and A_{k+1}, B_{k+1} are the inclusive
+        // scans of u and of A, into A0 and B0
         float A0[kNJ], B0[kNJ];
+        if (STAGE) {
+            seg_inclusive_scan(T, A0, sl, L);
+            seg_inclusive_scan(A0, B0, sl, L);
+            if (P == 2) {
+                // the first half's A_32, B_32 shift the second half's:
+                // A += A_32, B += B_32 + (sl + 1) A_32
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) {
+                    const float At = __shfl_sync(0xffffffffu, A0[j], 31);
+                    const float Bt = __shfl_sync(0xffffffffu, B0[j], 31);
+                    if (half == 0 && lane == 0) { sm.tot[pr][j] = At; sm.tot[pr][kNJ + j] = Bt; }
+                }
+                pair_barrier(pr);
+                if (half == 1) {
+#pragma unroll
+                    for (int j = 0; j < kNJ; ++j) {
+                        const float a0 = sm.tot[pr][j], b0 = sm.tot[pr][kNJ + j];
+                        B0[j] += fmaf(static_cast<float>(sl + 1), a0, b0);
+                        A0[j] += a0;
+                    }
+                }
+            }
+        } else {
         seg_exclusive_scan(T, A0, sl, L);
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) TB[j] = fmaf(static_cast<float>(C), A0[j], TB[j]);
@@ -574,6 +641,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 }
             }
         }
+        }
 
         // kinematics and costs of each of this lane's steps (Eqs. 6, 16-25),
         // then, on lane 0 of tile c0_tile, the k = 0 pass
@@ -585,29 +653,37 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         float lsum = 0.f, lcomp = 0.f;
         float runU[kNJ], runB[kNJ];
 #pragma unroll
-        for (int j = 0; j < kNJ; ++j) { runU[j] = 0.f; runB[j] = B0[j]; }
+        for (int j = 0; j < kNJ; ++j) { runU[j] = -0.f; runB[j] = B0[j]; }
         if (STAGE) {
-#pragma unroll 1
-            for (int s = 0; s < C; ++s) {
-                const int k = kbase + sl * C + s;
-                if (!(active && k < H)) break;
-                float u[kNJ];
-                float *qs = sm.qs + pm_idx(((warp * C + s) * kStageFloats) * 32, kWarps * kStageFloats * 32 -
+            // the lane's one step: q_{k+1}, qd_{k+1} from A0 = A_{k+1},
+            // B0 = B_{k+1}, and the control terms of u_k = T
+            const int k = kbase + sl;
+            if (active && k < H) {
+                float *qs = sm.qs + pm_idx((warp * kStageFloats) * 32, kWarps * kStageFloats * 32 -
                                            (kStageFloats - 1) * 32 - 31, kErrStage, g) + lane;
                 const float kp_dt = static_cast<float>(k + 1) * dt;
+                // joints in pairs through the packed FP32 units, the last one alone
+                const float2 dtp = make_float2(dt, dt), dt2p = make_float2(dt2, dt2), kpp = make_float2(kp_dt, kp_dt);
 #pragma unroll
-                for (int j = 0; j < kNJ; ++j) {
-                    u[j] = __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + sm.eps[E(warp, s, j) + lane];
-                    runU[j] += u[j];
-                    const float A = A0[j] + runU[j];           // A_{k+1}
-                    runB[j] += A;                               // B_{k+1}
-                    qs[j * 32] = fmaf(dt2, runB[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
-                    qs[(kNJ + j) * 32] = fmaf(dt, A, st.qd0[j]);
+                for (int p = 0; p < kNJ / 2; ++p) {
+                    const int j = 2 * p;
+                    const float2 A = make_float2(A0[j], A0[j + 1]);
+                    const float2 qd0 = make_float2(st.qd0[j], st.qd0[j + 1]);
+                    const float2 qq = __ffma2_rn(dt2p, make_float2(B0[j], B0[j + 1]),
+                                                 __ffma2_rn(kpp, qd0, make_float2(st.q0[j], st.q0[j + 1])));
+                    const float2 vv = __ffma2_rn(dtp, A, qd0);
+                    qs[j * 32] = qq.x; qs[(j + 1) * 32] = qq.y;
+                    qs[(kNJ + j) * 32] = vv.x; qs[(kNJ + j + 1) * 32] = vv.y;
+                }
+                {
+                    constexpr int j = kNJ - 1;
+                    qs[j * 32] = fmaf(dt2, B0[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
+                    qs[(kNJ + j) * 32] = fmaf(dt, A0[j], st.qd0[j]);
                 }
                 float *tr_u = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k,
                                                     static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
                                    : nullptr;
-                qs[(2 * kNJ) * 32] = control_cost<TRACE>(rc, u, tr_u);
+                qs[(2 * kNJ) * 32] = control_cost<TRACE>(rc, T, tr_u);
             }
         }
 #pragma unroll 1
