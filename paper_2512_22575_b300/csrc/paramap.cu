@@ -300,14 +300,14 @@ __global__ void joint_sincos_kernel(const float *x, float *sc, float *sc_ref, si
 struct Sigma { float s[8]; };
 
 __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint32_t s_hi,
-                                    uint32_t iter, float *eps)
+                                    uint32_t iter, float *eps, const __grid_constant__ SinCosPoly kp)
 {
     const size_t total = static_cast<size_t>(K) * H;
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const uint32_t m = static_cast<uint32_t>(i / H), k = static_cast<uint32_t>(i % H);
         float z[8];
-        step_normals(s_lo, s_hi, iter, m, k, z);
+        step_normals(s_lo, s_hi, iter, m, k, z, kp.kc);
         for (int j = 0; j < kNJ; ++j) eps[i * kNJ + j] = sg.s[j] * z[j];
     }
 }
@@ -964,6 +964,13 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         r.q_ref[j] = cp->q_ref[j];
     }
     for (int i = 0; i < 4; ++i) r.sincos_pk[i] = kSinCosPoly[i];
+    for (int j = 0; j < kNJ; ++j) {
+        r.fk_cs[j] = make_float2(r.ca[j], r.sa[j]);
+        r.fk_ad[j] = make_float2(r.a[j], r.d[j]);
+        r.fk_tw[j] = make_float2(r.th0[j], r.link_wg[j][0]);
+        r.fk_ww[j] = make_float2(r.link_wg[j][1], r.link_wg[j][2]);
+        r.fk_be[j] = make_int2(r.link_begin[j + 1], r.link_begin[j + 2]);
+    }
     for (int p = 0; p < kNJ / 2; ++p) {
         r.q_lo_pk[p] = make_float2(r.q_lo[2 * p], r.q_lo[2 * p + 1]);
         r.q_hi_pk[p] = make_float2(r.q_hi[2 * p], r.q_hi[2 * p + 1]);
@@ -1525,8 +1532,10 @@ pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed, uint3
     for (int j = 0; j < kNJ; ++j) sg.s[j] = sigma[j];
     const size_t total = static_cast<size_t>(K) * H;
     const unsigned blocks = static_cast<unsigned>(std::min<size_t>((total + 255) / 256, 65535));
+    SinCosPoly kp;
+    for (int i = 0; i < 4; ++i) kp.kc[i] = kSinCosPoly[i];
     sample_noise_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
-        K, H, sg, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), iter_index, eps);
+        K, H, sg, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), iter_index, eps, kp);
     PM_CUDA(nullptr, cudaGetLastError());
     return PM_OK;
 }

@@ -76,6 +76,12 @@ struct RobotConst {
     // coefficient pairs (sin, cos) of joint_sincos's Horner steps, highest
     // degree first (operands of packed FP32 FMAs, read from the parameter bank)
     float2 sincos_pk[4];
+    // the forward kinematics' per-joint constants in 8-byte pairs (one
+    // constant load each): (ca, sa), (a, d), (th0, link_wg[0]),
+    // (link_wg[1], link_wg[2]) and the frame's spheres (link_begin[j+1],
+    // link_begin[j+2])
+    float2 fk_cs[kNJ], fk_ad[kNJ], fk_tw[kNJ], fk_ww[kNJ];
+    int2 fk_be[kNJ];
     // joints (2p, 2p+1), p < 3, of the boxes of Eq. 21 and of q_ref
     float2 q_lo_pk[3], q_hi_pk[3], qd_lo_pk[3], qd_hi_pk[3], qdd_lo_pk[3], qdd_hi_pk[3], q_ref_pk[3];
     float link_lc[kNJ];           // frame layout: the bounding centre link_c = link_lc link_w
@@ -212,6 +218,55 @@ __device__ __forceinline__ void grid_dependency_prologue()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Coefficients of gen_sincos_poly.py (host copies; the kernels take the
+// sin/cos pairs from RobotConst::sincos_pk, the parameter bank):
+// (sin, cos) pairs, highest degree first, and the ln bracket, lowest first.
+constexpr float2 kSinCosPoly[4] = {{2.724328624e-06f, 2.445699101e-05f}, {-1.984003320e-04f, -1.388753648e-03f},
+                                   {8.333331905e-03f, 4.166664928e-02f}, {-1.666666716e-01f, -5.0e-01f}};
+constexpr float kLnP0 = 3.333333433e-01f, kLnP1 = 2.000006735e-01f, kLnP2 = 1.427491456e-01f,
+                kLnP3 = 1.167523712e-01f;
+constexpr float kRound = 12582912.0f;                  // 1.5 2^23: x + kRound rounds x to an integer
+
+// sin and cos of (pi/2) n + r, |r| <= 1.01 pi/4, given r and the bits qb of
+// a float whose low two bits are n mod 4: sin r and cos r by the odd and even
+// polynomials of gen_sincos_poly.py (least-squares fits on Chebyshev nodes,
+// within 0.9 ulp in float32 evaluation), their Horner steps paired in packed
+// FP32 FMAs, then the quadrant applied by a swap and two sign flips.
+__device__ __forceinline__ void sincos_quadrant(float r, unsigned qb, const float2 (&kc)[4], float &s, float &c)
+{
+    const float z = r * r;
+    const float2 zz = make_float2(z, z);
+    float2 p = __ffma2_rn(zz, kc[0], kc[1]);
+    p = __ffma2_rn(zz, p, kc[2]);
+    p = __ffma2_rn(zz, p, kc[3]);
+    const float sr = fmaf(r * z, p.x, r);
+    const float cr = fmaf(z, p.y, 1.0f);
+    const bool odd = (qb & 1u) != 0u;
+    const float sv = odd ? cr : sr, cv = odd ? sr : cr;
+    s = __uint_as_float(__float_as_uint(sv) ^ ((qb << 30) & 0x80000000u));          // n mod 4 in {2, 3}
+    c = __uint_as_float(__float_as_uint(cv) ^ (((qb + 1u) << 30) & 0x80000000u));   // n mod 4 in {1, 2}
+}
+
+// sin and cos of a joint angle x (Eq. 6).  Cody-Waite reduction by pi/2:
+// n = rint(x 2/pi), taken from the low bits of x 2/pi + 1.5 2^23 (valid for
+// |x| < 2^22 pi/2), r = x - n p1 - n p2 - n p3 with p1 + p2 + p3 = pi/2 in
+// three float32 parts; with FMA the first step is exact (x - n p1 is a
+// multiple of 2^-24 below 1 in magnitude).  Then sincos_quadrant.  Within 2
+// ulps for |x| <= 64 and 2^-23 absolute up to 1e4; NaN for non-finite x.
+__device__ __forceinline__ void joint_sincos(float x, float &s, float &c, const float2 (&kc)[4])
+{
+    constexpr float kTwoOverPi = 0.636619772367581343f;
+    constexpr float kPio2Hi = 1.57079637050628662f;        // float32(pi/2)
+    constexpr float kPio2Mid = -4.371138828673793e-8f;    // float32(pi/2 - kPio2Hi)
+    constexpr float kPio2Lo = -1.7763568394002505e-15f;   // float32(pi/2 - kPio2Hi - kPio2Mid)
+    const float t = fmaf(x, kTwoOverPi, kRound);
+    const float n = t - kRound;
+    float r = fmaf(-n, kPio2Hi, x);
+    r = fmaf(-n, kPio2Mid, r);
+    r = fmaf(-n, kPio2Lo, r);
+    sincos_quadrant(r, __float_as_uint(t), kc, s, c);
+}
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32: per round two 32x32 -> 64 bit products, words permuted and
 // xored with the key; the key is bumped by the Weyl constants each round.
@@ -238,29 +293,62 @@ __device__ __forceinline__ float word_to_uniform(uint32_t x)
     return fmaf(static_cast<float>(x >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
 }
 
-__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1)
+// ln u for u in [2^-24, 1) (the Box-Muller radius).  u = 2^e m with m in
+// [sqrt(1/2), sqrt(2)), split at the bits of sqrt(1/2) (the reduction of
+// the classic float logarithms, e.g. Tang's); ln m = 2 atanh(s) with
+// s = (m - 1)/(m + 1) = f/(2 + f), f = m - 1 exact, |s| <= 0.172, by
+// 2s (1 + s^2 P(s^2)), P the fit of gen_sincos_poly.py; e ln 2 in two
+// float32 parts.  Within 2 ulps (1.6 in emulation, plus the quotient's).
+__device__ __forceinline__ float ln_unit(float u)
 {
-    const float u0 = word_to_uniform(w0), u1 = word_to_uniform(w1);
+    constexpr float kLn2Hi = 0.693147182464599609f;        // float32(ln 2)
+    constexpr float kLn2Lo = -1.9046542121259336e-09f;     // float32(ln 2 - kLn2Hi)
+    const unsigned b = __float_as_uint(u);
+    const int e = static_cast<int>(b - 0x3f3504f3u) >> 23;
+    const float m = __uint_as_float(b - (static_cast<unsigned>(e) << 23));
+    const float f = m - 1.0f;
+    const float sq = __fdividef(f, 2.0f + f);               // 2 + f in [1.7, 2.5]: no special cases
+    const float z = sq * sq;
+    float p = fmaf(z, kLnP3, kLnP2);
+    p = fmaf(z, p, kLnP1);
+    p = fmaf(z, p, kLnP0);
+    const float s2 = sq + sq;
+    const float ef = static_cast<float>(e);
+    return fmaf(ef, kLn2Hi, fmaf(ef, kLn2Lo, fmaf(s2 * z, p, s2)));
+}
+
+// Two standard normals from two words (Eq. 27): radius sqrt(-2 ln u0),
+// angle 2 pi u1 = (pi/2) t with t = 4 u1 in (0, 4) exact, so the reduction
+// is exact too (n = rint(t), f = t - n in [-1/2, 1/2]) and the angle's
+// sin and cos come from sincos_quadrant at r = (pi/2) f.
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1, const float2 (&kc)[4])
+{
+    constexpr float kPio2 = 1.57079637050628662f;
+    const float u0 = word_to_uniform(w0);
     // v = -2 ln u0 lies in [1.2e-7, 33.3] (u0 in [2^-24, 1 - 2^-24]), so
     // v rsqrt(v) needs no special cases: within 3 ulp of sqrt(v)
-    const float v = -2.0f * logf(u0);
+    const float v = -2.0f * ln_unit(u0);
     const float r = v * rsqrtf(v);
+    // t = 4 u1 = 4 ((i + 1/2) 2^-23) = i 2^-21 + 2^-22
+    const float t = fmaf(static_cast<float>(w1 >> 9), 4.76837158203125e-7f, 2.384185791015625e-7f);
+    const float tq = t + kRound;
     float s, c;
-    sincospif(2.0f * u1, &s, &c);
+    sincos_quadrant((t - (tq - kRound)) * kPio2, __float_as_uint(tq), kc, s, c);
     z0 = r * c;
     z1 = r * s;
 }
 
 // Standard normals z[0..7] of roll-out m, step k (counter (m, k, b, iter)).
+// kc: the sin/cos coefficient pairs (RobotConst::sincos_pk or kSinCosPoly).
 __device__ __forceinline__ void step_normals(uint32_t seed_lo, uint32_t seed_hi, uint32_t iter,
-                                             uint32_t m, uint32_t k, float z[8])
+                                             uint32_t m, uint32_t k, float z[8], const float2 (&kc)[4])
 {
 #pragma unroll
     for (uint32_t b = 0; b < 2; ++b) {
         uint32_t x0 = m, x1 = k, x2 = b, x3 = iter;
         philox4x32_10(x0, x1, x2, x3, seed_lo, seed_hi);
-        box_muller(x0, x1, z[4 * b + 0], z[4 * b + 1]);
-        box_muller(x2, x3, z[4 * b + 2], z[4 * b + 3]);
+        box_muller(x0, x1, z[4 * b + 0], z[4 * b + 1], kc);
+        box_muller(x2, x3, z[4 * b + 2], z[4 * b + 3], kc);
     }
 }
 
@@ -300,47 +388,6 @@ __device__ __forceinline__ Frame base_frame()
 {
     return Frame{mk(1.f, 0.f, 0.f), mk(0.f, 1.f, 0.f), mk(0.f, 0.f, 1.f), mk(0.f, 0.f, 0.f)};
 }
-
-// sin and cos of a joint angle x (Eq. 6).  Cody-Waite reduction by pi/2:
-// n = rint(x 2/pi), taken from the low bits of x 2/pi + 1.5 2^23 (valid for
-// |x| < 2^22 pi/2), r = x - n p1 - n p2 - n p3 with p1 + p2 + p3 = pi/2 in
-// three float32 parts; with FMA the first step is exact (x - n p1 is a
-// multiple of 2^-24 below 1 in magnitude).  Then sin r and cos r on [-1.01 pi/4, 1.01 pi/4]
-// by the odd and even polynomials of gen_sincos_poly.py (least-squares fits
-// on Chebyshev nodes, within 0.9 ulp in float32 evaluation), their Horner
-// steps paired in packed FP32 FMAs, and the quadrant n mod 4 applied by a
-// swap and two sign flips.  Within 2 ulps for |x| <= 64 and 2^-23 absolute
-// up to 1e4; NaN for non-finite x.
-__device__ __forceinline__ void joint_sincos(float x, float &s, float &c, const float2 (&kc)[4])
-{
-    constexpr float kTwoOverPi = 0.636619772367581343f;
-    constexpr float kRound = 12582912.0f;                  // 1.5 2^23
-    constexpr float kPio2Hi = 1.57079637050628662f;        // float32(pi/2)
-    constexpr float kPio2Mid = -4.371138828673793e-8f;    // float32(pi/2 - kPio2Hi)
-    constexpr float kPio2Lo = -1.7763568394002505e-15f;   // float32(pi/2 - kPio2Hi - kPio2Mid)
-    const float t = fmaf(x, kTwoOverPi, kRound);
-    const float n = t - kRound;
-    const unsigned qb = __float_as_uint(t);                // n mod 4 in the low bits
-    float r = fmaf(-n, kPio2Hi, x);
-    r = fmaf(-n, kPio2Mid, r);
-    r = fmaf(-n, kPio2Lo, r);
-    const float z = r * r;
-    const float2 zz = make_float2(z, z);
-    float2 p = __ffma2_rn(zz, kc[0], kc[1]);
-    p = __ffma2_rn(zz, p, kc[2]);
-    p = __ffma2_rn(zz, p, kc[3]);
-    const float sr = fmaf(r * z, p.x, r);
-    const float cr = fmaf(z, p.y, 1.0f);
-    const bool odd = (qb & 1u) != 0u;
-    const float sv = odd ? cr : sr, cv = odd ? sr : cr;
-    s = __uint_as_float(__float_as_uint(sv) ^ ((qb << 30) & 0x80000000u));          // n mod 4 in {2, 3}
-    c = __uint_as_float(__float_as_uint(cv) ^ (((qb + 1u) << 30) & 0x80000000u));   // n mod 4 in {1, 2}
-}
-
-// joint_sincos's coefficients (sin, cos), highest degree first (host copy,
-// loaded into RobotConst::sincos_pk)
-constexpr float2 kSinCosPoly[4] = {{2.724328624e-06f, 2.445699101e-05f}, {-1.984003320e-04f, -1.388753648e-03f},
-                                   {8.333331905e-03f, 4.166664928e-02f}, {-1.666666716e-01f, -5.0e-01f}};
 
 // T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d)  (modified DH, Eq. 6).
 // kc: joint_sincos's coefficients as the kernel holds them (RobotConst::

@@ -120,13 +120,16 @@ __device__ __forceinline__ bool batch_may_gather(const float (&mn)[kSphereBatch]
 // interpolated from their 8 corners.
 template <typename GT, bool SELF>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
-                                          const Frame &F, int j, int b, int e, unsigned &ngath, float *sp)
+                                          const Frame &F, int j, int b, int e, float wg0, bool count,
+                                          unsigned &ngath, float *sp)
 {
     float env = 0.f;
     if (rc.link_line[j]) {
         // spheres on a line through the frame origin: grid coordinates
         // gt + lambda_s gv, gt of the origin and gv of the rotated direction
-        const f3 gv = axpy(rc.link_wg[j][2], F.c3, axpy(rc.link_wg[j][1], F.c2, scale(rc.link_wg[j][0], F.c1)));
+        // (wg0 = link_wg[j][0], loaded with th0)
+        const float2 ww = rc.fk_ww[j];
+        const f3 gv = axpy(ww.y, F.c3, axpy(ww.x, F.c2, scale(wg0, F.c1)));
         const float2 gtxy = __ffma2_rn(make_float2(F.t.x, F.t.y), g.inv_res_pk, g.bxy);
         const f3 gt = mk(gtxy.x, gtxy.y, fmaf(F.t.z, g.inv_res, g.bz));
         f3 v{};
@@ -162,7 +165,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             for (int i = 0; i < kSphereBatch; ++i) {
                 const int s = s0 + i;
                 if (i < e - s0 && !(mn[i] > ls[i].y)) {
-                    ++ngath;
+                    ngath += count ? 1u : 0u;
                     const float lam = ls[i].x;
                     const float2 gxy = __ffma2_rn(make_float2(lam, lam), make_float2(gv.x, gv.y), make_float2(gt.x, gt.y));
                     const Cell c = locate_grid(g, gxy.x, gxy.y, fmaf(lam, gv.z, gt.z));
@@ -197,7 +200,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             const int s = s0 + i;
             if (i < e - s0 && !(mn[i] > rc.sph_ls[s].y)) {
                 // the few spheres near an obstacle: locate again with fractions
-                ++ngath;
+                ngath += count ? 1u : 0u;
                 const Cell c = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
                 float v[8];
                 corners<GT>(g, c.base, v);
@@ -346,8 +349,11 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
                                             int qstride = 1)
 {
     if (!SELF || terminal) sp = nullptr;
+    // The terminal step (one lane in H) runs the step's terms too and drops
+    // them at the end: the lanes of a warp run together, and a branch around
+    // them would cost every lane its instructions.
     float lq = 0.f, lqd = 0.f, ns = 0.f;
-    if (!terminal) {
+    {
         // joints in pairs through the packed FP32 units, the last one alone
         float2 lq2 = make_float2(0.f, 0.f), lqd2 = make_float2(0.f, 0.f), ns2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -382,13 +388,14 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     }
 #pragma unroll 1
     for (int j = 0; j < kNJ; ++j) {
-        dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], (QMEM ? qa[j * qstride] : qr[0]) + rc.th0[j],
-                rc.sincos_pk);
+        const float2 cs = rc.fk_cs[j], ad = rc.fk_ad[j], tw = rc.fk_tw[j];
+        dh_step(F, cs.x, cs.y, ad.x, ad.y, (QMEM ? qa[j * qstride] : qr[0]) + tw.x, rc.sincos_pk);
         if (!QMEM) {
 #pragma unroll
             for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
         }
-        if (!terminal) env += link_env<GT, SELF>(rc, g, F, j, rc.link_begin[j + 1], rc.link_begin[j + 2], ngath, sp);
+        const int2 be = rc.fk_be[j];
+        env += link_env<GT, SELF>(rc, g, F, j, be.x, be.y, tw.y, !terminal, ngath, sp);
         if (SELF && sp && !rc.self_frames &&
             pm_ok(3 * rc.n_spheres + 3 * j + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {
             const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
@@ -529,13 +536,14 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     const int R = 32 / L;
     const int seg = lane / L, sl = lane % L;
     const int H = job.H;
-    // slot (w, s, j) of the [kWarps][C][7][32] tile arrays (lane added by the caller)
+    // this lane's slot (w, s, j) of the [kWarps][C][7][32] tile arrays
     auto E = [&](int w, int s, int j) {
-        return static_cast<int>(pm_idx(((w * C + s) * kNJ + j) * 32, kWarps * C * kNJ * 32 - 31, kErrTile, g));
+        return static_cast<int>(pm_idx(((w * C + s) * kNJ + j) * 32 + lane, kWarps * C * kNJ * 32, kErrTile, g));
     };
+
     for (int s = 0; s < C; ++s)
 #pragma unroll
-        for (int j = 0; j < kNJ; ++j) sm.acc[E(warp, s, j) + lane] = 0.f;
+        for (int j = 0; j < kNJ; ++j) sm.acc[E(warp, s, j)] = 0.f;
     __syncthreads();
 
     float run_m = CUDART_INF_F, run_z = 0.f;
@@ -576,7 +584,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             const bool live = active && k < H;
             if (live) {
                 step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
-                             static_cast<uint32_t>(k), z);
+                             static_cast<uint32_t>(k), z, rc.sincos_pk);
             }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
@@ -585,7 +593,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 if (job.noise_dtype == 1) e = __half2float(__float2half_rn(e));
                 else if (job.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
                 const float u = live ? __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + e : 0.f;
-                sm.eps[E(warp, s, j) + lane] = e;
+                sm.eps[E(warp, s, j)] = e;
                 T[j] += u;
                 TB[j] += T[j];
             }
@@ -719,7 +727,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 const float kp_dt = static_cast<float>(k + 1) * dt;
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
-                    u[j] = __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + sm.eps[E(warp, s, j) + lane];
+                    u[j] = __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + sm.eps[E(warp, s, j)];
                     runU[j] += u[j];
                     const float A = A0[j] + runU[j];           // A_{k+1}
                     runB[j] += A;                               // B_{k+1}
@@ -773,8 +781,8 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             for (int s = 0; s < C; ++s)
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
-                    float &acc = sm.acc[E(warp, s, j) + lane];
-                    acc = fmaf(acc, f_old, f_new * sm.eps[E(warp, s, j) + lane]);
+                    float &acc = sm.acc[E(warp, s, j)];
+                    acc = fmaf(acc, f_old, f_new * sm.eps[E(warp, s, j)]);
                 }
             run_m = nm;
         }
@@ -793,7 +801,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         for (int s = 0; s < C; ++s)
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                float &mine = sm.acc[E(warp, s, j) + lane];
+                float &mine = sm.acc[E(warp, s, j)];
                 const float o = __shfl_xor_sync(0xffffffffu, mine, off);
                 mine = mine * fa + o * fb;
             }
@@ -818,7 +826,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 if (k < H && pm_ok(k < C * L * P, kErrBlock, g)) {
 #pragma unroll
                     for (int j = 0; j < kNJ; ++j)
-                        sm.blk[k * kNJ + j] = fmaf(fw, sm.acc[E(warp, s, j) + lane], sm.blk[k * kNJ + j]);
+                        sm.blk[k * kNJ + j] = fmaf(fw, sm.acc[E(warp, s, j)], sm.blk[k * kNJ + j]);
                 }
             }
         }

@@ -9,7 +9,11 @@ library is chosen when the package is imported) and runs the plain
 iteration, ragged and maximal shapes, every tile shape, the trace, the
 host-buffer graph path, a replan, a batch through both batch kernels, the
 self-collision variant and the no-allocation entry point; every word must
-stay 0 and the results must still match the oracle.
+stay 0 and the results must still match the oracle: costs within S_REL, U*
+within U_ISO of the FP64 update from the GPU's own costs, and within U_ABS of
+the oracle's U* where the soft-min is well conditioned (the conditioning
+reading of the cost weights: with few roll-outs and lambda = 0.05 the FP32
+rounding of S alone can move U* by more than U_ABS).
 """
 import json
 import os
@@ -18,6 +22,8 @@ import sys
 import textwrap
 
 import pytest
+
+from parity_common import S_REL, U_ABS, U_ISO
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -35,7 +41,7 @@ CHILD = textwrap.dedent("""
     sys.path.insert(0, {tests!r})
     import paper_2512_22575_b300 as pm
     import oracle, workloads
-    from parity_common import Scene, SIGMA, S_REL, U_ABS
+    from parity_common import Scene, SIGMA, S_REL, U_ABS, first_order_bound, fp64_update_from_costs
     out = {{"checked": pm.bounds_checked(), "lib": pm.lib_path(), "words": {{}}, "parity": {{}}}}
     dev = torch.device("cuda:0")
     sc = Scene("cfg1_seed3")
@@ -53,7 +59,10 @@ CHILD = textwrap.dedent("""
         p.smpc_iterate(sc.q0, sc.qd0, sc.T, Ug, K, 0.02, 0.05, SIGMA, seed, it, costs_out=Sg)
         p.set_tile_shape(0, 0, 0)
         Uo, So, _ = sc.oracle_iterate(U, K, 0.02, 0.05, SIGMA, seed, it)
-        return float((np.abs(Sg - So) / np.abs(So)).max()), float(np.abs(Ug - Uo).max())
+        eps = oracle.eps_tensor(seed, it, K, H, SIGMA)
+        Uiso, _ = fp64_update_from_costs(Sg, eps, U, 0.05)
+        return (float((np.abs(Sg - So) / np.abs(So)).max()), float(np.abs(Ug - Uo).max()),
+                float(np.abs(Ug - Uiso).max()), first_order_bound(Sg, So, SIGMA, 0.05))
 
     out["parity"]["cfg1_graph"] = both(256, 32, 7, 0)
     word("cfg1_graph")
@@ -128,5 +137,12 @@ def test_checked_build_finds_no_violation_and_keeps_parity():
     bad = {k: v for k, v in res["words"].items() if v != 0}
     assert not bad, f"bounds violations (bit mask per workload): {bad}"
     assert len(res["words"]) >= 24
-    for tag, (s_rel, u_abs) in res["parity"].items():
-        assert s_rel <= 1e-4 and u_abs <= 1e-5, (tag, s_rel, u_abs)
+    for tag, (s_rel, u_abs, u_iso, bound) in res["parity"].items():
+        # costs within S_REL and the update exact given the GPU's costs
+        # (U_ISO) everywhere; U* against the oracle's within U_ABS wherever the
+        # soft-min is well conditioned (first-order bound of the FP32 cost
+        # rounding sigma max|dS|/lambda below U_ABS / 2; on the few-roll-out
+        # shapes it is not, and that bound, not the kernel, sets the error)
+        assert s_rel <= S_REL and u_iso <= U_ISO, (tag, s_rel, u_iso)
+        assert u_abs <= U_ABS or bound > U_ABS / 2, (tag, u_abs, bound)
+        print(f"{tag}: S rel {s_rel:.1e}, |U-U_iso| {u_iso:.1e}, |U-U_ref| {u_abs:.1e}, bound {bound:.1e}")
