@@ -1,11 +1,14 @@
-"""CPU checks of the joint sin/cos polynomials the kernels use (Eq. 6).
+"""CPU checks of the polynomials the kernels use for the joint sin/cos
+(Eq. 6) and the Box-Muller radius and angle (Eq. 27).
 
-The coefficients in smpc_device.cuh (kSinCosPoly) must be those that
-gen_sincos_poly.py fits, and the float32 evaluation of the polynomials (every
-operation rounded to float32, as emulated by that script) must stay within
-one ulp of sin and cos on the reduced range [-1.01 pi/4, 1.01 pi/4].  A
-Taylor check pins the fit: the leading coefficients are -1/6 and -1/2 to
-float32 rounding, the next ones 1/120 and 1/24 within 1e-5 relative.
+The coefficients in smpc_device.cuh (kSinCosPoly, kLnP0-3) must be those
+that gen_sincos_poly.py fits, and the float32 evaluation (every operation
+rounded to float32, as emulated by that script) must stay within one ulp of
+sin and cos on the reduced range [-1.01 pi/4, 1.01 pi/4] and within two ulps
+of ln u on the sampler's uniforms u = (i + 1/2) 2^-23.  Taylor checks pin the
+fits: the leading sin/cos coefficients are -1/6 and -1/2 to float32
+rounding, the next ones 1/120 and 1/24 within 1e-5 relative; the atanh
+series' 1/3 and 1/5 within 1e-5.
 """
 import importlib.util
 import os
@@ -59,3 +62,26 @@ def test_float32_evaluation_within_one_ulp():
     uc = np.spacing(np.abs(np.cos(r)).astype(np.float32)).astype(np.float64)
     assert np.max(np.abs(s - np.sin(r)) / us) < 1.0
     assert np.max(np.abs(c - np.cos(r)) / uc) < 1.0
+
+
+def header_ln_coefficients():
+    src = open(os.path.join(CSRC, "smpc_device.cuh")).read()
+    vals = [float(re.search(r"kLnP%d = (-?\d\.\d+e[-+]\d+)f" % i, src).group(1)) for i in range(4)]
+    return np.array(vals, dtype=np.float32)
+
+
+def test_ln_header_matches_generator_and_taylor():
+    gen = load_generator()
+    L = header_ln_coefficients()
+    np.testing.assert_allclose(L, gen.fit_ln(), rtol=2e-7)
+    assert abs(L[0] * 3.0 - 1.0) < 1e-5 and abs(L[1] * 5.0 - 1.0) < 1e-5
+
+
+def test_ln_float32_evaluation_within_two_ulps():
+    gen = load_generator()
+    L = header_ln_coefficients()
+    i = np.concatenate([np.arange(0, 1 << 23, 5), np.arange((1 << 23) - 4096, 1 << 23)]).astype(np.int64)
+    u = gen.f32((i + 0.5) * 2.0 ** -23)
+    ln = gen.ln_unit(u, L)
+    ulp = np.spacing(np.abs(np.log(u)).astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(ln - np.log(u)) / ulp) < 2.0
