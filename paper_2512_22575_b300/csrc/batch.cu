@@ -438,6 +438,7 @@ pm_status stage_batch(pm_batch *b, const pm_batch_item *it, int n, const Plan &p
         I.job.inv_lambda = 1.0f / x.lambda;
         I.job.noise_dtype = c->noise_dtype;
         I.job.dyn = nullptr;
+        I.job.rk = nullptr;         // the batch kernels derive the round keys (one key per instance)
         I.c0 = b->d_c0 + 2 * i;
         if (flags & PM_BATCH_REPLAN) {
             I.q_out = x.q;

@@ -540,6 +540,7 @@ pm_status enqueue_iteration(pm_ctx *c, cudaStream_t s, IterKernel fn, int nb, si
     a.cs.iter = iter;
     a.cs.dt = dt;
     a.cs.inv_lambda = trace ? 1.0f : 1.0f / lambda;
+    philox_round_keys(a.cs.seed_lo, a.cs.seed_hi, a.rk);
     const bool prof = c->prof && !trace;
     if (prof) {
         while (c->prof_ev.size() < c->prof_used + 2) {

@@ -285,6 +285,31 @@ __device__ __forceinline__ void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32
     }
 }
 
+// Round keys of Philox4x32-10: (k0 + r W0, k1 + r W1) for rounds r < 10.
+// A kernel that knows the key at launch takes them as parameters, so the
+// rounds read them in place instead of bumping the key.
+__host__ __device__ inline void philox_round_keys(uint32_t k0, uint32_t k1, uint2 (&rk)[10])
+{
+    for (int r = 0; r < 10; ++r) {
+        rk[r].x = k0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+        rk[r].y = k1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+    }
+}
+
+// philox4x32_10 with the round keys given
+__device__ __forceinline__ void philox4x32_10_rk(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+                                                 const uint2 (&rk)[10])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        const uint32_t y0 = hi1 ^ x1 ^ rk[r].x;
+        const uint32_t y2 = hi0 ^ x3 ^ rk[r].y;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+    }
+}
+
 // u = ((x >> 9) + 0.5) 2^-23: a 23-bit integer plus one half fits the 24-bit
 // significand, so u is exact in FP32 and strictly inside (0, 1).
 __device__ __forceinline__ float word_to_uniform(uint32_t x)
@@ -339,14 +364,17 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, 
 }
 
 // Standard normals z[0..7] of roll-out m, step k (counter (m, k, b, iter)).
-// kc: the sin/cos coefficient pairs (RobotConst::sincos_pk or kSinCosPoly).
+// kc: the sin/cos coefficient pairs (RobotConst::sincos_pk or kSinCosPoly);
+// rk: the key's round keys (philox_round_keys), or null to derive them.
 __device__ __forceinline__ void step_normals(uint32_t seed_lo, uint32_t seed_hi, uint32_t iter,
-                                             uint32_t m, uint32_t k, float z[8], const float2 (&kc)[4])
+                                             uint32_t m, uint32_t k, float z[8], const float2 (&kc)[4],
+                                             const uint2 (*rk)[10] = nullptr)
 {
 #pragma unroll
     for (uint32_t b = 0; b < 2; ++b) {
         uint32_t x0 = m, x1 = k, x2 = b, x3 = iter;
-        philox4x32_10(x0, x1, x2, x3, seed_lo, seed_hi);
+        if (rk) philox4x32_10_rk(x0, x1, x2, x3, *rk);
+        else philox4x32_10(x0, x1, x2, x3, seed_lo, seed_hi);
         box_muller(x0, x1, z[4 * b + 0], z[4 * b + 1], kc);
         box_muller(x2, x3, z[4 * b + 2], z[4 * b + 3], kc);
     }
@@ -576,19 +604,19 @@ __device__ __forceinline__ float quad_cost(const float xi[6], const float *Q)
     return 0.5f * s;
 }
 
-// delta(x) of Eq. 21 on the tightened box [lo, hi].
+// delta(x) of Eq. 21 on the tightened box [lo, hi] (lo < hi): x - hi above
+// the box, x - lo below it, 0 inside, as x minus x clamped to the box (the
+// same value, rounding included; NaN for NaN x).
 __device__ __forceinline__ float limit_violation(float x, float lo, float hi)
 {
-    return fmaxf(x - hi, 0.0f) + fminf(x - lo, 0.0f);
+    return x - fminf(fmaxf(x, lo), hi);
 }
 
 // limit_violation of two joints at once
 __device__ __forceinline__ float2 limit_violation_pk(float2 x, float2 lo, float2 hi)
 {
-    const float2 dh = __fadd2_rn(x, make_float2(-hi.x, -hi.y));
-    const float2 dl = __fadd2_rn(x, make_float2(-lo.x, -lo.y));
-    return __fadd2_rn(make_float2(fmaxf(dh.x, 0.0f), fmaxf(dh.y, 0.0f)),
-                      make_float2(fminf(dl.x, 0.0f), fminf(dl.y, 0.0f)));
+    const float2 cl = make_float2(fminf(fmaxf(x.x, lo.x), hi.x), fminf(fmaxf(x.y, lo.y), hi.y));
+    return __fadd2_rn(x, make_float2(-cl.x, -cl.y));
 }
 
 // ------------------------------------------------------ compensated sums

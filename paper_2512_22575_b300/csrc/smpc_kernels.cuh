@@ -72,6 +72,7 @@ struct IterArgs {
     int noise_dtype;            // PM_F32 (0), PM_F16 (1) or PM_BF16 (2): rounding of eps
     int K, H;
     CallScalars cs;             // seed, iteration index, dt, 1/lambda (see CallInputs::dyn)
+    uint2 rk[10];               // Philox round keys of cs's seed (kernels without CallInputs::dyn)
 };
 
 // ------------------------------------------------------------ cost terms
@@ -483,6 +484,8 @@ struct TileJob {
     // DYN kernels: the call's scalars in shared memory (they replace the five
     // above), read where they are used so that they hold no registers
     const CallScalars *dyn;
+    // the seed's Philox round keys in the kernel's parameters, or null
+    const uint2 (*rk)[10];
 };
 
 // A call scalar of a tile job: the field, or with DYN its copy in shared
@@ -584,7 +587,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             const bool live = active && k < H;
             if (live) {
                 step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
-                             static_cast<uint32_t>(k), z, rc.sincos_pk);
+                             static_cast<uint32_t>(k), z, rc.sincos_pk, DYN ? nullptr : job.rk);
             }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
@@ -596,6 +599,15 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 sm.eps[E(warp, s, j)] = e;
                 T[j] += u;
                 TB[j] += T[j];
+            }
+            if (STAGE && live) {
+                // one step per lane: its control terms now (T = u_k), staged
+                // with its state below, so that u holds no registers in the scans
+                float *tr_u = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k,
+                                                    static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
+                                   : nullptr;
+                sm.qs[pm_idx((warp * kStageFloats + 2 * kNJ) * 32, kWarps * kStageFloats * 32 - 31, kErrStage, g) + lane] =
+                    control_cost<TRACE>(rc, T, tr_u);
             }
         }
 
@@ -664,7 +676,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         for (int j = 0; j < kNJ; ++j) { runU[j] = -0.f; runB[j] = B0[j]; }
         if (STAGE) {
             // the lane's one step: q_{k+1}, qd_{k+1} from A0 = A_{k+1},
-            // B0 = B_{k+1}, and the control terms of u_k = T
+            // B0 = B_{k+1} (its control terms are staged already)
             const int k = kbase + sl;
             if (active && k < H) {
                 float *qs = sm.qs + pm_idx((warp * kStageFloats) * 32, kWarps * kStageFloats * 32 -
@@ -688,10 +700,6 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                     qs[j * 32] = fmaf(dt2, B0[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
                     qs[(kNJ + j) * 32] = fmaf(dt, A0[j], st.qd0[j]);
                 }
-                float *tr_u = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k,
-                                                    static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
-                                   : nullptr;
-                qs[(2 * kNJ) * 32] = control_cost<TRACE>(rc, T, tr_u);
             }
         }
 #pragma unroll 1
@@ -890,9 +898,11 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     job.K = a.K;
     job.H = a.H;
     job.nb = gridDim.x;
+    job.rk = nullptr;
     if (DYN) {
         job.dyn = &st.cs;
     } else {
+        job.rk = &a.rk;
         job.seed_lo = a.cs.seed_lo;
         job.seed_hi = a.cs.seed_hi;
         job.iter = a.cs.iter;
