@@ -214,6 +214,15 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
     return env;
 }
 
+// |c_a - c_b| from a squared distance d2 of a pair in contact range: d2 in
+// [1e-30, ...) times its reciprocal square root (within 3 ulp of sqrt; the
+// correctly rounded sqrtf costs a refinement and a special-value path).
+__device__ __forceinline__ float pair_distance(float d2)
+{
+    const float v = fmaxf(d2, 1e-30f);
+    return v * rsqrtf(v);
+}
+
 // Self-collision term (Eqs. 18-20): w_self sum over S of max(0, -d_self)^2,
 // d_self = |c_a - c_b| - (r_a + r_b), from the sphere and bounding-sphere
 // centres the step stored in its lane's slots sp (stride 32 floats).
@@ -250,24 +259,34 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
             const float wa2 = rc.link_w2[fa], wb2 = rc.link_w2[fb];
             const int a_lo = rc.link_begin[fa + 1], a_hi = rc.link_begin[fa + 2];
             const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
-            float lb[kSelfDense], Qb[kSelfDense], br[kSelfDense];
+            // frame b's spheres in pairs (2h, 2h+1) for the packed FP32 units:
+            // lambda, Q_b and radius (past nb: the last sphere again, masked)
+            static_assert(kSelfDense == 4, "two pairs of frame-b spheres");
+            float2 lb[2], Qb[2], br[2];
 #pragma unroll
-            for (int i = 0; i < kSelfDense; ++i) {
-                const int sb = b_lo + min(i, nb - 1);
-                lb[i] = rc.sph_ls[sb].x;
-                Qb[i] = lb[i] * fmaf(lb[i], wb2, -Db2);
-                br[i] = rc.sph_r[sb];
+            for (int h = 0; h < 2; ++h) {
+                const int s0 = b_lo + min(2 * h, nb - 1), s1 = b_lo + min(2 * h + 1, nb - 1);
+                lb[h] = make_float2(rc.sph_ls[s0].x, rc.sph_ls[s1].x);
+                br[h] = make_float2(rc.sph_r[s0], rc.sph_r[s1]);
+                Qb[h] = __fmul2_rn(lb[h], __ffma2_rn(lb[h], make_float2(wb2, wb2), make_float2(-Db2, -Db2)));
             }
             for (int a = a_lo; a < a_hi; ++a) {
                 const float la = rc.sph_ls[a].x, ra = rc.sph_r[a];
                 const float Pa = fmaf(la, fmaf(la, wa2, Da2), D), ma = la * Vab2;
 #pragma unroll
-                for (int i = 0; i < kSelfDense; ++i) {
-                    const float d2 = fmaf(ma, lb[i], Pa + Qb[i]);
-                    const float rs = ra + br[i];
-                    const float t = __fadd_ru(rs, 1e-5f);
-                    if (i < nb && d2 <= __fmul_ru(t, t)) {
-                        const float del = fmaxf(rs - sqrtf(fmaxf(d2, 0.f)), 0.f);
+                for (int h = 0; h < 2; ++h) {
+                    // the same operations as per pair: d2 = m_a l_b + (P_a + Q_b),
+                    // threshold (r_a + r_b + 1e-5)^2 rounded up
+                    const float2 d2 = __ffma2_rn(make_float2(ma, ma), lb[h], __fadd2_rn(make_float2(Pa, Pa), Qb[h]));
+                    const float2 rs = __fadd2_rn(make_float2(ra, ra), br[h]);
+                    const float2 t = __fadd2_ru(rs, make_float2(1e-5f, 1e-5f));
+                    const float2 t2 = __fmul2_ru(t, t);
+                    if (2 * h < nb && d2.x <= t2.x) {
+                        const float del = fmaxf(rs.x - pair_distance(d2.x), 0.f);
+                        acc = fmaf(del, del, acc);
+                    }
+                    if (2 * h + 1 < nb && d2.y <= t2.y) {
+                        const float del = fmaxf(rs.y - pair_distance(d2.y), 0.f);
                         acc = fmaf(del, del, acc);
                     }
                 }
@@ -307,7 +326,7 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
                     const float rs = ra + br[i];
                     const float t = __fadd_ru(rs, 1e-5f);
                     if (i < nb && d2 <= __fmul_ru(t, t)) {
-                        const float del = fmaxf(rs - sqrtf(d2), 0.f);
+                        const float del = fmaxf(rs - pair_distance(d2), 0.f);
                         acc = fmaf(del, del, acc);
                     }
                 }
@@ -331,7 +350,7 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
             const float ez = az - sp[(b + 2) * 32];
             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
             if (d2 <= pr.z) {           // otherwise |c_a - c_b| > r_a + r_b: exactly 0
-                const float del = fmaxf(pr.y - sqrtf(d2), 0.f);
+                const float del = fmaxf(pr.y - pair_distance(d2), 0.f);
                 acc = fmaf(del, del, acc);
             }
         }
@@ -862,11 +881,12 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 // steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
 // totals of the first half and their partial costs through shared memory.
 // MINB is the residency the registers are fitted to: 6 blocks per SM for
-// the one-step shapes (80 registers), 5 for the others; the one-step
-// shapes also have a kDenseBlocks instantiation (72 registers, neither
-// spills), which the host picks when its extra units save a round of
-// tiles on a short launch.
-template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 ? 6 : 5), bool DYN = false>
+// the one-step shapes without the self term (80 registers), 5 for the
+// others (96; with the self term the 80-register fit spills and runs
+// slower); the one-step shapes also have a kDenseBlocks instantiation (72
+// registers, no spills), which the host picks when its extra units save a
+// round of tiles on a short launch.
+template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 && !SELF ? 6 : 5), bool DYN = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
                       const __grid_constant__ IterArgs a)
