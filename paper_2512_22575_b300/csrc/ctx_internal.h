@@ -119,6 +119,10 @@ inline GridConst grid_const(const pm_ctx *c)
     g.mz = static_cast<float>(c->gd.nz - 1);
     g.inv_res_pk = make_float2(g.inv_res, g.inv_res);
     g.bxy = make_float2(g.bx, g.by);
+    g.res = c->gd.res;
+    g.mbxy = make_float2(static_cast<float>(-static_cast<double>(g.bx) * c->gd.res),
+                         static_cast<float>(-static_cast<double>(g.by) * c->gd.res));
+    g.mbz = static_cast<float>(-static_cast<double>(g.bz) * c->gd.res);
     g.err = c->d_err;
     return g;
 }

@@ -965,9 +965,13 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         r.q_ref[j] = cp->q_ref[j];
     }
     for (int i = 0; i < 4; ++i) r.sincos_pk[i] = kSinCosPoly[i];
+    r.flange_dg = static_cast<float>(static_cast<double>(rb->flange_d) / static_cast<double>(gd->res));
+    for (int i = 0; i < kMaxSpheres + kSpherePad; ++i)
+        for (int k = 0; k < 3; ++k) r.sph_off_g[i][k] = static_cast<float>(r.sph_off[i][k] / static_cast<double>(gd->res));
     for (int j = 0; j < kNJ; ++j) {
         r.fk_cs[j] = make_float2(r.ca[j], r.sa[j]);
-        r.fk_ad[j] = make_float2(r.a[j], r.d[j]);
+        r.fk_ad[j] = make_float2(static_cast<float>(r.a[j] / static_cast<double>(gd->res)),
+                                 static_cast<float>(r.d[j] / static_cast<double>(gd->res)));
         r.fk_tw[j] = make_float2(r.th0[j], r.link_wg[j][0]);
         r.fk_ww[j] = make_float2(r.link_wg[j][1], r.link_wg[j][2]);
         r.fk_be[j] = make_int2(r.link_begin[j + 1], r.link_begin[j + 2]);

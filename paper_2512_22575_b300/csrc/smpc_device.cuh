@@ -82,6 +82,12 @@ struct RobotConst {
     // link_begin[j+2])
     float2 fk_cs[kNJ], fk_ad[kNJ], fk_tw[kNJ], fk_ww[kNJ];
     int2 fk_be[kNJ];
+    // The iteration kernels run the chain in grid units (the base frame at
+    // the world origin's grid coordinate, lengths divided by the voxel
+    // size), so a frame's origin is already the texture coordinate of the
+    // skip bounds: fk_ad is (a, d) / res, and these are the other lengths
+    float flange_dg;                                 // flange_d / res
+    float sph_off_g[kMaxSpheres + kSpherePad][3];    // sph_off / res
     // joints (2p, 2p+1), p < 3, of the boxes of Eq. 21 and of q_ref
     float2 q_lo_pk[3], q_hi_pk[3], qd_lo_pk[3], qd_hi_pk[3], qdd_lo_pk[3], qdd_hi_pk[3], q_ref_pk[3];
     float link_lc[kNJ];           // frame layout: the bounding centre link_c = link_lc link_w
@@ -118,6 +124,9 @@ struct GridConst {
     float bx, by, bz;             // -origin / res - 1/2: grid coordinate g = p / res + b
     float mx, my, mz;             // n - 1 (clamp bound)
     float2 inv_res_pk, bxy;       // (inv_res, inv_res) and (bx, by), for packed operations
+    float res;                    // voxel size: p = (g - b) res
+    float2 mbxy;                  // -(bx, by) res
+    float mbz;                    // -bz res
     unsigned *err;                // bounds-checked builds: the context's violation word (else null)
 };
 
@@ -434,6 +443,13 @@ __device__ __forceinline__ void dh_step(Frame &F, float ca, float sa, float a, f
     F.c2 = y2;
     F.c3 = x3;
     F.t = axpy(d, x3, F.t);                         // TransZ(d)
+}
+
+// A point in grid units, in metres: (g - b) res.
+__device__ __forceinline__ f3 grid_to_metres(const GridConst &g, f3 p)
+{
+    const float2 xy = __ffma2_rn(make_float2(p.x, p.y), make_float2(g.res, g.res), g.mbxy);
+    return mk(xy.x, xy.y, fmaf(p.z, g.res, g.mbz));
 }
 
 // Point o given in frame F, in world coordinates: R o + t.

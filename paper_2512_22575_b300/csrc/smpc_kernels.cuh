@@ -131,14 +131,15 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         // (wg0 = link_wg[j][0], loaded with th0)
         const float2 ww = rc.fk_ww[j];
         const f3 gv = axpy(ww.y, F.c3, axpy(ww.x, F.c2, scale(wg0, F.c1)));
-        const float2 gtxy = __ffma2_rn(make_float2(F.t.x, F.t.y), g.inv_res_pk, g.bxy);
-        const f3 gt = mk(gtxy.x, gtxy.y, fmaf(F.t.z, g.inv_res, g.bz));
-        f3 v{};
+        const f3 gt = F.t;          // the chain runs in grid units
+        f3 v{}, tm{};
         if (SELF && sp) {
+            // the self term works in metres: the origin converted, v = R w
+            tm = grid_to_metres(g, F.t);
             v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
             if (rc.self_frames && pm_ok(kSelfFrameSlots * j + 5 < self_slots(rc.n_spheres, true), kErrSelf, g)) {
                 float *fs = sp + kSelfFrameSlots * j * 32;
-                fs[0] = F.t.x; fs[32] = F.t.y; fs[64] = F.t.z;
+                fs[0] = tm.x; fs[32] = tm.y; fs[64] = tm.z;
                 fs[96] = v.x; fs[128] = v.y; fs[160] = v.z;
             }
         }
@@ -152,7 +153,7 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                 const float lam = ls[i].x;
                 if (SELF && sp && !rc.self_frames && i < e - s0 &&
                     pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {   // kept for the self term
-                    const f3 p = axpy(lam, v, F.t);
+                    const f3 p = axpy(lam, v, tm);
                     sp[(3 * s) * 32] = p.x;
                     sp[(3 * s + 1) * 32] = p.y;
                     sp[(3 * s + 2) * 32] = p.z;
@@ -185,15 +186,16 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
 #pragma unroll
         for (int i = 0; i < kSphereBatch; ++i) {
             const int s = s0 + i;               // past e: zero padding, masked below
-            const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
+            // grid coordinates of the centre (the chain runs in grid units)
+            const f3 p = frame_point(F, rc.sph_off_g[s][0], rc.sph_off_g[s][1], rc.sph_off_g[s][2]);
             if (SELF && sp && !rc.self_frames && i < e - s0 &&
                 pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {   // kept for the self term
-                sp[(3 * s) * 32] = p.x;
-                sp[(3 * s + 1) * 32] = p.y;
-                sp[(3 * s + 2) * 32] = p.z;
+                const f3 pm = grid_to_metres(g, p);
+                sp[(3 * s) * 32] = pm.x;
+                sp[(3 * s + 1) * 32] = pm.y;
+                sp[(3 * s + 2) * 32] = pm.z;
             }
-            mn[i] = tex3D<float>(g.cmin_tex, fmaf(p.x, g.inv_res, g.bx), fmaf(p.y, g.inv_res, g.by),
-                                 fmaf(p.z, g.inv_res, g.bz));
+            mn[i] = tex3D<float>(g.cmin_tex, p.x, p.y, p.z);
         }
         if (batch_may_gather(mn, rc.sph_ls[s0].y, rc.sph_ls[s0 + 1].y, rc.sph_ls[s0 + 2].y, rc.sph_ls[s0 + 3].y))
 #pragma unroll
@@ -202,7 +204,8 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             if (i < e - s0 && !(mn[i] > rc.sph_ls[s].y)) {
                 // the few spheres near an obstacle: locate again with fractions
                 ngath += count ? 1u : 0u;
-                const Cell c = locate(g, frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]));
+                const f3 p = frame_point(F, rc.sph_off_g[s][0], rc.sph_off_g[s][1], rc.sph_off_g[s][2]);
+                const Cell c = locate_grid(g, p.x, p.y, p.z);
                 float v[8];
                 corners<GT>(g, c.base, v);
                 const float phi = interpolate(v, c.fx, c.fy, c.fz);
@@ -394,7 +397,9 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         lqd = fmaf(b, b, lqd2.x + lqd2.y);
         ns = fmaf(e, e, ns2.x + ns2.y);
     }
+    // the chain in grid units: the base at the world origin's grid coordinate
     Frame F = base_frame();
+    F.t = mk(g.bx, g.by, g.bz);
     float env = 0.f;
     // Not unrolled: the kernel's code then fits the instruction cache, which
     // outweighs the indexed constant loads this costs.  With QMEM the joint
@@ -418,14 +423,15 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         env += link_env<GT, SELF>(rc, g, F, j, be.x, be.y, tw.y, !terminal, ngath, sp);
         if (SELF && sp && !rc.self_frames &&
             pm_ok(3 * rc.n_spheres + 3 * j + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {
-            const f3 c = frame_point(F, rc.link_c[j][0], rc.link_c[j][1], rc.link_c[j][2]);
+            const f3 c = grid_to_metres(g, frame_point(F, rc.link_c[j][0] * g.inv_res, rc.link_c[j][1] * g.inv_res,
+                                                       rc.link_c[j][2] * g.inv_res));
             const int t = 3 * rc.n_spheres + 3 * j;
             sp[t * 32] = c.x;
             sp[(t + 1) * 32] = c.y;
             sp[(t + 2) * 32] = c.z;
         }
     }
-    const f3 tee = axpy(rc.flange_d, F.c3, F.t);
+    const f3 tee = grid_to_metres(g, axpy(rc.flange_dg, F.c3, F.t));
     float xi[6];
     pose_error(st.Rg, st.tg, F.c1, F.c2, F.c3, tee, xi);
     if (terminal) {
