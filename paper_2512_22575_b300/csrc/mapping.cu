@@ -369,7 +369,7 @@ __global__ void sphere_world_kernel(const RobotConst rc, const float *q, float i
     int link = 0;
     while (link < kNJ && rc.link_begin[link + 2] <= s) ++link;   // sphere s lies on frame link + 1
     Frame F = base_frame();
-    for (int j = 0; j <= link; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j], rc.sincos_pk);
+    for (int j = 0; j <= link; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], q[j] + rc.th0[j], rc.poly);
     const f3 p = frame_point(F, rc.sph_off[s][0], rc.sph_off[s][1], rc.sph_off[s][2]);
     out[s] = make_float4(p.x, p.y, p.z, rc.sph_r[s] + inflate);
 }

@@ -279,14 +279,13 @@ __global__ void pose_error_kernel(const float *Tg, const float *T, float *xi, si
 
 // joint_sincos with the coefficients as the kernels hold them (parameter
 // bank), beside CUDA's sincosf of the same argument for comparison
-struct SinCosPoly { float2 kc[4]; };
 
-__global__ void joint_sincos_kernel(const float *x, float *sc, float *sc_ref, size_t n, const __grid_constant__ SinCosPoly kp)
+__global__ void joint_sincos_kernel(const float *x, float *sc, float *sc_ref, size_t n, const __grid_constant__ PolyConst kp)
 {
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
         float s, c;
-        joint_sincos(x[i], s, c, kp.kc);
+        joint_sincos(x[i], s, c, kp);
         sc[2 * i] = s;
         sc[2 * i + 1] = c;
         if (sc_ref) {
@@ -300,14 +299,14 @@ __global__ void joint_sincos_kernel(const float *x, float *sc, float *sc_ref, si
 struct Sigma { float s[8]; };
 
 __global__ void sample_noise_kernel(int K, int H, Sigma sg, uint32_t s_lo, uint32_t s_hi,
-                                    uint32_t iter, float *eps, const __grid_constant__ SinCosPoly kp)
+                                    uint32_t iter, float *eps, const __grid_constant__ PolyConst kp)
 {
     const size_t total = static_cast<size_t>(K) * H;
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const uint32_t m = static_cast<uint32_t>(i / H), k = static_cast<uint32_t>(i % H);
         float z[8];
-        step_normals(s_lo, s_hi, iter, m, k, z, kp.kc);
+        step_normals(s_lo, s_hi, iter, m, k, z, kp);
         for (int j = 0; j < kNJ; ++j) eps[i * kNJ + j] = sg.s[j] * z[j];
     }
 }
@@ -381,7 +380,7 @@ __global__ void episode_step_kernel(const RobotConst rc, const float *Tg, float 
     __syncthreads();
     if (threadIdx.x == 0) {
         Frame F = base_frame();
-        for (int j = 0; j < kNJ; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], s_q[j] + rc.th0[j], rc.sincos_pk);
+        for (int j = 0; j < kNJ; ++j) dh_step(F, rc.ca[j], rc.sa[j], rc.a[j], rc.d[j], s_q[j] + rc.th0[j], rc.poly);
         const f3 t = axpy(rc.flange_d, F.c3, F.t);
         const f3 e = sub(t, mk(Tg[3], Tg[7], Tg[11]));
         // R_d = R_g^T R: entries from the goal's columns and the frame's columns
@@ -964,7 +963,7 @@ pm_status pm_create(const pm_robot *rb, const pm_grid_desc *gd, const pm_cost_pa
         r.qdd_hi[j] = static_cast<float>(acc - mf * 2.0 * acc);
         r.q_ref[j] = cp->q_ref[j];
     }
-    for (int i = 0; i < 4; ++i) r.sincos_pk[i] = kSinCosPoly[i];
+    r.poly = poly_const();
     r.flange_dg = static_cast<float>(static_cast<double>(rb->flange_d) / static_cast<double>(gd->res));
     for (int i = 0; i < kMaxSpheres + kSpherePad; ++i)
         for (int k = 0; k < 3; ++k) r.sph_off_g[i][k] = static_cast<float>(r.sph_off[i][k] / static_cast<double>(gd->res));
@@ -1518,8 +1517,7 @@ pm_status pm_joint_sincos(const float *x, float *sc, float *sc_ref, size_t n, vo
     if (n == 0) return PM_OK;
     if (!is_device_ptr(x) || !is_device_ptr(sc) || (sc_ref && !is_device_ptr(sc_ref)))
         return set_err(nullptr, PM_EINVAL, "x/sc/sc_ref must be device memory");
-    SinCosPoly kp;
-    for (int i = 0; i < 4; ++i) kp.kc[i] = kSinCosPoly[i];
+    const PolyConst kp = poly_const();
     const unsigned blocks = static_cast<unsigned>(std::min<size_t>((n + 127) / 128, 65535));
     joint_sincos_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, sc, sc_ref, n, kp);
     PM_CUDA(nullptr, cudaGetLastError());
@@ -1537,8 +1535,7 @@ pm_status pm_sample_noise(int K, int H, const float *sigma, uint64_t seed, uint3
     for (int j = 0; j < kNJ; ++j) sg.s[j] = sigma[j];
     const size_t total = static_cast<size_t>(K) * H;
     const unsigned blocks = static_cast<unsigned>(std::min<size_t>((total + 255) / 256, 65535));
-    SinCosPoly kp;
-    for (int i = 0; i < 4; ++i) kp.kc[i] = kSinCosPoly[i];
+    const PolyConst kp = poly_const();
     sample_noise_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
         K, H, sg, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), iter_index, eps, kp);
     PM_CUDA(nullptr, cudaGetLastError());

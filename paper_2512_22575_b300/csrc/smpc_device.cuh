@@ -29,6 +29,15 @@ constexpr int kMaxSelfGroups = (kNJ * (kNJ + 1)) / 2;   // frame pairs (a <= b) 
 constexpr int kMaxSelfPairs = 4096;
 constexpr int kSelfDense = 4;        // spheres per frame of a dense self-collision group
 
+// Coefficients of the sin/cos and ln polynomials (gen_sincos_poly.py) as the
+// kernels read them, from their parameters: the (sin, cos) pairs are the
+// operands of packed FMAs, the ln coefficients the addends of scalar ones
+// (an FMA takes a constant-bank addend, not an immediate one).
+struct PolyConst {
+    float2 sc[4];                 // (sin, cos) pairs, highest degree first
+    float ln[4];                  // the atanh bracket, lowest degree first
+};
+
 // Arm + cost constants, passed by value as a kernel parameter (constant bank).
 struct RobotConst {
     int n_spheres;
@@ -73,9 +82,7 @@ struct RobotConst {
     float grp_thr2[kMaxSelfGroups];
     float link_c[kNJ][3];         // bounding-sphere centre of frame j+1's spheres, in that frame
     float link_w2[kNJ];           // |link_w|^2 (the rotated direction's squared length)
-    // coefficient pairs (sin, cos) of joint_sincos's Horner steps, highest
-    // degree first (operands of packed FP32 FMAs, read from the parameter bank)
-    float2 sincos_pk[4];
+    PolyConst poly;               // the sin/cos and ln coefficients
     // the forward kinematics' per-joint constants in 8-byte pairs (one
     // constant load each): (ca, sa), (a, d), (th0, link_wg[0]),
     // (link_wg[1], link_wg[2]) and the frame's spheres (link_begin[j+1],
@@ -227,13 +234,20 @@ __device__ __forceinline__ void grid_dependency_prologue()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// Coefficients of gen_sincos_poly.py (host copies; the kernels take the
-// sin/cos pairs from RobotConst::sincos_pk, the parameter bank):
+// Coefficients of gen_sincos_poly.py (host copies; the kernels take them
+// from RobotConst::poly, in the parameter bank):
 // (sin, cos) pairs, highest degree first, and the ln bracket, lowest first.
 constexpr float2 kSinCosPoly[4] = {{2.724328624e-06f, 2.445699101e-05f}, {-1.984003320e-04f, -1.388753648e-03f},
                                    {8.333331905e-03f, 4.166664928e-02f}, {-1.666666716e-01f, -5.0e-01f}};
 constexpr float kLnP0 = 3.333333433e-01f, kLnP1 = 2.000006735e-01f, kLnP2 = 1.427491456e-01f,
                 kLnP3 = 1.167523712e-01f;
+inline PolyConst poly_const()
+{
+    PolyConst p;
+    for (int i = 0; i < 4; ++i) p.sc[i] = kSinCosPoly[i];
+    p.ln[0] = kLnP0; p.ln[1] = kLnP1; p.ln[2] = kLnP2; p.ln[3] = kLnP3;
+    return p;
+}
 constexpr float kRound = 12582912.0f;                  // 1.5 2^23: x + kRound rounds x to an integer
 
 // sin and cos of (pi/2) n + r, |r| <= 1.01 pi/4, given r and the bits qb of
@@ -241,13 +255,13 @@ constexpr float kRound = 12582912.0f;                  // 1.5 2^23: x + kRound r
 // polynomials of gen_sincos_poly.py (least-squares fits on Chebyshev nodes,
 // within 0.9 ulp in float32 evaluation), their Horner steps paired in packed
 // FP32 FMAs, then the quadrant applied by a swap and two sign flips.
-__device__ __forceinline__ void sincos_quadrant(float r, unsigned qb, const float2 (&kc)[4], float &s, float &c)
+__device__ __forceinline__ void sincos_quadrant(float r, unsigned qb, const PolyConst &pc, float &s, float &c)
 {
     const float z = r * r;
     const float2 zz = make_float2(z, z);
-    float2 p = __ffma2_rn(zz, kc[0], kc[1]);
-    p = __ffma2_rn(zz, p, kc[2]);
-    p = __ffma2_rn(zz, p, kc[3]);
+    float2 p = __ffma2_rn(zz, pc.sc[0], pc.sc[1]);
+    p = __ffma2_rn(zz, p, pc.sc[2]);
+    p = __ffma2_rn(zz, p, pc.sc[3]);
     const float sr = fmaf(r * z, p.x, r);
     const float cr = fmaf(z, p.y, 1.0f);
     const bool odd = (qb & 1u) != 0u;
@@ -262,7 +276,7 @@ __device__ __forceinline__ void sincos_quadrant(float r, unsigned qb, const floa
 // three float32 parts; with FMA the first step is exact (x - n p1 is a
 // multiple of 2^-24 below 1 in magnitude).  Then sincos_quadrant.  Within 2
 // ulps for |x| <= 64 and 2^-23 absolute up to 1e4; NaN for non-finite x.
-__device__ __forceinline__ void joint_sincos(float x, float &s, float &c, const float2 (&kc)[4])
+__device__ __forceinline__ void joint_sincos(float x, float &s, float &c, const PolyConst &kc)
 {
     constexpr float kTwoOverPi = 0.636619772367581343f;
     constexpr float kPio2Hi = 1.57079637050628662f;        // float32(pi/2)
@@ -333,7 +347,7 @@ __device__ __forceinline__ float word_to_uniform(uint32_t x)
 // s = (m - 1)/(m + 1) = f/(2 + f), f = m - 1 exact, |s| <= 0.172, by
 // 2s (1 + s^2 P(s^2)), P the fit of gen_sincos_poly.py; e ln 2 in two
 // float32 parts.  Within 2 ulps (1.6 in emulation, plus the quotient's).
-__device__ __forceinline__ float ln_unit(float u)
+__device__ __forceinline__ float ln_unit(float u, const PolyConst &pc)
 {
     constexpr float kLn2Hi = 0.693147182464599609f;        // float32(ln 2)
     constexpr float kLn2Lo = -1.9046542121259336e-09f;     // float32(ln 2 - kLn2Hi)
@@ -343,9 +357,9 @@ __device__ __forceinline__ float ln_unit(float u)
     const float f = m - 1.0f;
     const float sq = __fdividef(f, 2.0f + f);               // 2 + f in [1.7, 2.5]: no special cases
     const float z = sq * sq;
-    float p = fmaf(z, kLnP3, kLnP2);
-    p = fmaf(z, p, kLnP1);
-    p = fmaf(z, p, kLnP0);
+    float p = fmaf(z, pc.ln[3], pc.ln[2]);
+    p = fmaf(z, p, pc.ln[1]);
+    p = fmaf(z, p, pc.ln[0]);
     const float s2 = sq + sq;
     const float ef = static_cast<float>(e);
     return fmaf(ef, kLn2Hi, fmaf(ef, kLn2Lo, fmaf(s2 * z, p, s2)));
@@ -355,13 +369,13 @@ __device__ __forceinline__ float ln_unit(float u)
 // angle 2 pi u1 = (pi/2) t with t = 4 u1 in (0, 4) exact, so the reduction
 // is exact too (n = rint(t), f = t - n in [-1/2, 1/2]) and the angle's
 // sin and cos come from sincos_quadrant at r = (pi/2) f.
-__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1, const float2 (&kc)[4])
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1, const PolyConst &kc)
 {
     constexpr float kPio2 = 1.57079637050628662f;
     const float u0 = word_to_uniform(w0);
     // v = -2 ln u0 lies in [1.2e-7, 33.3] (u0 in [2^-24, 1 - 2^-24]), so
     // v rsqrt(v) needs no special cases: within 3 ulp of sqrt(v)
-    const float v = -2.0f * ln_unit(u0);
+    const float v = -2.0f * ln_unit(u0, kc);
     const float r = v * rsqrtf(v);
     // t = 4 u1 = 4 ((i + 1/2) 2^-23) = i 2^-21 + 2^-22
     const float t = fmaf(static_cast<float>(w1 >> 9), 4.76837158203125e-7f, 2.384185791015625e-7f);
@@ -373,10 +387,10 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, 
 }
 
 // Standard normals z[0..7] of roll-out m, step k (counter (m, k, b, iter)).
-// kc: the sin/cos coefficient pairs (RobotConst::sincos_pk or kSinCosPoly);
+// kc: the polynomial coefficients (RobotConst::poly, or a diagnostic's copy);
 // rk: the key's round keys (philox_round_keys), or null to derive them.
 __device__ __forceinline__ void step_normals(uint32_t seed_lo, uint32_t seed_hi, uint32_t iter,
-                                             uint32_t m, uint32_t k, float z[8], const float2 (&kc)[4],
+                                             uint32_t m, uint32_t k, float z[8], const PolyConst &kc,
                                              const uint2 (*rk)[10] = nullptr)
 {
 #pragma unroll
@@ -427,10 +441,9 @@ __device__ __forceinline__ Frame base_frame()
 }
 
 // T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d)  (modified DH, Eq. 6).
-// kc: joint_sincos's coefficients as the kernel holds them (RobotConst::
-// sincos_pk, in the parameter bank, so the packed FMAs read them in place).
+// kc: the polynomial coefficients as the kernel holds them (RobotConst::poly).
 __device__ __forceinline__ void dh_step(Frame &F, float ca, float sa, float a, float d, float theta,
-                                        const float2 (&kc)[4])
+                                        const PolyConst &kc)
 {
     F.t = axpy(a, F.c1, F.t);                       // TransX(a); RotX keeps the x axis
     const f3 x2 = axpy(sa, F.c3, scale(ca, F.c2));  // RotX(alpha): y' = ca y + sa z

@@ -414,7 +414,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
 #pragma unroll 1
     for (int j = 0; j < kNJ; ++j) {
         const float2 cs = rc.fk_cs[j], ad = rc.fk_ad[j], tw = rc.fk_tw[j];
-        dh_step(F, cs.x, cs.y, ad.x, ad.y, (QMEM ? qa[j * qstride] : qr[0]) + tw.x, rc.sincos_pk);
+        dh_step(F, cs.x, cs.y, ad.x, ad.y, (QMEM ? qa[j * qstride] : qr[0]) + tw.x, rc.poly);
         if (!QMEM) {
 #pragma unroll
             for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
@@ -612,7 +612,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             const bool live = active && k < H;
             if (live) {
                 step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
-                             static_cast<uint32_t>(k), z, rc.sincos_pk, DYN ? nullptr : job.rk);
+                             static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
             }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
@@ -778,14 +778,23 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             if (extra) {
                 ngath = ng0;        // lookups of the roll-outs only
                 *job.c0 = sc;
+            } else if (STAGE) {
+                lsum = cc + sc;         // one step per lane: nothing to compensate yet
             } else {
                 kahan_add(lsum, lcomp, cc + sc);
             }
         }
 
-        // S'^(m): compensated sum over the segment's lanes
+        // S'^(m): compensated sum over the segment's lanes (one step per
+        // lane: the first level starts without an error term)
         float ssum = lsum, serr = -lcomp;
-        for (int off = L / 2; off > 0; off >>= 1) {
+        int off0 = L / 2;
+        if (STAGE && off0 > 0) {
+            const float os = __shfl_xor_sync(0xffffffffu, ssum, off0);
+            two_sum(ssum, os, ssum, serr);
+            off0 >>= 1;
+        }
+        for (int off = off0; off > 0; off >>= 1) {
             const float os = __shfl_xor_sync(0xffffffffu, ssum, off);
             const float oe = __shfl_xor_sync(0xffffffffu, serr, off);
             float ns, e;
