@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     extern __shared__ float s_dyn[];
     __shared__ RobotConst s_rc;
     __shared__ BatchInstance s_inst;
-    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
+    __shared__ __align__(16) float s_tot[kWarps / 2 + 1][2 * kNJ];
     __shared__ float s_S[kWarps / 2 + 1][2][2];
     __shared__ float s_state[kStateFloats];
     __shared__ float s_blk[kBatchMaxSteps * kNJ];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
     extern __shared__ float s_dyn[];
     __shared__ RobotConst s_rc;
     __shared__ BatchInstance s_inst;
-    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
+    __shared__ __align__(16) float s_tot[kWarps / 2 + 1][2 * kNJ];
     __shared__ float s_S[kWarps / 2 + 1][2][2];
     __shared__ float s_state[kStateFloats];
     __shared__ float s_blk[kBatchC1Steps * kNJ];

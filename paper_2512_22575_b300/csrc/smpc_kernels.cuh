@@ -539,7 +539,7 @@ template <bool DYN> __device__ __forceinline__ float job_inv_lambda(const TileJo
 // Shared-memory arrays a block needs for run_block.
 struct BlockSmem {
     float *eps, *acc;           // [kWarps][C][7][32] each
-    float (*tot)[2 * kNJ];      // [kWarps/2 + 1] pair scan totals
+    float (*tot)[2 * kNJ];      // [kWarps/2 + 1] pair scan totals, (A_j, B_j) pairs (8-byte aligned rows)
     float (*S)[2][2];           // [kWarps/2 + 1] pair partial costs
     float *blk;                 // [C*L*P*7] block accumulator
     float *wm, *wz;             // [kWarps]
@@ -610,17 +610,21 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             const int k = kbase + sl * C + s;
             float z[8];
             const bool live = active && k < H;
-            if (live) {
-                step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
-                             static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
-            }
+            // Steps past the horizon, and roll-outs past K, are sampled too
+            // (from the last row of Ubar): in the scans a lane's values reach
+            // only its own later steps and higher lanes, which are past the
+            // horizon as well, and no result of theirs is kept.  Sampling
+            // them saves the selects a branch-free zeroing would cost.
+            const int kc = min(k, H - 1);
+            step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
+                         static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                float e = live ? st.sigma[j] * z[j] : 0.f;
+                float e = st.sigma[j] * z[j];
                 // precision variant: eps rounded as if stored in FP16 / BF16
                 if (job.noise_dtype == 1) e = __half2float(__float2half_rn(e));
                 else if (job.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
-                const float u = live ? __ldg(job.Ubar + pm_idx(k * kNJ + j, H * kNJ, kErrUbar, g)) + e : 0.f;
+                const float u = __ldg(job.Ubar + pm_idx(kc * kNJ + j, H * kNJ, kErrUbar, g)) + e;
                 sm.eps[E(warp, s, j)] = e;
                 T[j] += u;
                 TB[j] += T[j];
@@ -644,21 +648,20 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             seg_inclusive_scan(T, A0, sl, L);
             seg_inclusive_scan(A0, B0, sl, L);
             if (P == 2) {
-                // the first half's A_32, B_32 shift the second half's:
-                // A += A_32, B += B_32 + (sl + 1) A_32
+                // the first half's A_32, B_32 (lane 31's inclusive values)
+                // shift the second half's: A += A_32, B += B_32 + (sl + 1) A_32
+                float2 *tot = reinterpret_cast<float2 *>(sm.tot[pr]);   // (A_j, B_j) pairs
+                if (half == 0 && lane == 31) {
 #pragma unroll
-                for (int j = 0; j < kNJ; ++j) {
-                    const float At = __shfl_sync(0xffffffffu, A0[j], 31);
-                    const float Bt = __shfl_sync(0xffffffffu, B0[j], 31);
-                    if (half == 0 && lane == 0) { sm.tot[pr][j] = At; sm.tot[pr][kNJ + j] = Bt; }
+                    for (int j = 0; j < kNJ; ++j) tot[j] = make_float2(A0[j], B0[j]);
                 }
                 pair_barrier(pr);
                 if (half == 1) {
 #pragma unroll
                     for (int j = 0; j < kNJ; ++j) {
-                        const float a0 = sm.tot[pr][j], b0 = sm.tot[pr][kNJ + j];
-                        B0[j] += fmaf(static_cast<float>(sl + 1), a0, b0);
-                        A0[j] += a0;
+                        const float2 ab = tot[j];
+                        B0[j] += fmaf(static_cast<float>(sl + 1), ab.x, ab.y);
+                        A0[j] += ab.x;
                     }
                 }
             }
@@ -670,19 +673,18 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         if (P == 2) {
             // A_{32C} and B_{32C} of the first half shift the second half's scans:
             // A0 += A_{32C}, B0 += B_{32C} + (k0 - 32C) A_{32C}
+            float2 *tot = reinterpret_cast<float2 *>(sm.tot[pr]);       // (A_j, B_j) pairs
+            if (half == 0 && lane == 31) {
 #pragma unroll
-            for (int j = 0; j < kNJ; ++j) {
-                const float At = __shfl_sync(0xffffffffu, A0[j] + T[j], 31);
-                const float Bt = __shfl_sync(0xffffffffu, B0[j] + TB[j], 31);
-                if (half == 0 && lane == 0) { sm.tot[pr][j] = At; sm.tot[pr][kNJ + j] = Bt; }
+                for (int j = 0; j < kNJ; ++j) tot[j] = make_float2(A0[j] + T[j], B0[j] + TB[j]);
             }
             pair_barrier(pr);
             if (half == 1) {
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) {
-                    const float a0 = sm.tot[pr][j], b0 = sm.tot[pr][kNJ + j];
-                    B0[j] += fmaf(static_cast<float>(sl * C), a0, b0);
-                    A0[j] += a0;
+                    const float2 ab = tot[j];
+                    B0[j] += fmaf(static_cast<float>(sl * C), ab.x, ab.y);
+                    A0[j] += ab.x;
                 }
             }
         }
@@ -910,7 +912,7 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     static_assert(P == 1 || (P == 2 && L == 32 && kWarps % 2 == 0), "pair tiles are whole warps");
     static_assert(kBlock >= 44, "state loader needs 44 threads");
     extern __shared__ float s_dyn[];
-    __shared__ float s_tot[kWarps / 2 + 1][2 * kNJ];
+    __shared__ __align__(16) float s_tot[kWarps / 2 + 1][2 * kNJ];
     __shared__ float s_S[kWarps / 2 + 1][2][2];
     __shared__ float s_state[kStateFloats];
     // block accumulator [k][j], k < C*L*P (>= H, host-checked); with the
