@@ -361,21 +361,11 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
     return rc.w_self * acc;
 }
 
-// State terms at a step (Eqs. 16, 19-20, 22, 24), or the terminal cost (Eq. 25).
-// Forward kinematics runs frame by frame; the spheres of each frame are
-// looked up as soon as it is known.
-template <typename GT, bool TRACE, bool SELF, bool QMEM = false>
-__device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
-                                            const InstanceState &st, const float *q,
-                                            const float *qd, bool terminal, float *tr,
-                                            unsigned &ngath, float *sp, const float *qa = nullptr,
-                                            int qstride = 1)
+// The joint-limit and null-space sums of a state (Eqs. 21, 24; weights not
+// applied): lq = sum delta(q)^2, lqd = sum delta(qd)^2, ns = sum (q - q_ref)^2.
+__device__ __forceinline__ void state_limits(const RobotConst &rc, const float *q, const float *qd, float &lq,
+                                             float &lqd, float &ns)
 {
-    if (!SELF || terminal) sp = nullptr;
-    // The terminal step (one lane in H) runs the step's terms too and drops
-    // them at the end: the lanes of a warp run together, and a branch around
-    // them would cost every lane its instructions.
-    float lq = 0.f, lqd = 0.f, ns = 0.f;
     {
         // joints in pairs through the packed FP32 units, the last one alone
         float2 lq2 = make_float2(0.f, 0.f), lqd2 = make_float2(0.f, 0.f), ns2 = make_float2(0.f, 0.f);
@@ -397,6 +387,34 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
         lqd = fmaf(b, b, lqd2.x + lqd2.y);
         ns = fmaf(e, e, ns2.x + ns2.y);
     }
+}
+
+// The weighted state-limit terms of a step: w_q lq + w_qd lqd + w_ns ns.
+__device__ __forceinline__ float state_limit_cost(const RobotConst &rc, const float *q, const float *qd)
+{
+    float lq, lqd, ns;
+    state_limits(rc, q, qd, lq, lqd, ns);
+    return fmaf(rc.w_q, lq, fmaf(rc.w_qd, lqd, rc.w_ns * ns));
+}
+
+// State terms at a step (Eqs. 16, 19-20, 22, 24), or the terminal cost (Eq. 25).
+// Forward kinematics runs frame by frame; the spheres of each frame are
+// looked up as soon as it is known.  LIM = false: the step's limit and
+// null-space terms were evaluated where its state was staged (q and qd
+// are not read).
+template <typename GT, bool TRACE, bool SELF, bool QMEM = false, bool LIM = true>
+__device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
+                                            const InstanceState &st, const float *q,
+                                            const float *qd, bool terminal, float *tr,
+                                            unsigned &ngath, float *sp, const float *qa = nullptr,
+                                            int qstride = 1)
+{
+    if (!SELF || terminal) sp = nullptr;
+    // The terminal step (one lane in H) runs the step's terms too and drops
+    // them at the end: the lanes of a warp run together, and a branch around
+    // them would cost every lane its instructions.
+    float lq = 0.f, lqd = 0.f, ns = 0.f;
+    if (LIM) state_limits(rc, q, qd, lq, lqd, ns);
     // the chain in grid units: the base at the world origin's grid coordinate
     Frame F = base_frame();
     F.t = mk(g.bx, g.by, g.bz);
@@ -605,6 +623,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
         float T[kNJ], TB[kNJ];
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) { T[j] = -0.f; TB[j] = -0.f; }
+        float ccost = 0.f;          // STAGE: the lane's control terms
 #pragma unroll 1
         for (int s = 0; s < C; ++s) {
             const int k = kbase + sl * C + s;
@@ -616,6 +635,11 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             // horizon as well, and no result of theirs is kept.  Sampling
             // them saves the selects a branch-free zeroing would cost.
             const int kc = min(k, H - 1);
+            // the step's row of Ubar, loaded before the sampling arithmetic
+            // so that its latency is hidden behind it
+            float ub[kNJ];
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) ub[j] = __ldg(job.Ubar + pm_idx(kc * kNJ + j, H * kNJ, kErrUbar, g));
             step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
                          static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
 #pragma unroll
@@ -624,7 +648,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 // precision variant: eps rounded as if stored in FP16 / BF16
                 if (job.noise_dtype == 1) e = __half2float(__float2half_rn(e));
                 else if (job.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
-                const float u = __ldg(job.Ubar + pm_idx(kc * kNJ + j, H * kNJ, kErrUbar, g)) + e;
+                const float u = ub[j] + e;
                 sm.eps[E(warp, s, j)] = e;
                 T[j] += u;
                 TB[j] += T[j];
@@ -635,8 +659,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 float *tr_u = TRACE ? trace + pm_idx(static_cast<long long>(m) * (H + 1) + k,
                                                     static_cast<long long>(job.K) * (H + 1), kErrTrace, g) * kTraceCols
                                    : nullptr;
-                sm.qs[pm_idx((warp * kStageFloats + 2 * kNJ) * 32, kWarps * kStageFloats * 32 - 31, kErrStage, g) + lane] =
-                    control_cost<TRACE>(rc, T, tr_u);
+                ccost = control_cost<TRACE>(rc, T, tr_u);
             }
         }
 
@@ -711,6 +734,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 const float kp_dt = static_cast<float>(k + 1) * dt;
                 // joints in pairs through the packed FP32 units, the last one alone
                 const float2 dtp = make_float2(dt, dt), dt2p = make_float2(dt2, dt2), kpp = make_float2(kp_dt, kp_dt);
+                float qn[kNJ], qdn[kNJ];    // q_{k+1}, qd_{k+1}
 #pragma unroll
                 for (int p = 0; p < kNJ / 2; ++p) {
                     const int j = 2 * p;
@@ -719,13 +743,24 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                     const float2 qq = __ffma2_rn(dt2p, make_float2(B0[j], B0[j + 1]),
                                                  __ffma2_rn(kpp, qd0, make_float2(st.q0[j], st.q0[j + 1])));
                     const float2 vv = __ffma2_rn(dtp, A, qd0);
-                    qs[j * 32] = qq.x; qs[(j + 1) * 32] = qq.y;
-                    qs[(kNJ + j) * 32] = vv.x; qs[(kNJ + j + 1) * 32] = vv.y;
+                    qn[j] = qq.x; qn[j + 1] = qq.y;
+                    qdn[j] = vv.x; qdn[j + 1] = vv.y;
                 }
                 {
                     constexpr int j = kNJ - 1;
-                    qs[j * 32] = fmaf(dt2, B0[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
-                    qs[(kNJ + j) * 32] = fmaf(dt, A0[j], st.qd0[j]);
+                    qn[j] = fmaf(dt2, B0[j], fmaf(kp_dt, st.qd0[j], st.q0[j]));
+                    qdn[j] = fmaf(dt, A0[j], st.qd0[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j) qs[j * 32] = qn[j];
+                if (TRACE) {
+#pragma unroll
+                    for (int j = 0; j < kNJ; ++j) qs[(kNJ + j) * 32] = qdn[j];
+                    qs[(2 * kNJ) * 32] = ccost;
+                } else {
+                    // the state's limit and null-space terms here, with the
+                    // state in registers (none at the terminal state, Eq. 25)
+                    qs[(2 * kNJ) * 32] = ccost + (k + 1 == H ? 0.f : state_limit_cost(rc, qn, qdn));
                 }
             }
         }
@@ -749,11 +784,15 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             if (extra) {
 #pragma unroll
                 for (int j = 0; j < kNJ; ++j) { q[j] = st.q0[j]; qd[j] = st.qd0[j]; }
+                // with STAGE the state terms below leave out the limits: add them
+                if (STAGE && !TRACE) cc = state_limit_cost(rc, q, qd);
             } else if (STAGE) {
                 const float *qs = sm.qs + pm_idx(((warp * C + s) * kStageFloats) * 32, kWarps * kStageFloats * 32 -
                                                  (kStageFloats - 1) * 32 - 31, kErrStage, g) + lane;
+                if (TRACE) {
 #pragma unroll
-                for (int j = 0; j < kNJ; ++j) { q[j] = qs[j * 32]; qd[j] = qs[(kNJ + j) * 32]; }
+                    for (int j = 0; j < kNJ; ++j) { q[j] = qs[j * 32]; qd[j] = qs[(kNJ + j) * 32]; }
+                }
                 cc = qs[(2 * kNJ) * 32];
                 qa = qs;
                 qstride = 32;
@@ -775,11 +814,12 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
                 cc = control_cost<TRACE>(rc, u, tr_u);
             }
             const unsigned ng0 = ngath;
-            const float sc = state_cost<GT, TRACE, SELF, STAGE>(rc, g, st, q, qd, !extra && k + 1 == H, tr_x, ngath, sp,
-                                                                qa, qstride);
+            // staged one-step lanes carry their limit terms in cc (LIM = false)
+            const float sc = state_cost<GT, TRACE, SELF, STAGE, !STAGE || TRACE>(rc, g, st, q, qd, !extra && k + 1 == H,
+                                                                               tr_x, ngath, sp, qa, qstride);
             if (extra) {
                 ngath = ng0;        // lookups of the roll-outs only
-                *job.c0 = sc;
+                *job.c0 = sc + cc;
             } else if (STAGE) {
                 lsum = cc + sc;         // one step per lane: nothing to compensate yet
             } else {
