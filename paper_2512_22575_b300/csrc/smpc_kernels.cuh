@@ -642,12 +642,19 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             for (int j = 0; j < kNJ; ++j) ub[j] = __ldg(job.Ubar + pm_idx(kc * kNJ + j, H * kNJ, kErrUbar, g));
             step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
                          static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
+            float ev[kNJ];
+#pragma unroll
+            for (int j = 0; j < kNJ; ++j) ev[j] = st.sigma[j] * z[j];
+            if (job.noise_dtype != 0) {
+                // precision variant: eps rounded as if stored in FP16 / BF16
+#pragma unroll
+                for (int j = 0; j < kNJ; ++j)
+                    ev[j] = job.noise_dtype == 1 ? __half2float(__float2half_rn(ev[j]))
+                                                 : __bfloat162float(__float2bfloat16_rn(ev[j]));
+            }
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) {
-                float e = st.sigma[j] * z[j];
-                // precision variant: eps rounded as if stored in FP16 / BF16
-                if (job.noise_dtype == 1) e = __half2float(__float2half_rn(e));
-                else if (job.noise_dtype == 2) e = __bfloat162float(__float2bfloat16_rn(e));
+                const float e = ev[j];
                 const float u = ub[j] + e;
                 sm.eps[E(warp, s, j)] = e;
                 T[j] += u;
