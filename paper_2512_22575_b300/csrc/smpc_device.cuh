@@ -566,14 +566,20 @@ __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 
     const float nv = sqrtf(dot(vee, vee));
     const float cth = 0.5f * (r00 + r11 + r22 - 1.0f);   // cos(th)
     const float th = atan2f(0.5f * nv, cth);
-    f3 w;
-    if (th < 1e-4f) {
-        w = scale(0.5f + th * th * (1.0f / 12.0f), vee);
-    } else if (th < CUDART_PI_F - 0.05f) {
-        // nv = 2 sin th lies in [2e-4, 2] here: __fdividef (2 ulp) needs no
-        // special cases, and so does the quotient of c(th) below
-        w = scale(__fdividef(th, nv), vee);
-    } else {
+    // The small-angle series and the quotient forms (nv = 2 sin th lies in
+    // [2e-4, 2] where the quotients are used, so __fdividef, 2 ulp, needs no
+    // special cases) are both evaluated and selected, without a branch; only
+    // the rare near-pi regime branches.
+    //   w = k_w vee, k_w = th / nv, or 1/2 + th^2/12 below th = 1e-4;
+    //   v = V(th)^{-1} t_delta, c(th) = (1 - (th/2) cot(th/2)) / th^2 with
+    //   (th/2) cot(th/2) = th (1 + cos th) / (2 sin th) = th (1 + cth) / nv,
+    //   or 1/12 + th^2/720 below th = 1e-2.
+    const float th2 = th * th;
+    const float kw = th < 1e-4f ? 0.5f + th2 * (1.0f / 12.0f) : __fdividef(th, nv);
+    float cc = th < 1e-2f ? (1.0f / 12.0f) + th2 * (1.0f / 720.0f)
+                          : __fdividef(1.0f - __fdividef(th * (1.0f + cth), nv), th2);
+    f3 w = scale(kw, vee);
+    if (th >= CUDART_PI_F - 0.05f) {
         // Near pi: (R + R^T)/2 = cos(th) I + (1 - cos(th)) a a^T; take the axis
         // from the column with the largest diagonal, the sign from vee.
         const float inv = 1.0f / (1.0f - cth);
@@ -602,20 +608,10 @@ __device__ __forceinline__ void pose_error(const float *Rg, const float *tg, f3 
             sgn = big >= 0.0f ? 1.0f : -1.0f;
         }
         w = scale(sgn * th, ax);
-    }
-    // v = V(th)^{-1} t_delta, c(th) = (1 - (th/2) cot(th/2)) / th^2 with
-    // (th/2) cot(th/2) = th (1 + cos th) / (2 sin th) = th (1 + cth) / nv
-    // away from 0 and pi (nv = |vee| = 2 sin th)
-    float cc;
-    if (th < 1e-2f) {
-        cc = (1.0f / 12.0f) + th * th * (1.0f / 720.0f);
-    } else if (th < CUDART_PI_F - 0.05f) {
-        cc = __fdividef(1.0f - __fdividef(th * (1.0f + cth), nv), th * th);
-    } else {
         const float h = 0.5f * th;
         float sh, ch;
         sincosf(h, &sh, &ch);
-        cc = (1.0f - h * ch / sh) / (th * th);
+        cc = (1.0f - h * ch / sh) / th2;
     }
     const f3 wxt = cross(w, td);
     const f3 wwxt = cross(w, wxt);
