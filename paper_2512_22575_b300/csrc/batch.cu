@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     const int tid = threadIdx.x;
     grid_dependency_prologue();
 
+    int cur = -1;          // the instance whose descriptor, constants and state are in shared memory
     for (;;) {
         __syncthreads();   // the previous item is done with shared memory
         if (tid == 0) s_item = static_cast<int>(atomicAdd(ba.queue, 1u));
@@ -71,19 +72,24 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
         const int item = s_item;
         if (item >= ba.n_work) return;
         const int2 w = ba.work[item];
-        {
-            const int *src = reinterpret_cast<const int *>(ba.inst + w.x);
-            int *dst = reinterpret_cast<int *>(&s_inst);
-            for (int i = tid; i < static_cast<int>(sizeof(BatchInstance) / 4); i += kBlock) dst[i] = src[i];
+        // items come instance by instance, so a block's next item is mostly
+        // of the same instance: then its shared copies are kept
+        if (w.x != cur) {
+            {
+                const int *src = reinterpret_cast<const int *>(ba.inst + w.x);
+                int *dst = reinterpret_cast<int *>(&s_inst);
+                for (int i = tid; i < static_cast<int>(sizeof(BatchInstance) / 4); i += kBlock) dst[i] = src[i];
+            }
+            __syncthreads();
+            {
+                const int *src = reinterpret_cast<const int *>(s_inst.rc);
+                int *dst = reinterpret_cast<int *>(&s_rc);
+                for (int i = tid; i < static_cast<int>(sizeof(RobotConst) / 4); i += kBlock) dst[i] = __ldg(src + i);
+            }
+            load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
+            __syncthreads();
+            cur = w.x;
         }
-        __syncthreads();
-        {
-            const int *src = reinterpret_cast<const int *>(s_inst.rc);
-            int *dst = reinterpret_cast<int *>(&s_rc);
-            for (int i = tid; i < static_cast<int>(sizeof(RobotConst) / 4); i += kBlock) dst[i] = __ldg(src + i);
-        }
-        load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
-        __syncthreads();
         const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
         TileJob job = s_inst.job;
         job.iter += ba.it;
@@ -127,6 +133,7 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
     const int tid = threadIdx.x;
     grid_dependency_prologue();
 
+    int cur = -1;          // the instance whose descriptor, constants and state are in shared memory
     for (;;) {
         __syncthreads();   // the previous item is done with shared memory
         if (tid == 0) s_item = static_cast<int>(atomicAdd(ba.queue, 1u));
@@ -134,19 +141,24 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
         const int item = s_item;
         if (item >= ba.n_work) return;
         const int2 w = ba.work[item];
-        {
-            const int *src = reinterpret_cast<const int *>(ba.inst + w.x);
-            int *dst = reinterpret_cast<int *>(&s_inst);
-            for (int i = tid; i < static_cast<int>(sizeof(BatchInstance) / 4); i += kBlock) dst[i] = src[i];
+        // items come instance by instance, so a block's next item is mostly
+        // of the same instance: then its shared copies are kept
+        if (w.x != cur) {
+            {
+                const int *src = reinterpret_cast<const int *>(ba.inst + w.x);
+                int *dst = reinterpret_cast<int *>(&s_inst);
+                for (int i = tid; i < static_cast<int>(sizeof(BatchInstance) / 4); i += kBlock) dst[i] = src[i];
+            }
+            __syncthreads();
+            {
+                const int *src = reinterpret_cast<const int *>(s_inst.rc);
+                int *dst = reinterpret_cast<int *>(&s_rc);
+                for (int i = tid; i < static_cast<int>(sizeof(RobotConst) / 4); i += kBlock) dst[i] = __ldg(src + i);
+            }
+            load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
+            __syncthreads();
+            cur = w.x;
         }
-        __syncthreads();
-        {
-            const int *src = reinterpret_cast<const int *>(s_inst.rc);
-            int *dst = reinterpret_cast<int *>(&s_rc);
-            for (int i = tid; i < static_cast<int>(sizeof(RobotConst) / 4); i += kBlock) dst[i] = __ldg(src + i);
-        }
-        load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
-        __syncthreads();
         const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
         TileJob job = s_inst.job;
         job.iter += ba.it;
