@@ -260,21 +260,26 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
             const float D = dot(dl, dl), Da2 = 2.0f * dot(dl, va), Db2 = 2.0f * dot(dl, vb);
             const float Vab2 = -2.0f * dot(va, vb);
             const float wa2 = rc.link_w2[fa], wb2 = rc.link_w2[fb];
-            const int a_lo = rc.link_begin[fa + 1], a_hi = rc.link_begin[fa + 2];
+            const int a_lo = rc.link_begin[fa + 1], na = rc.link_begin[fa + 2] - a_lo;
             const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
-            // frame b's spheres in pairs (2h, 2h+1) for the packed FP32 units:
-            // lambda, Q_b and radius (past nb: the last sphere again, masked)
+            // The group as a full 4 x 4 block: past a frame's count, its last
+            // sphere again with a NaN radius, whose pair thresholds are NaN, so
+            // the contact tests below fail for them (no masks, no loop bounds).
+            // Frame b's spheres in pairs (2h, 2h+1) for the packed FP32 units.
             static_assert(kSelfDense == 4, "two pairs of frame-b spheres");
+            const float nan = __int_as_float(0x7fc00000);
             float2 lb[2], Qb[2], br[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int s0 = b_lo + min(2 * h, nb - 1), s1 = b_lo + min(2 * h + 1, nb - 1);
                 lb[h] = make_float2(rc.sph_ls[s0].x, rc.sph_ls[s1].x);
-                br[h] = make_float2(rc.sph_r[s0], rc.sph_r[s1]);
+                br[h] = make_float2(2 * h < nb ? rc.sph_r[s0] : nan, 2 * h + 1 < nb ? rc.sph_r[s1] : nan);
                 Qb[h] = __fmul2_rn(lb[h], __ffma2_rn(lb[h], make_float2(wb2, wb2), make_float2(-Db2, -Db2)));
             }
-            for (int a = a_lo; a < a_hi; ++a) {
-                const float la = rc.sph_ls[a].x, ra = rc.sph_r[a];
+#pragma unroll
+            for (int i = 0; i < kSelfDense; ++i) {
+                const int a = a_lo + min(i, na - 1);
+                const float la = rc.sph_ls[a].x, ra = i < na ? rc.sph_r[a] : nan;
                 const float Pa = fmaf(la, fmaf(la, wa2, Da2), D), ma = la * Vab2;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -284,11 +289,11 @@ __device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp
                     const float2 rs = __fadd2_rn(make_float2(ra, ra), br[h]);
                     const float2 t = __fadd2_ru(rs, make_float2(1e-5f, 1e-5f));
                     const float2 t2 = __fmul2_ru(t, t);
-                    if (2 * h < nb && d2.x <= t2.x) {
+                    if (d2.x <= t2.x) {
                         const float del = fmaxf(rs.x - pair_distance(d2.x), 0.f);
                         acc = fmaf(del, del, acc);
                     }
-                    if (2 * h + 1 < nb && d2.y <= t2.y) {
+                    if (d2.y <= t2.y) {
                         const float del = fmaxf(rs.y - pair_distance(d2.y), 0.f);
                         acc = fmaf(del, del, acc);
                     }
