@@ -788,8 +788,8 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_measured_fma": fma_peak, "frac_of_measured_fma": achieved / fma_peak,
-                "kernel": "smpc_iteration_kernel<C=1,L=32,P=2,float>, the 7-blocks-per-SM "
-                          "instantiation the launch picks for K=4096, H=64",
+                "kernel": "smpc_iteration_kernel<C=1,L=32,P=2,float> at K=4096, H=64 "
+                          "(72 registers, 7 blocks per SM)",
                 "gathered_fraction": gathers_per_launch / (K * (H - 1) * 28),
                 "kernel_ms_per_launch": avg_kernel_s * 1e3, "launches_timed": launches,
                 "kernel_timing": f"CUDA events around each iteration kernel on its stream, second timed "
