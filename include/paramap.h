@@ -36,7 +36,7 @@
  *    row-major float[H][n_joints]; poses are row-major float[16]
  *    homogeneous matrices; the distance field is float[nz][ny][nx]
  *    (x fastest).
- *  - This build compiles the kinematic chain for n_joints == 7.
+ *  - The library compiles the kinematic chain for n_joints == 7.
  */
 #ifndef PARAMAP_H
 #define PARAMAP_H

@@ -477,17 +477,17 @@ def test_cfg2_replan_equals_its_iterations(cfg2):
           f"{np.abs(u0 - u0o).max():.2e}, best {best[0]:.6g} vs {besto:.6g}")
 
 
-@pytest.mark.parametrize("scale", ["survey", "episode"])
+@pytest.mark.parametrize("scale", ["5x", "episode"])
 def test_parity_at_working_cost_scales(scale):
-    """The cfg1 scenes with the pose weights the planner works at: the
-    survey's Q = diag(1, 0.1), Q_H = diag(10, 1) (5x the parity weights) and
-    the episodes' 10x.  The per-roll-out costs must hold the 1e-4 relative
+    """The cfg1 scenes with the pose weights the planner works at: Q =
+    diag(1, 0.1), Q_H = diag(10, 1) (5x the parity weights) and the
+    episodes' 10x.  The per-roll-out costs must hold the 1e-4 relative
     bar and the FP64 update from the GPU's own costs must match the GPU U*
     within 1e-6 (the reduction is exact at this scale too).  The end-to-end
     U* error is reported beside its first-order bound sigma max|dS|/lambda:
     at these scales the soft-min (lambda = 0.05, S ~ 10-40) amplifies the
     FP32 rounding of S beyond 1e-5 on some scenes."""
-    f = {"survey": 5.0, "episode": 10.0}[scale]
+    f = {"5x": 5.0, "episode": 10.0}[scale]
     rows = []
     for seed in range(10):
         base = Scene(f"cfg1_seed{seed}")
