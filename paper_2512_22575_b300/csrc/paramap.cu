@@ -86,12 +86,13 @@ IterKernel lookup_dense_kernel(int dtype, TileShape s)
 
 // The iteration kernel of a call, its shared memory and resident blocks.
 // A one-step shape without tracing or the self term switches to its
-// kDenseBlocks instantiation when the extra units run the launch in fewer
-// rounds of tiles, and in at most two: a short launch is dominated by its
-// partly filled last round (K = 4096, H = 64: 3 rounds of 1776 units or 2
-// of 2072, replan 290 -> 280 us), a long one by the throughput per round,
-// where the 6-block kernel wins (K = 16384: 862 against 927 us per
-// replan).
+// kDenseBlocks instantiation when that holds more blocks per SM and the
+// extra units run the launch in fewer rounds of tiles, and in at most two:
+// a short launch is dominated by its partly filled last round, a long one
+// by the throughput per round.  (When the instantiations were fitted at 80
+// and 72 registers, K = 4096, H = 64 ran 3 rounds of 1776 units or 2 of
+// 2072, replan 290 -> 280 us, and K = 16384 862 against 927 us per replan;
+// both now hold 7 blocks per SM for that shape, and the default one runs.)
 struct KernelPick {
     IterKernel fn = nullptr;
     size_t smem = 0;

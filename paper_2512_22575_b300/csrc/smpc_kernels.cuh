@@ -950,11 +950,12 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
 // steps [0, 32C) and warp 2p+1 steps [32C, 64C); they exchange the scan
 // totals of the first half and their partial costs through shared memory.
 // MINB is the residency the registers are fitted to: 6 blocks per SM for
-// the one-step shapes without the self term (80 registers), 5 for the
-// others (96; with the self term the 80-register fit spills and runs
-// slower); the one-step shapes also have a kDenseBlocks instantiation (72
-// registers, no spills), which the host picks when its extra units save a
-// round of tiles on a short launch.
+// the one-step shapes without the self term (a budget of 80 registers; the
+// (1,32,2) kernel now needs 72 and holds 7), 5 for the others (96; with the
+// self term the 80-register fit spills and runs slower); the one-step
+// shapes also have a kDenseBlocks instantiation (72 registers, no spills),
+// which the host picks when its extra residency saves a round of tiles on
+// a short launch.
 template <int C, int L, int P, typename GT, bool TRACE, bool SELF, int MINB = (C == 1 && !SELF ? 6 : 5), bool DYN = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_constant__ GridConst g,
