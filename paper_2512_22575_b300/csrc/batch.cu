@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
     __shared__ float s_state[kStateFloats];
     __shared__ float s_blk[kBatchMaxSteps * kNJ];
     __shared__ float s_wm[kWarps], s_wz[kWarps];
+    __shared__ float4 s_grp[SELF ? kMaxSelfGroups * kSelfGroupRec : 1];
     __shared__ int s_item;
     const int tid = threadIdx.x;
     grid_dependency_prologue();
@@ -88,6 +89,10 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
             }
             load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
             __syncthreads();
+            if (SELF && s_rc.n_self_groups > 0 && s_rc.self_frames) {
+                build_self_groups(s_rc, s_inst.g, s_grp);
+                __syncthreads();
+            }
             cur = w.x;
         }
         const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(kBlock, 4) smpc_batch_kernel(const __grid_cons
         const int C = s_inst.C;
         BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
                      (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kBatchCMax * kNJ * 32 : nullptr,
-                     nullptr};
+                     nullptr, (SELF && s_rc.n_self_groups > 0 && s_rc.self_frames) ? s_grp : nullptr};
         unsigned ngath = 0;
         run_block<GT, false, SELF, false>(s_rc, s_inst.g, st, job, nullptr, C, s_inst.L, s_inst.P, w.y, sm, ngath);
     }
@@ -129,6 +134,7 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
     __shared__ float s_blk[kBatchC1Steps * kNJ];
     __shared__ float s_wm[kWarps], s_wz[kWarps];
     __shared__ float s_qs[kWarps * kStageFloats * 32];
+    __shared__ float4 s_grp[SELF ? kMaxSelfGroups * kSelfGroupRec : 1];
     __shared__ int s_item;
     const int tid = threadIdx.x;
     grid_dependency_prologue();
@@ -157,6 +163,10 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
             }
             load_state(s_inst.in, CallScalars{s_inst.job.seed_lo, s_inst.job.seed_hi, s_inst.job.iter, s_inst.job.dt, s_inst.job.inv_lambda}, s_state);
             __syncthreads();
+            if (SELF && s_rc.n_self_groups > 0 && s_rc.self_frames) {
+                build_self_groups(s_rc, s_inst.g, s_grp);
+                __syncthreads();
+            }
             cur = w.x;
         }
         const InstanceState &st = *reinterpret_cast<const InstanceState *>(s_state);
@@ -164,7 +174,8 @@ __global__ void __launch_bounds__(kBlock, MINB) smpc_batch_kernel_c1(const __gri
         job.iter += ba.it;
         job.c0 = s_inst.c0;
         BlockSmem sm{s_dyn, s_dyn + kWarps * kNJ * 32, s_tot, s_S, s_blk, s_wm, s_wz,
-                     (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kNJ * 32 : nullptr, s_qs};
+                     (SELF && s_rc.n_self_groups > 0) ? s_dyn + 2 * kWarps * kNJ * 32 : nullptr, s_qs,
+                     (SELF && s_rc.n_self_groups > 0 && s_rc.self_frames) ? s_grp : nullptr};
         unsigned ngath = 0;
         if (s_inst.L == 32)
             run_block<GT, false, SELF, true>(s_rc, s_inst.g, st, job, nullptr, 1, 32, s_inst.P, w.y, sm, ngath);

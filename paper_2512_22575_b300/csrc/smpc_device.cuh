@@ -108,8 +108,14 @@ struct RobotConst {
 // the world centres of the step's spheres, then of the frames' bounding
 // spheres.  Frame layout (self_frames, every group dense and every frame
 // in a group on a line, its bounding-sphere centre too): per frame j, its
-// origin t and its rotated direction v = R w, 6 floats; every sphere and
-// bounding centre of the frame is t + lambda v.
+// origin t and its rotated direction v = R w, 6 floats in grid units (the
+// chain's own origin and R w / res); every sphere and bounding centre of the
+// frame is t + lambda v.  The sphere layout keeps a
+// slot's 32 lanes contiguous (slot s of a lane at s * 32); the frame layout
+// keeps a lane's 6 floats of a frame contiguous (frame j of lane l at
+// j * 192 + 6 l: t.x, t.y, v.x, v.y, t.z, v.z), read and written as three
+// 8-byte pairs (a warp's 8-byte accesses at a 24-byte lane stride fall in
+// distinct banks per half-warp).
 constexpr int kSelfFrameSlots = 6;
 __host__ __device__ constexpr int self_slots(int n_spheres, bool frames)
 {

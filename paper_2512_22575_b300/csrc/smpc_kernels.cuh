@@ -134,13 +134,19 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         const f3 gt = F.t;          // the chain runs in grid units
         f3 v{}, tm{};
         if (SELF && sp) {
-            // the self term works in metres: the origin converted, v = R w
-            tm = grid_to_metres(g, F.t);
-            v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
-            if (rc.self_frames && pm_ok(kSelfFrameSlots * j + 5 < self_slots(rc.n_spheres, true), kErrSelf, g)) {
-                float *fs = sp + kSelfFrameSlots * j * 32;
-                fs[0] = tm.x; fs[32] = tm.y; fs[64] = tm.z;
-                fs[96] = v.x; fs[128] = v.y; fs[160] = v.z;
+            if (rc.self_frames) {
+                // the frame layout works in grid units: the origin and the
+                // direction as the chain has them
+                if (pm_ok(kSelfFrameSlots * j + 5 < self_slots(rc.n_spheres, true), kErrSelf, g)) {
+                    float2 *fs = reinterpret_cast<float2 *>(sp + kSelfFrameSlots * j * 32);
+                    fs[0] = make_float2(gt.x, gt.y);
+                    fs[1] = make_float2(gv.x, gv.y);
+                    fs[2] = make_float2(gt.z, gv.z);
+                }
+            } else {
+                // the sphere layout works in metres: the origin converted, v = R w
+                tm = grid_to_metres(g, F.t);
+                v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
             }
         }
         for (int s0 = b; s0 < e; s0 += kSphereBatch) {
@@ -226,76 +232,155 @@ __device__ __forceinline__ float pair_distance(float d2)
     return v * rsqrtf(v);
 }
 
+// Frame layout: the self-collision groups as per-block records in shared
+// memory, kSelfGroupRec float4 each, built once per block from RobotConst,
+// so that a step reads a group's constants with a few broadcast loads
+// instead of indexing the constant tables through the group's frames and
+// spheres.  The frame layout works in grid units (lengths / res): the slots
+// hold the chain's own origins and directions, and the squared thresholds
+// are scaled by 1/res^2, rounded up:
+//   [0]  slot offsets of frames a and b (floats, as int bits), link_lc[a], link_lc[b]
+//   [1]  grp_thr2 / res^2, |w_a / res|^2, |w_b / res|^2, res
+//   [2], [3]  lambda and radius (metres) of frame a's spheres 0..3; [4], [5] frame b's
+//   [6 + i]   the contact thresholds ((r_a + r_b + 1e-5 m) / res)^2, rounded
+//             up, of frame a's sphere i with frame b's spheres 0..3.
+// Past a frame's count a record repeats its last sphere with a NaN radius,
+// whose pair thresholds are NaN, so the contact tests fail for them.  A
+// group whose frame or sphere indices are out of range (bounds-checked
+// builds) gets offsets 0 and NaN radii.
+constexpr int kSelfGroupRec = 10;
+__device__ __forceinline__ void self_frame_rec(const RobotConst &rc, const GridConst &g, int f, bool ok,
+                                               float4 &l4, float4 &r4)
+{
+    static_assert(kSelfDense == 4, "one float4 per frame's lambdas and radii");
+    const float nan = __int_as_float(0x7fc00000);
+    const int lo = ok ? rc.link_begin[f + 1] : 0, n = ok ? rc.link_begin[f + 2] - lo : 0;
+    float l[kSelfDense], rr[kSelfDense];
+#pragma unroll
+    for (int i = 0; i < kSelfDense; ++i) {
+        const int s = lo + max(min(i, n - 1), 0);
+        const bool sok = pm_ok(s >= 0 && s < kMaxSpheres, kErrSelf, g);
+        l[i] = sok ? rc.sph_ls[s].x : 0.f;
+        rr[i] = sok && i < n ? rc.sph_r[s] : nan;
+    }
+    l4 = make_float4(l[0], l[1], l[2], l[3]);
+    r4 = make_float4(rr[0], rr[1], rr[2], rr[3]);
+}
+__device__ __forceinline__ void build_self_groups(const RobotConst &rc, const GridConst &g, float4 *tab)
+{
+    for (int gi = threadIdx.x; gi < rc.n_self_groups; gi += blockDim.x) {
+        if (!pm_ok(gi < kMaxSelfGroups, kErrSelf, g)) break;
+        const int fa = rc.grp_fa[gi], fb = rc.grp_fb[gi];
+        const bool ok = pm_ok(fa < kNJ && fb < kNJ, kErrSelf, g);
+        float4 *r = tab + kSelfGroupRec * gi;
+        r[0] = make_float4(__int_as_float(ok ? kSelfFrameSlots * fa * 32 : 0),
+                           __int_as_float(ok ? kSelfFrameSlots * fb * 32 : 0),
+                           ok ? rc.link_lc[fa] : 0.f, ok ? rc.link_lc[fb] : 0.f);
+        // 1/res rounded up keeps every scaled threshold at or above its exact value
+        const float ir = __frcp_ru(g.res);
+        const float *wa = rc.link_wg[ok ? fa : 0], *wb = rc.link_wg[ok ? fb : 0];
+        r[1] = make_float4(__fmul_ru(__fmul_ru(rc.grp_thr2[gi], ir), ir),
+                           fmaf(wa[0], wa[0], fmaf(wa[1], wa[1], wa[2] * wa[2])),
+                           fmaf(wb[0], wb[0], fmaf(wb[1], wb[1], wb[2] * wb[2])), g.res);
+        float4 la4, ra4, lb4, rb4;
+        self_frame_rec(rc, g, fa, ok, la4, ra4);
+        self_frame_rec(rc, g, fb, ok, lb4, rb4);
+        r[2] = la4; r[3] = ra4; r[4] = lb4; r[5] = rb4;
+        const float ra[4] = {ra4.x, ra4.y, ra4.z, ra4.w}, rb[4] = {rb4.x, rb4.y, rb4.z, rb4.w};
+        float t2[4];
+#pragma unroll
+        for (int i = 0; i < kSelfDense; ++i) {
+#pragma unroll
+            for (int k = 0; k < kSelfDense; ++k) {
+                const float t = __fmul_ru(__fadd_ru(__fadd_rn(ra[i], rb[k]), 1e-5f), ir);
+                t2[k] = __fmul_ru(t, t);
+            }
+            r[6 + i] = make_float4(t2[0], t2[1], t2[2], t2[3]);
+        }
+    }
+}
+
 // Self-collision term (Eqs. 18-20): w_self sum over S of max(0, -d_self)^2,
 // d_self = |c_a - c_b| - (r_a + r_b), from the sphere and bounding-sphere
-// centres the step stored in its lane's slots sp (stride 32 floats).
-__device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp)
+// centres the step stored in its lane's slots sp (sphere layout: stride 32
+// floats; frame layout: a frame's 6 floats contiguous, frames 192 floats
+// apart); with the frame layout, grp holds the groups' records
+// (build_self_groups).
+__device__ __forceinline__ float self_cost(const RobotConst &rc, const float *sp, const float4 *grp)
 {
     float acc = 0.f;
     if (rc.self_frames) {
         // frame layout: every group dense, every centre t + lambda_s v of its
         // frame (the same pairs and order as the dense blocks below)
         for (int gi = 0; gi < rc.n_self_groups; ++gi) {
-            const int fa = rc.grp_fa[gi], fb = rc.grp_fb[gi];
-            const float *pa = sp + kSelfFrameSlots * fa * 32, *pb = sp + kSelfFrameSlots * fb * 32;
-            const f3 tb = mk(pb[0], pb[32], pb[64]), vb = mk(pb[96], pb[128], pb[160]);
-            const f3 ta = mk(pa[0], pa[32], pa[64]), va = mk(pa[96], pa[128], pa[160]);
+            const float4 *rec = grp + kSelfGroupRec * gi;
+            const float4 r0 = rec[0], r1 = rec[1];
+            const float2 *pa = reinterpret_cast<const float2 *>(sp + __float_as_int(r0.x));
+            const float2 *pb = reinterpret_cast<const float2 *>(sp + __float_as_int(r0.y));
+            const float2 b0 = pb[0], b1 = pb[1], b2 = pb[2], a0 = pa[0], a1 = pa[1], a2 = pa[2];
+            const f3 tb = mk(b0.x, b0.y, b2.x), vb = mk(b1.x, b1.y, b2.y);
+            const f3 ta = mk(a0.x, a0.y, a2.x), va = mk(a1.x, a1.y, a2.y);
             // c_a - c_b = dl + l_a va - l_b vb with dl = ta - tb, so
             // |c_a - c_b|^2 = P_a + Q_b + m_a l_b with, per group, the dot
             // products of dl, va, vb (|va|^2 = |w_a|^2: a rotation keeps lengths):
             //   P_a = |dl|^2 + l_a (l_a |w_a|^2 + 2 dl.va),  m_a = -2 l_a va.vb,
             //   Q_b = l_b (l_b |w_b|^2 - 2 dl.vb),
-            // two operations per pair instead of six.  The skip test is still
-            // exact: the rounding of this sum stays below 1e-7 m^2 for arm-sized
-            // frames, far inside the pair threshold's 1e-5 m margin (about
-            // 2e-6 m^2 at these radii).
+            // two operations per pair instead of six, all in grid units.  The
+            // skip test is still exact: the rounding of this sum stays below
+            // 1e-6 of the squared frame distances (1e-7 m^2 for arm-sized
+            // frames), far inside the pair threshold's 1e-5 m margin (about
+            // 2e-6 m^2 at these radii); both scale alike by 1/res^2.
             // the frames' bounding spheres, centred at lambda-bar on each line:
             // apart beyond their radii + 0.1 mm, every pair of the group is
             // apart (exact zero); tested before the group's dot products
             {
-                const f3 g = sub(axpy(rc.link_lc[fa], va, ta), axpy(rc.link_lc[fb], vb, tb));
-                if (dot(g, g) > rc.grp_thr2[gi]) continue;
+                const f3 gc = sub(axpy(r0.z, va, ta), axpy(r0.w, vb, tb));
+                if (dot(gc, gc) > r1.x) continue;
             }
             const f3 dl = sub(ta, tb);
             const float D = dot(dl, dl), Da2 = 2.0f * dot(dl, va), Db2 = 2.0f * dot(dl, vb);
             const float Vab2 = -2.0f * dot(va, vb);
-            const float wa2 = rc.link_w2[fa], wb2 = rc.link_w2[fb];
-            const int a_lo = rc.link_begin[fa + 1], na = rc.link_begin[fa + 2] - a_lo;
-            const int b_lo = rc.link_begin[fb + 1], nb = rc.link_begin[fb + 2] - b_lo;
-            // The group as a full 4 x 4 block: past a frame's count, its last
-            // sphere again with a NaN radius, whose pair thresholds are NaN, so
-            // the contact tests below fail for them (no masks, no loop bounds).
-            // Frame b's spheres in pairs (2h, 2h+1) for the packed FP32 units.
+            const float wa2 = r1.y, wb2 = r1.z, res = r1.w;
+            // The group as a full 4 x 4 block (NaN radii past a frame's
+            // count: no masks, no loop bounds); frame b's spheres in pairs
+            // (2h, 2h+1) for the packed FP32 units.
             static_assert(kSelfDense == 4, "two pairs of frame-b spheres");
-            const float nan = __int_as_float(0x7fc00000);
-            float2 lb[2], Qb[2], br[2];
+            const float4 la4 = rec[2], ra4 = rec[3], lb4 = rec[4], rb4 = rec[5];
+            const float2 lb[2] = {make_float2(lb4.x, lb4.y), make_float2(lb4.z, lb4.w)};
+            const float2 br[2] = {make_float2(rb4.x, rb4.y), make_float2(rb4.z, rb4.w)};
+            float2 Qb[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int s0 = b_lo + min(2 * h, nb - 1), s1 = b_lo + min(2 * h + 1, nb - 1);
-                lb[h] = make_float2(rc.sph_ls[s0].x, rc.sph_ls[s1].x);
-                br[h] = make_float2(2 * h < nb ? rc.sph_r[s0] : nan, 2 * h + 1 < nb ? rc.sph_r[s1] : nan);
+            for (int h = 0; h < 2; ++h)
                 Qb[h] = __fmul2_rn(lb[h], __ffma2_rn(lb[h], make_float2(wb2, wb2), make_float2(-Db2, -Db2)));
-            }
 #pragma unroll
             for (int i = 0; i < kSelfDense; ++i) {
-                const int a = a_lo + min(i, na - 1);
-                const float la = rc.sph_ls[a].x, ra = i < na ? rc.sph_r[a] : nan;
+                const float la = i == 0 ? la4.x : i == 1 ? la4.y : i == 2 ? la4.z : la4.w;
+                const float ra = i == 0 ? ra4.x : i == 1 ? ra4.y : i == 2 ? ra4.z : ra4.w;
                 const float Pa = fmaf(la, fmaf(la, wa2, Da2), D), ma = la * Vab2;
+                const float4 t24 = rec[6 + i];
+                const float2 t2[2] = {make_float2(t24.x, t24.y), make_float2(t24.z, t24.w)};
+                // the same operations as per pair: d2 = m_a l_b + (P_a + Q_b);
+                // one branch per row of four pairs, taken where one of them
+                // is within its threshold (rarely: most pairs of a group that
+                // passed its bounding test are still apart)
+                float2 d2[2];
+                bool near = false;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    // the same operations as per pair: d2 = m_a l_b + (P_a + Q_b),
-                    // threshold (r_a + r_b + 1e-5)^2 rounded up
-                    const float2 d2 = __ffma2_rn(make_float2(ma, ma), lb[h], __fadd2_rn(make_float2(Pa, Pa), Qb[h]));
-                    const float2 rs = __fadd2_rn(make_float2(ra, ra), br[h]);
-                    const float2 t = __fadd2_ru(rs, make_float2(1e-5f, 1e-5f));
-                    const float2 t2 = __fmul2_ru(t, t);
-                    if (d2.x <= t2.x) {
-                        const float del = fmaxf(rs.x - pair_distance(d2.x), 0.f);
-                        acc = fmaf(del, del, acc);
-                    }
-                    if (d2.y <= t2.y) {
-                        const float del = fmaxf(rs.y - pair_distance(d2.y), 0.f);
-                        acc = fmaf(del, del, acc);
+                    d2[h] = __ffma2_rn(make_float2(ma, ma), lb[h], __fadd2_rn(make_float2(Pa, Pa), Qb[h]));
+                    near |= (d2[h].x <= t2[h].x) | (d2[h].y <= t2[h].y);
+                }
+                if (near) {
+                    // the row's pairs in order, del in metres; a pair apart
+                    // adds del = 0 (acc + 0 = acc: the same sum as skipping it)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float dx =
+                            d2[h].x <= t2[h].x ? fmaxf(fmaf(-res, pair_distance(d2[h].x), ra + br[h].x), 0.f) : 0.f;
+                        acc = fmaf(dx, dx, acc);
+                        const float dy =
+                            d2[h].y <= t2[h].y ? fmaxf(fmaf(-res, pair_distance(d2[h].y), ra + br[h].y), 0.f) : 0.f;
+                        acc = fmaf(dy, dy, acc);
                     }
                 }
             }
@@ -411,7 +496,7 @@ template <typename GT, bool TRACE, bool SELF, bool QMEM = false, bool LIM = true
 __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridConst &g,
                                             const InstanceState &st, const float *q,
                                             const float *qd, bool terminal, float *tr,
-                                            unsigned &ngath, float *sp, const float *qa = nullptr,
+                                            unsigned &ngath, float *sp, const float4 *sg, const float *qa = nullptr,
                                             int qstride = 1)
 {
     if (!SELF || terminal) sp = nullptr;
@@ -467,7 +552,7 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
     lq *= rc.w_q;
     lqd *= rc.w_qd;
     ns *= rc.w_ns;
-    const float self = (SELF && sp) ? self_cost(rc, sp) : 0.f;
+    const float self = (SELF && sp) ? self_cost(rc, sp, sg) : 0.f;
     if (TRACE) { tr[0] = pose; tr[1] = env; tr[2] = self; tr[3] = lq; tr[4] = lqd; tr[7] = ns; }
     return pose + env + self + lq + lqd + ns;
 }
@@ -568,6 +653,7 @@ struct BlockSmem {
     float *wm, *wz;             // [kWarps]
     float *self;                // [kWarps][self_slots][32] when the self term is on, else null
     float *qs;                  // [kWarps][C][kStageFloats][32]: q, qd, control cost per step (STAGE)
+    const float4 *grp;          // [n_self_groups][kSelfGroupRec] (frame layout), else null
 };
 
 // Floats staged per step: q, qd and the control cost.
@@ -600,7 +686,9 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
     float run_m = CUDART_INF_F, run_z = 0.f;
     const float dt = job_dt<DYN>(job), dt2 = dt * dt;
     float *sp = (SELF && rc.n_self_groups > 0 && sm.self)
-                    ? sm.self + warp * self_slots(rc.n_spheres, rc.self_frames) * 32 + lane : nullptr;
+                    ? sm.self + warp * self_slots(rc.n_spheres, rc.self_frames) * 32 +
+                          (rc.self_frames ? kSelfFrameSlots * lane : lane)
+                    : nullptr;
     const int half = (P == 2) ? (warp & 1) : 0;
     const int pr = warp >> 1;
     const int kbase = half * 32 * C;
@@ -828,7 +916,7 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             const unsigned ng0 = ngath;
             // staged one-step lanes carry their limit terms in cc (LIM = false)
             const float sc = state_cost<GT, TRACE, SELF, STAGE, !STAGE || TRACE>(rc, g, st, q, qd, !extra && k + 1 == H,
-                                                                               tr_x, ngath, sp, qa, qstride);
+                                                                               tr_x, ngath, sp, sm.grp, qa, qstride);
             if (extra) {
                 ngath = ng0;        // lookups of the roll-outs only
                 *job.c0 = sc + cc;
@@ -975,7 +1063,12 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     // one-step shapes stage their steps' states (run_block, STAGE)
     constexpr bool kStage = (C == 1);
     __shared__ float s_qs[kStage ? kWarps * kStageFloats * 32 : 1];
+    __shared__ float4 s_grp[SELF ? kMaxSelfGroups * kSelfGroupRec : 1];
 
+    // the group records depend on the parameters alone: built before the
+    // wait for the previous kernel
+    const bool frame_groups = SELF && rc.n_self_groups > 0 && rc.self_frames;
+    if (frame_groups) build_self_groups(rc, g, s_grp);
     grid_dependency_prologue();
     load_state(a.in, a.cs, s_state);
     __syncthreads();
@@ -1002,7 +1095,8 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     job.noise_dtype = a.noise_dtype;
     float *self_slots_base = s_dyn + 2 * kWarps * C * kNJ * 32;
     BlockSmem sm{s_dyn, s_dyn + kWarps * C * kNJ * 32, s_tot, s_S, SELF ? self_slots_base : s_blk, s_wm, s_wz,
-                 (SELF && rc.n_self_groups > 0) ? self_slots_base : nullptr, s_qs};
+                 (SELF && rc.n_self_groups > 0) ? self_slots_base : nullptr, s_qs,
+                 frame_groups ? s_grp : nullptr};
     unsigned ngath = 0;
     run_block<GT, TRACE, SELF, kStage, DYN>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
     if (!TRACE && a.gathers) {
