@@ -91,8 +91,11 @@ IterKernel lookup_dense_kernel(int dtype, TileShape s)
 // a short launch is dominated by its partly filled last round, a long one
 // by the throughput per round.  (When the instantiations were fitted at 80
 // and 72 registers, K = 4096, H = 64 ran 3 rounds of 1776 units or 2 of
-// 2072, replan 290 -> 280 us, and K = 16384 862 against 927 us per replan;
-// both now hold 7 blocks per SM for that shape, and the default one runs.)
+// 2072, replan 290 -> 280 us, and K = 16384 862 against 927 us per replan.)
+// At equal residency the dense one runs as well on a launch of at most two
+// rounds: only it draws its first tile's normals before the wait for the
+// previous kernel (replan K = 4096, H = 64 2.3% and K = 1024 5.6% shorter;
+// at K = 16384, eight rounds, the default one is 2% faster).
 struct KernelPick {
     IterKernel fn = nullptr;
     size_t smem = 0;
@@ -117,7 +120,10 @@ pm_status pick_kernel(pm_ctx *c, long long K, TileShape sh, bool trace, KernelPi
         const long long upb = kWarps / sh.P, tiles = (K + 32 / sh.L - 1) / (32 / sh.L);
         const long long units = out.resident * upb, units_d = static_cast<long long>(c->n_sm) * per_sm_d * upb;
         const long long rounds = (tiles + units - 1) / units, rounds_d = (tiles + units_d - 1) / units_d;
-        if (per_sm_d > per_sm && rounds_d < rounds && rounds_d <= 2) {
+        // at equal residency the dense one runs too on a launch of at most
+        // two rounds: it draws its first tile's normals before waiting for
+        // the previous kernel
+        if (rounds_d <= 2 && (per_sm_d == per_sm || (per_sm_d > per_sm && rounds_d < rounds))) {
             out.fn = dense;
             out.resident = static_cast<long long>(c->n_sm) * per_sm_d;
         }

@@ -30,6 +30,8 @@
 // given launch shape.
 #pragma once
 
+#include <type_traits>
+
 #include "smpc_device.cuh"
 
 namespace pm {
@@ -667,7 +669,8 @@ template <typename GT, bool TRACE, bool SELF, bool STAGE, bool DYN = false>
 __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst &g,
                                           const InstanceState &st, const TileJob &job,
                                           float *trace, const int C, const int L, const int P,
-                                          const int lb, const BlockSmem &sm, unsigned &ngath)
+                                          const int lb, const BlockSmem &sm, unsigned &ngath,
+                                          const float *z0 = nullptr)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = 32 / L;
@@ -733,8 +736,15 @@ __device__ __forceinline__ void run_block(const RobotConst &rc, const GridConst 
             float ub[kNJ];
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) ub[j] = __ldg(job.Ubar + pm_idx(kc * kNJ + j, H * kNJ, kErrUbar, g));
-            step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
-                         static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
+            if (STAGE && z0 && tile == unit) {
+                // the first tile's normals, drawn before the kernel waited
+                // for the previous one (smpc_iteration_kernel)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) z[j] = z0[j];
+            } else {
+                step_normals(job_seed_lo<DYN>(job), job_seed_hi<DYN>(job), job_iter<DYN>(job), static_cast<uint32_t>(m),
+                             static_cast<uint32_t>(k), z, rc.poly, DYN ? nullptr : job.rk);
+            }
             float ev[kNJ];
 #pragma unroll
             for (int j = 0; j < kNJ; ++j) ev[j] = st.sigma[j] * z[j];
@@ -1069,6 +1079,26 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     // wait for the previous kernel
     const bool frame_groups = SELF && rc.n_self_groups > 0 && rc.self_frames;
     if (frame_groups) build_self_groups(rc, g, s_grp);
+    // The normals of a one-step lane's first tile depend on the parameters
+    // alone (the Philox key, the iteration, the roll-out and step indices):
+    // drawn before the wait, they overlap the previous kernels' tails (replan
+    // 2% shorter).  Only in the kDenseBlocks instantiations, which fit it in
+    // 72 registers with a float field (the 80-register budget of the default
+    // one would take 80 and hold a block fewer; the half-precision fields'
+    // fits would spill); not with the self term, whose kernel is at its
+    // register budget (0.7% longer), nor where the scalars come from device
+    // memory.
+    constexpr bool kPreSample =
+        kStage && !DYN && !TRACE && !SELF && MINB == kDenseBlocks && std::is_same<GT, float>::value;
+    float z0[8];
+    if (kPreSample) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int unit = (static_cast<int>(blockIdx.x) * kWarps + warp) / P;   // run_block's first tile
+        const int m = unit * (32 / L) + lane / L;
+        const int k = ((P == 2) ? (warp & 1) : 0) * 32 + lane % L;
+        step_normals(a.cs.seed_lo, a.cs.seed_hi, a.cs.iter, static_cast<uint32_t>(m), static_cast<uint32_t>(k), z0,
+                     rc.poly, &a.rk);
+    }
     grid_dependency_prologue();
     load_state(a.in, a.cs, s_state);
     __syncthreads();
@@ -1098,7 +1128,8 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
                  (SELF && rc.n_self_groups > 0) ? self_slots_base : nullptr, s_qs,
                  frame_groups ? s_grp : nullptr};
     unsigned ngath = 0;
-    run_block<GT, TRACE, SELF, kStage, DYN>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath);
+    run_block<GT, TRACE, SELF, kStage, DYN>(rc, g, st, job, a.trace, C, L, P, blockIdx.x, sm, ngath,
+                                            kPreSample ? z0 : nullptr);
     if (!TRACE && a.gathers) {
         const int lane = threadIdx.x & 31;
         unsigned n = ngath;
