@@ -124,7 +124,7 @@ __device__ __forceinline__ bool batch_may_gather(const float (&mn)[kSphereBatch]
 template <typename GT, bool SELF>
 __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst &g,
                                           const Frame &F, int j, int b, int e, float wg0, bool count,
-                                          unsigned &ngath, float *sp)
+                                          unsigned &ngath, float *spf, float *sps)
 {
     float env = 0.f;
     if (rc.link_line[j]) {
@@ -134,21 +134,26 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
         const float2 ww = rc.fk_ww[j];
         const f3 gv = axpy(ww.y, F.c3, axpy(ww.x, F.c2, scale(wg0, F.c1)));
         const f3 gt = F.t;          // the chain runs in grid units
-        f3 v{}, tm{};
-        if (SELF && sp) {
-            if (rc.self_frames) {
-                // the frame layout works in grid units: the origin and the
-                // direction as the chain has them
-                if (pm_ok(kSelfFrameSlots * j + 5 < self_slots(rc.n_spheres, true), kErrSelf, g)) {
-                    float2 *fs = reinterpret_cast<float2 *>(sp + kSelfFrameSlots * j * 32);
-                    fs[0] = make_float2(gt.x, gt.y);
-                    fs[1] = make_float2(gv.x, gv.y);
-                    fs[2] = make_float2(gt.z, gv.z);
-                }
-            } else {
-                // the sphere layout works in metres: the origin converted, v = R w
-                tm = grid_to_metres(g, F.t);
-                v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
+        if (SELF && spf) {
+            // the frame layout works in grid units: the origin and the
+            // direction as the chain has them
+            if (pm_ok(kSelfFrameSlots * j + 5 < self_slots(rc.n_spheres, true), kErrSelf, g)) {
+                float2 *fs = reinterpret_cast<float2 *>(spf + kSelfFrameSlots * j * 32);
+                fs[0] = make_float2(gt.x, gt.y);
+                fs[1] = make_float2(gv.x, gv.y);
+                fs[2] = make_float2(gt.z, gv.z);
+            }
+        } else if (SELF && sps) {
+            // the sphere layout works in metres: the origin converted,
+            // v = R w, each centre t + lambda_s v kept for the self term
+            const f3 tm = grid_to_metres(g, F.t);
+            const f3 v = axpy(rc.link_w[j][2], F.c3, axpy(rc.link_w[j][1], F.c2, scale(rc.link_w[j][0], F.c1)));
+            for (int s = b; s < e; ++s) {
+                if (!pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) break;
+                const f3 p = axpy(rc.sph_ls[s].x, v, tm);
+                sps[(3 * s) * 32] = p.x;
+                sps[(3 * s + 1) * 32] = p.y;
+                sps[(3 * s + 2) * 32] = p.z;
             }
         }
         for (int s0 = b; s0 < e; s0 += kSphereBatch) {
@@ -159,13 +164,6 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
                 const int s = s0 + i;               // past e: zero padding, masked below
                 ls[i] = rc.sph_ls[s];
                 const float lam = ls[i].x;
-                if (SELF && sp && !rc.self_frames && i < e - s0 &&
-                    pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {   // kept for the self term
-                    const f3 p = axpy(lam, v, tm);
-                    sp[(3 * s) * 32] = p.x;
-                    sp[(3 * s + 1) * 32] = p.y;
-                    sp[(3 * s + 2) * 32] = p.z;
-                }
                 const float2 gxy = __ffma2_rn(make_float2(lam, lam), make_float2(gv.x, gv.y), make_float2(gt.x, gt.y));
                 mn[i] = tex3D<float>(g.cmin_tex, gxy.x, gxy.y, fmaf(lam, gv.z, gt.z));
             }
@@ -196,12 +194,12 @@ __device__ __forceinline__ float link_env(const RobotConst &rc, const GridConst 
             const int s = s0 + i;               // past e: zero padding, masked below
             // grid coordinates of the centre (the chain runs in grid units)
             const f3 p = frame_point(F, rc.sph_off_g[s][0], rc.sph_off_g[s][1], rc.sph_off_g[s][2]);
-            if (SELF && sp && !rc.self_frames && i < e - s0 &&
+            if (SELF && sps && i < e - s0 &&
                 pm_ok(3 * s + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {   // kept for the self term
                 const f3 pm = grid_to_metres(g, p);
-                sp[(3 * s) * 32] = pm.x;
-                sp[(3 * s + 1) * 32] = pm.y;
-                sp[(3 * s + 2) * 32] = pm.z;
+                sps[(3 * s) * 32] = pm.x;
+                sps[(3 * s + 1) * 32] = pm.y;
+                sps[(3 * s + 2) * 32] = pm.z;
             }
             mn[i] = tex3D<float>(g.cmin_tex, p.x, p.y, p.z);
         }
@@ -521,6 +519,9 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
 #pragma unroll
         for (int j = 0; j < kNJ; ++j) qr[j] = q[j];
     }
+    // the self term's slots by layout, decided once per step
+    float *const spf = (SELF && sp && rc.self_frames) ? sp : nullptr;
+    float *const sps = (SELF && sp && !rc.self_frames) ? sp : nullptr;
 #pragma unroll 1
     for (int j = 0; j < kNJ; ++j) {
         const float2 cs = rc.fk_cs[j], ad = rc.fk_ad[j], tw = rc.fk_tw[j];
@@ -530,15 +531,15 @@ __device__ __forceinline__ float state_cost(const RobotConst &rc, const GridCons
             for (int i = 0; i + 1 < kNJ; ++i) qr[i] = qr[i + 1];
         }
         const int2 be = rc.fk_be[j];
-        env += link_env<GT, SELF>(rc, g, F, j, be.x, be.y, tw.y, !terminal, ngath, sp);
-        if (SELF && sp && !rc.self_frames &&
+        env += link_env<GT, SELF>(rc, g, F, j, be.x, be.y, tw.y, !terminal, ngath, spf, sps);
+        if (SELF && sps &&
             pm_ok(3 * rc.n_spheres + 3 * j + 2 < self_slots(rc.n_spheres, false), kErrSelf, g)) {
             const f3 c = grid_to_metres(g, frame_point(F, rc.link_c[j][0] * g.inv_res, rc.link_c[j][1] * g.inv_res,
                                                        rc.link_c[j][2] * g.inv_res));
             const int t = 3 * rc.n_spheres + 3 * j;
-            sp[t * 32] = c.x;
-            sp[(t + 1) * 32] = c.y;
-            sp[(t + 2) * 32] = c.z;
+            sps[t * 32] = c.x;
+            sps[(t + 1) * 32] = c.y;
+            sps[(t + 2) * 32] = c.z;
         }
     }
     const f3 tee = grid_to_metres(g, axpy(rc.flange_dg, F.c3, F.t));
