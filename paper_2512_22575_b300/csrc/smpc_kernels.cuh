@@ -1087,18 +1087,23 @@ smpc_iteration_kernel(const __grid_constant__ RobotConst rc, const __grid_consta
     // 72 registers with a float field (the 80-register budget of the default
     // one would take 80 and hold a block fewer; the half-precision fields'
     // fits would spill); not with the self term, whose kernel is at its
-    // register budget (0.7% longer), nor where the scalars come from device
-    // memory.
+    // register budget (0.7% longer).
     constexpr bool kPreSample =
-        kStage && !DYN && !TRACE && !SELF && MINB == kDenseBlocks && std::is_same<GT, float>::value;
+        kStage && !TRACE && !SELF && MINB == kDenseBlocks && std::is_same<GT, float>::value;
     float z0[8];
     if (kPreSample) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int unit = (static_cast<int>(blockIdx.x) * kWarps + warp) / P;   // run_block's first tile
         const int m = unit * (32 / L) + lane / L;
         const int k = ((P == 2) ? (warp & 1) : 0) * 32 + lane % L;
-        step_normals(a.cs.seed_lo, a.cs.seed_hi, a.cs.iter, static_cast<uint32_t>(m), static_cast<uint32_t>(k), z0,
-                     rc.poly, &a.rk);
+        // a replayed graph's scalars: its call block, which a copy before
+        // the graph wrote and no kernel of the graph writes (load_state
+        // forms the same key and iteration from it)
+        const uint32_t s_lo = DYN ? __float_as_uint(__ldg(a.in.dyn + kDynSeedLo)) : a.cs.seed_lo;
+        const uint32_t s_hi = DYN ? __float_as_uint(__ldg(a.in.dyn + kDynSeedHi)) : a.cs.seed_hi;
+        const uint32_t it = DYN ? __float_as_uint(__ldg(a.in.dyn + kDynIter0)) + a.cs.iter : a.cs.iter;
+        step_normals(s_lo, s_hi, it, static_cast<uint32_t>(m), static_cast<uint32_t>(k), z0, rc.poly,
+                     DYN ? nullptr : &a.rk);
     }
     grid_dependency_prologue();
     load_state(a.in, a.cs, s_state);
