@@ -8,7 +8,8 @@ skips the access (no trap).  A child process loads that build (the
 library is chosen when the package is imported) and runs the plain
 iteration, ragged and maximal shapes, every tile shape, the trace, the
 host-buffer graph path, a replan, a batch through both batch kernels, the
-self-collision variant and the no-allocation entry point; every word must
+self-collision variant in both slot layouts (alone, traced and batched)
+and the no-allocation entry point; every word must
 stay 0 and the results must still match the oracle: costs within S_REL, U*
 within U_ISO of the FP64 update from the GPU's own costs, and within U_ABS of
 the oracle's U* where the soft-min is well conditioned (the conditioning
@@ -117,6 +118,32 @@ CHILD = textwrap.dedent("""
     Us = np.zeros((32, 7), np.float32)
     ps.smpc_iterate(sc.q0, sc.qd0, sc.T, Us, 512, 0.02, 0.05, SIGMA, 3, 0)
     out["words"]["self"] = ps.bounds_status(reset=True)
+    # its trace, and the sphere layout (same-frame pairs: groups that are
+    # not dense blocks)
+    tr = torch.zeros((64, 33, 8), dtype=torch.float32, device=dev)
+    ps.rollout_trace(sc.q0, sc.qd0, sc.T, np.zeros((32, 7), np.float32), 64, 0.02, SIGMA, 3, 0, tr)
+    out["words"]["self_trace"] = ps.bounds_status(reset=True)
+    rb0 = workloads.panda_robot()
+    rb0["self_pairs"] = workloads.self_collision_pairs(rb0, min_link_gap=0)
+    ps0 = pm.Planner(rb0, sc.grid_desc, cp)
+    ps0.set_distance_field(sc.phi)
+    Us0 = np.zeros((32, 7), np.float32)
+    ps0.smpc_iterate(sc.q0, sc.qd0, sc.T, Us0, 512, 0.02, 0.05, SIGMA, 3, 0)
+    out["words"]["self_spheres"] = ps0.bounds_status(reset=True)
+    # both layouts through the batch kernels (their group records are built
+    # per instance), one-step and run-time shapes
+    for H, tag in ((32, "batch_self_one_step"), (100, "batch_self_run_time")):
+        items = [dict(ctx=pl, q=torch.from_numpy(sc.q0.astype(np.float32)).to(dev),
+                      qd=torch.from_numpy(sc.qd0.astype(np.float32)).to(dev),
+                      T_goal=torch.from_numpy(np.asarray(sc.T, np.float32).ravel().copy()).to(dev),
+                      U=torch.zeros((H, 7), dtype=torch.float32, device=dev), K=256, seed=50 + i)
+                 for i, pl in enumerate((ps, ps0))]
+        b = pm.Batch(0)
+        b.run(items, n_iters=2, flags=pm.PM_BATCH_REPLAN)
+        torch.cuda.synchronize()
+        b.close()
+        out["words"][tag] = max(it["ctx"].bounds_status(reset=True) for it in items)
+    ps0.close()
     ps.close()
     for pl in planners:
         pl.close()
@@ -136,7 +163,7 @@ def test_checked_build_finds_no_violation_and_keeps_parity():
     assert res["checked"] is True and res["lib"].endswith("libparamap_checked.so")
     bad = {k: v for k, v in res["words"].items() if v != 0}
     assert not bad, f"bounds violations (bit mask per workload): {bad}"
-    assert len(res["words"]) >= 24
+    assert len(res["words"]) >= 28
     for tag, (s_rel, u_abs, u_iso, bound) in res["parity"].items():
         # costs within S_REL and the update exact given the GPU's costs
         # (U_ISO) everywhere; U* against the oracle's within U_ABS wherever the
